@@ -332,6 +332,6 @@ def element_matrices(X, signs, k, nu):
 
 def load_vector(X, signs, k, f, q=None):
     """F_i = (f, phi^u_i)_T on each element; f(x[..., d]) -> [..., d]."""
-    D = element_data(X, signs, k, q=q if q is not None else k + 4)
+    D = element_data(X, signs, k, q=q if q is not None else k + 8)
     fv = f(D.xq)
     return np.einsum("eq,eqa,eqia->ei", D.wq, fv, D.U)

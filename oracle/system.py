@@ -270,3 +270,17 @@ def recover_stress(D: Discretization, x: np.ndarray):
     rhs[:, :ns] = -(np.einsum("eij,ei->ej", m["Bu"], xu) + np.einsum("eij,ei->ej", m["Bh"], xh))
     sol = np.linalg.solve(Mloc, rhs[..., None])[..., 0]
     return sol[:, :ns], sol[:, ns:]
+
+
+def pattern(D: Discretization) -> sp.csr_matrix:
+    """Structural sparsity of K = [[A, B^T], [B, 0]]: every element couples its (u, uhat) dofs
+    with each other and its u dofs with its pressure dofs (entries of value 1, no cancellation)."""
+    ne = D.mesh.elems.shape[0]
+    am = D.a_map
+    nA, nu_, npp = am.shape[1], D.u_map.shape[1], D.p_map.shape[1]
+    A = assemble(am, am, np.ones((ne, nA, nA)), (D.ndof, D.ndof))
+    B = assemble(D.p_map, D.u_map, np.ones((ne, npp, nu_)), (D.ndof, D.ndof))
+    P = (A + B + B.T).tocsr()
+    P.data[:] = 1.0
+    P.sort_indices()
+    return P
