@@ -1,0 +1,176 @@
+/*
+ * libmcs — GB300-native hot path of the mass-conserving mixed-stress (MCS)
+ * Stokes method of arXiv 2207.08481 ("A conforming auxiliary space
+ * preconditioner for the mass conserving mixed stress method").
+ *
+ * The library performs the two data-parallel steps of the method on one GPU:
+ *   1. static condensation of the element-local stress sigma and rotation
+ *      omega (Sec. 4.2, eq. femSPmat), followed by the bubble ("double Schur")
+ *      condensation (eqs. Hcoeffs, factorSsigma);
+ *   2. the preconditioned Krylov solve of the condensed saddle-point system
+ *      K = [[A, B^T], [B, 0]] with the block preconditioner of eq.
+ *      (mhatinvfactor), Shat_p = M_p (Sec. 5.1), and the multiplicative
+ *      auxiliary-space preconditioner on the condensed velocity block
+ *      (Sec. 6.1, Theorem aux_pc_schur, Corollary aux_pc_mult): facet-block
+ *      Gauss-Seidel, the embedding E^d of conforming P1 vector fields (eq.
+ *      defED) and one geometric-multigrid V-cycle as the solver C for
+ *      abar(u, v) = nu (eps u, eps v) (eq. defAhat).
+ *
+ * Conventions
+ *   - Every function returns an int status: MCS_OK (0) or a negative MCS_ERR_*.
+ *     mcs_last_error() returns a thread-local message for the last failure.
+ *     No C++ exception, abort or device trap crosses this interface.
+ *   - "device" pointers are CUDA global-memory pointers on the handle's device
+ *     (e.g. from torch); "host" pointers are ordinary CPU memory.  The caller
+ *     owns every buffer it passes; the library owns the handle and the
+ *     operators it keeps resident on the device.
+ *   - Calls are asynchronous on the handle's stream unless stated otherwise.
+ *   - Vectors of the condensed system have length ndof, layout
+ *       [u_d | u_o | uhat | p]
+ *     u_d: BDM facet moments (interior facet rank r, mode j) at r*nF + j;
+ *     u_o: BDM bubbles (element T, m) at off_o + T*n_bub + m;
+ *     uhat: tangential facet dofs (r, tangent m, mode j) at off_h + r*nhF + m*dimP^{k-1}(F) + j;
+ *     p: pressure (T, mode j) at off_p + T*n_p + j.
+ *     Basis functions, facet orientation and numbering follow the dof contract
+ *     documented in the design doc (Dubiner bases, Kuhn meshes, lexicographic
+ *     facets).  All boundary facets are Dirichlet (u = 0) and carry no dofs;
+ *     the pressure is fixed by a zero mean.
+ */
+#ifndef MCS_H
+#define MCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MCS_OK = 0,
+  MCS_ERR_INVALID_ARG = -1,
+  MCS_ERR_OOM = -2,
+  MCS_ERR_CUDA = -3,
+  MCS_ERR_NOT_CONVERGED = -4,
+  MCS_ERR_BREAKDOWN = -5,
+  MCS_ERR_TIMEOUT = -6,
+  MCS_ERR_UNSUPPORTED = -7
+};
+
+enum { MCS_FP64 = 0, MCS_MIXED = 1 };
+
+typedef struct mcs_handle mcs_handle;
+
+typedef struct {
+  int precision;      /* MCS_FP64: preconditioner in FP64; MCS_MIXED: preconditioner (smoother,
+                         E^d, V-cycle, bubble solves) in FP32, outer Krylov and K in FP64 */
+  int smooth_steps;   /* facet-block Gauss-Seidel sweeps before and after the coarse correction (2) */
+  int gmg_levels;     /* multigrid levels incl. the coarsest (-1: auto, coarsest 16^2 / 4^3 cells) */
+  int gmg_smooth;     /* l1-Jacobi sweeps before and after each coarse-grid correction (2) */
+  double rtol;        /* stop when ||r||_{Khat^{-1}} <= rtol * ||F - K x0||_{Khat^{-1}} (1e-8) */
+  int maxit;          /* total MinRes iterations (1000) */
+  int max_refine;     /* MCS_MIXED: outer FP64 refinement cycles (8) */
+  double inner_rtol;  /* MCS_MIXED: relative reduction per refinement cycle (1e-5) */
+} mcs_options;
+
+typedef struct {
+  int64_t ndof, n_dd, n_oo, n_hat, n_pres;  /* condensed system and its blocks */
+  int64_t off_o, off_h, off_p;
+  int64_t ne, nint, nfacets, nvertices;     /* mesh */
+  int64_t np1;                              /* conforming P1 dofs (interior vertices * d) */
+  int32_t dim, k, nF, n_bub, nhF, n_p, n_A, n_c, mF;
+  int32_t ncolours, gmg_levels;
+  int32_t nq_load;                          /* load quadrature points per element */
+  int64_t bytes_resident;                   /* device bytes held by the handle */
+} mcs_sizes_t;
+
+typedef struct {
+  int iterations;            /* MinRes iterations (all refinement cycles) */
+  int refinements;           /* outer cycles (1 for MCS_FP64) */
+  int status;                /* MCS_OK, MCS_ERR_NOT_CONVERGED or MCS_ERR_BREAKDOWN */
+  double rel_res_precond;    /* ||F - K x||_{Khat^{-1}} / ||F - K x0||_{Khat^{-1}} */
+  double rel_res_true;       /* ||F - K x||_2 / ||F||_2 (FP64) */
+} mcs_solve_info;
+
+/* Version of the library (e.g. 100 = 0.1.0). */
+int mcs_version(void);
+/* Thread-local description of the last error (never NULL). */
+const char* mcs_last_error(void);
+/* Fills *o with the defaults listed above. */
+int mcs_default_options(mcs_options* o);
+
+/* Set-up on the Kuhn triangulation of [0,1]^dim with N cells per direction
+ * (Sec. 7 uses unstructured meshes; the synthetic workloads use this nested
+ * family so that the conforming space has a geometric multigrid hierarchy).
+ * dim in {2, 3}, k >= 2 (Sec. 3; k = 1 is the variant of Sec. 6, not supported),
+ * nu > 0 as printed in eq. (stokes).  stream: a cudaStream_t (NULL = default).
+ * Builds mesh, facets, dof maps, colouring and the multigrid hierarchy on the
+ * host and uploads them; allocates the resident operators.  Synchronous.
+ * Errors: INVALID_ARG (bad sizes, N not divisible for the requested levels),
+ * UNSUPPORTED (dim/k out of range), OOM, CUDA. */
+int mcs_setup_structured(int dim, int N, int k, double nu, const mcs_options* opt, void* stream,
+                         mcs_handle** out);
+
+/* Set-up on a general simplicial mesh (host arrays, copied): coords [nv][dim],
+ * elems [ne][dim+1] with ascending vertex ids per element.  The conforming
+ * solver C is then an exact solve on the mesh's own P1 space (single level),
+ * so this is meant for small meshes.  Errors as above. */
+int mcs_setup_mesh(int dim, int64_t nv, const double* coords, int64_t ne, const int32_t* elems, int k,
+                   double nu, const mcs_options* opt, void* stream, mcs_handle** out);
+
+/* Sizes, offsets and resident bytes of a handle. */
+int mcs_sizes(const mcs_handle* h, mcs_sizes_t* s);
+
+/* Mesh and numbering export (host buffers, for bit-exact checks of the dof contract):
+ * facets [nfacets][dim] sorted vertex ids; elem_facets [ne][dim+1]; signs [ne][dim+1]
+ * orientation s_{T,f}; colour [nint] facet colour per interior rank.  NULL skips an array. */
+int mcs_export_mesh(const mcs_handle* h, int32_t* facets, int32_t* elem_facets, int8_t* signs, int32_t* colour);
+/* elem_dofs [ne][n_A + n_p]: global index of every local dof (local order u_d(f,j) | u_o |
+ * uhat(f,m,j) | p), -1 on Dirichlet facets.  Host buffer. */
+int mcs_export_dofmap(const mcs_handle* h, int64_t* elem_dofs);
+/* CSR sparsity pattern of K (host).  rowptr [ndof+1]; col [rowptr[ndof]] ascending per
+ * row, or NULL to query rowptr only. */
+int mcs_export_pattern(const mcs_handle* h, int64_t* rowptr, int32_t* col);
+
+/* Static condensation (Sec. 4.2): per element A_T (FP64), then A^d_T, G_T = A_oo^{-1} A_od,
+ * A_oo^{-1} and the inverted facet blocks of the smoother in the preconditioner's
+ * precision.  Asynchronous; idempotent. */
+int mcs_condense(mcs_handle* h);
+
+/* Copies the packed lower triangle of A_T (FP64, [count][n_A(n_A+1)/2], row-major
+ * packing i(i+1)/2 + j, local order u_d | u_o | uhat, orientation signs applied) of
+ * elements T0 .. T0+count-1 to a host buffer.  Synchronous. */
+int mcs_copy_element_matrices(const mcs_handle* h, int64_t T0, int64_t count, double* AT_host);
+/* Copies A^d_T ([count][n_c][n_c]) and G_T ([count][n_bub][n_c]) as FP64 to host buffers;
+ * coupling dofs in facet-major order (facet f: nF facet moments then nhF tangential dofs). */
+int mcs_copy_schur(const mcs_handle* h, int64_t T0, int64_t count, double* Ad_host, double* G_host);
+
+/* Physical load quadrature points, device buffer xq [ne*nq_load][dim]. */
+int mcs_load_points(mcs_handle* h, double* xq);
+/* F = (f, phi^u) for f given at the load points (device fq [ne*nq_load][dim]); F device [ndof],
+ * zero outside the velocity block. */
+int mcs_load_vector(mcs_handle* h, const double* fq, double* F);
+/* F = M_u c: velocity mass matrix times the coefficient vector c (device [ndof]; only the
+ * velocity blocks u_d, u_o are read); used for random right-hand sides f = sum c_j phi_j. */
+int mcs_mass_velocity(mcs_handle* h, const double* c, double* F);
+
+/* y = K x (eq. femSPmat), FP64, device vectors [ndof]. */
+int mcs_apply(mcs_handle* h, const double* x, double* y);
+/* z = Khat^{-1} r (eq. mhatinvfactor applied with two Ahat^{-1}), device vectors [ndof];
+ * the pressure part of z is not mean-corrected. */
+int mcs_precond(mcs_handle* h, const double* r, double* z);
+/* Solves K x = F by preconditioned MinRes (FP64 recurrence; MCS_MIXED adds FP64
+ * iterative refinement around FP32-preconditioned cycles).  x: in = initial guess,
+ * out = solution with mean-zero pressure.  Device vectors.  Synchronises with the
+ * stream to read the convergence state.  info may be NULL.  Returns MCS_OK, or
+ * MCS_ERR_NOT_CONVERGED / MCS_ERR_BREAKDOWN (x then holds the last iterate). */
+int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info);
+/* Same as mcs_solve with HOST vectors F, x [ndof]: copies F and x in, solves, copies x out. */
+int mcs_solve_host(mcs_handle* h, const double* F_host, double* x_host, mcs_solve_info* info);
+
+/* Releases the handle and its device memory (synchronises its stream). */
+int mcs_destroy(mcs_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCS_H */

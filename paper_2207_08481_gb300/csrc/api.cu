@@ -1,0 +1,810 @@
+// C-ABI of libmcs: handle management, set-up, condensation and the Krylov driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/mcs.h"
+#include "kernels.h"
+#include "meshing.h"
+#include "reference.h"
+
+using namespace mcs;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+struct McsError : std::runtime_error {
+  int code;
+  McsError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    int code = (e == cudaErrorMemoryAllocation) ? MCS_ERR_OOM : MCS_ERR_CUDA;
+    throw McsError(code, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const McsError& e) {
+    g_err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return MCS_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return MCS_ERR_INVALID_ARG;
+  } catch (...) {
+    g_err = "unknown error";
+    return MCS_ERR_INVALID_ARG;
+  }
+}
+
+ElemSizes elem_sizes(const Sizes& s) {
+  ElemSizes e;
+  e.d = s.d; e.k = s.k; e.nk = s.nk; e.nF = s.nF; e.nFm1 = s.nFm1; e.n_u = s.n_u; e.n_A = s.n_A;
+  e.n_hat = s.n_hat; e.nhF = s.nhF; e.n_p = s.n_p; e.n_s0 = s.n_s0; e.n_raw = s.n_raw; e.n_con = s.n_con;
+  e.n_w = s.n_w; e.n_wskew = s.n_wskew; e.n_cc = s.n_cc; e.n_bub = s.n_bub; e.n_c = s.n_c; e.mF = s.mF;
+  return e;
+}
+
+}  // namespace
+
+struct PrecBundle {
+  // device storage of one precision
+  void *Ad = nullptr, *G = nullptr, *Aoi = nullptr, *Dinv = nullptr, *Eb = nullptr;
+  std::vector<void*> lev_val, lev_dl1, lev_pval, lev_rval;
+};
+
+struct mcs_handle {
+  int d = 0, k = 0;
+  double nu = 1.0;
+  mcs_options opt{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  HostMesh mesh;
+  RefTables ref;
+  Sizes sz{};
+  ElemSizes es{};
+  Layout L{};
+  double total_adet = 0;
+  int ncol = 0;
+  std::vector<int32_t> colour;          // per interior rank
+  std::vector<int64_t> colour_off;      // host offsets into colour_list
+  int nlev = 0;
+  std::vector<int> level_N;
+  int64_t np1 = 0;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  // device data
+  DevMesh dm{};
+  DevTables dt{};
+  double* AT = nullptr;
+  PrecData<float> pf{};
+  PrecData<double> pd{};
+  bool condensed = false;
+  // Krylov work
+  double *kv[10] = {nullptr};
+  double* scratch = nullptr;
+  MinresScalars* S = nullptr;
+  MinresScalars* S_host = nullptr;  // pinned
+  double* cond_scratch = nullptr;
+  int64_t cond_scratch_doubles = 0;
+
+  template <class T>
+  T* dalloc(int64_t n) {
+    if (n <= 0) n = 1;
+    void* p = nullptr;
+    cuda_check(cudaMalloc(&p, sizeof(T) * n), "cudaMalloc");
+    allocs.push_back(p);
+    bytes += (int64_t)sizeof(T) * n;
+    return (T*)p;
+  }
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    T* p = dalloc<T>((int64_t)v.size());
+    if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice), "upload");
+    return p;
+  }
+  ~mcs_handle() {
+    for (void* p : allocs) cudaFree(p);
+    if (S_host) cudaFreeHost(S_host);
+  }
+};
+
+namespace {
+
+void validate_options(const mcs_options& o) {
+  if (o.precision != MCS_FP64 && o.precision != MCS_MIXED) throw McsError(MCS_ERR_INVALID_ARG, "precision");
+  if (o.smooth_steps < 0 || o.smooth_steps > 16) throw McsError(MCS_ERR_INVALID_ARG, "smooth_steps");
+  if (o.gmg_smooth < 1 || o.gmg_smooth > 16) throw McsError(MCS_ERR_INVALID_ARG, "gmg_smooth");
+  if (!(o.rtol > 0) || o.maxit < 1) throw McsError(MCS_ERR_INVALID_ARG, "rtol/maxit");
+}
+
+template <class R>
+std::vector<R> cast_vec(const std::vector<double>& v) {
+  return std::vector<R>(v.begin(), v.end());
+}
+
+// dense inverse of an SPD matrix (Cholesky), host FP64
+std::vector<double> spd_inverse(const Csr& A) {
+  const int64_t n = A.nrows;
+  std::vector<double> M(n * n, 0.0);
+  for (int64_t r = 0; r < n; ++r)
+    for (int64_t t = A.rowptr[r]; t < A.rowptr[r + 1]; ++t) M[r * n + A.col[t]] = A.val[t];
+  // Cholesky M = L L^T
+  for (int64_t j = 0; j < n; ++j) {
+    double s = M[j * n + j];
+    for (int64_t p = 0; p < j; ++p) s -= M[j * n + p] * M[j * n + p];
+    if (!(s > 0)) throw McsError(MCS_ERR_INVALID_ARG, "coarse operator not SPD");
+    double l = std::sqrt(s);
+    M[j * n + j] = l;
+    for (int64_t i = j + 1; i < n; ++i) {
+      double v = M[i * n + j];
+      for (int64_t p = 0; p < j; ++p) v -= M[i * n + p] * M[j * n + p];
+      M[i * n + j] = v / l;
+    }
+  }
+  std::vector<double> Inv(n * n, 0.0), y(n);
+  for (int64_t c = 0; c < n; ++c) {
+    for (int64_t i = 0; i < n; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int64_t p = 0; p < i; ++p) v -= M[i * n + p] * y[p];
+      y[i] = v / M[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int64_t p = i + 1; p < n; ++p) v -= M[p * n + i] * Inv[p * n + c];
+      Inv[i * n + c] = v / M[i * n + i];
+    }
+  }
+  return Inv;
+}
+
+std::vector<int32_t> to_i32(const std::vector<int64_t>& v) {
+  std::vector<int32_t> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    if (v[i] > 0x7fffffff) throw McsError(MCS_ERR_UNSUPPORTED, "sparse matrix too large for int32 indices");
+    o[i] = (int32_t)v[i];
+  }
+  return o;
+}
+
+template <class R>
+void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, const std::vector<Csr>& Pr,
+                     const std::vector<Csr>& Rt, const std::vector<double>& coarse_inv,
+                     const std::vector<double>& Eb, const std::vector<int32_t>& fvr,
+                     const std::vector<int32_t>& vf_ptr, const std::vector<int32_t>& vf_idx,
+                     const std::vector<int32_t>& clist) {
+  const Sizes& s = h->sz;
+  const int64_t ne = h->mesh.ne, nint = h->mesh.nint;
+  P.Ad = h->dalloc<R>(ne * s.n_c * s.n_c);
+  P.G = h->dalloc<R>(ne * s.n_bub * s.n_c);
+  P.Aoi = h->dalloc<R>(ne * s.n_bub * s.n_bub);
+  P.Dinv = h->dalloc<R>(nint * s.mF * s.mF);
+  P.Eb = h->upload(cast_vec<R>(Eb));
+  P.fvr = h->upload(fvr);
+  P.vf_ptr = h->upload(vf_ptr);
+  P.vf_idx = h->upload(vf_idx);
+  P.nP1 = h->np1 / h->d;
+  P.colour_list = h->upload(clist);
+  P.colour_off = h->colour_off.data();
+  P.ncol = h->ncol;
+  P.smooth = h->opt.smooth_steps;
+  P.gmg_smooth = h->opt.gmg_smooth;
+  P.multiplicative = 1;
+  P.nlev = h->nlev;
+  for (int l = 0; l < h->nlev; ++l) {
+    GmgLevel& G = P.lev[l];
+    G.n = A[l].nrows;
+    G.rowptr = h->upload(to_i32(A[l].rowptr));
+    G.col = h->upload(A[l].col);
+    G.val = h->upload(cast_vec<R>(A[l].val));
+    std::vector<double> dl1(A[l].nrows, 0.0);
+    for (int64_t r = 0; r < A[l].nrows; ++r) {
+      double sabs = 0;
+      for (int64_t t = A[l].rowptr[r]; t < A[l].rowptr[r + 1]; ++t) sabs += std::fabs(A[l].val[t]);
+      dl1[r] = 1.0 / sabs;
+    }
+    G.dl1inv = h->upload(cast_vec<R>(dl1));
+    if (l > 0) {
+      G.prow = h->upload(to_i32(Pr[l].rowptr));
+      G.pcol = h->upload(Pr[l].col);
+      G.pval = h->upload(cast_vec<R>(Pr[l].val));
+      G.rrow = h->upload(to_i32(Rt[l].rowptr));
+      G.rcol = h->upload(Rt[l].col);
+      G.rval = h->upload(cast_vec<R>(Rt[l].val));
+    }
+    P.pb[l] = h->dalloc<R>(G.n);
+    P.px[l] = h->dalloc<R>(G.n);
+    P.pr[l] = h->dalloc<R>(G.n);
+    P.ptmp[l] = h->dalloc<R>(G.n);
+  }
+  P.coarse_inv = h->upload(coarse_inv);
+  const int64_t n = h->L.ndof;
+  P.b = h->dalloc<R>(n);
+  P.x = h->dalloc<R>(n);
+  P.t = h->dalloc<R>(n);
+  P.rr = h->dalloc<R>(n);
+  P.zz = h->dalloc<R>(n);
+  P.coarse_tmp = nullptr;
+}
+
+void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
+  const int d = h->d;
+  HostMesh& m = h->mesh;
+  h->ref = build_reference(d, h->k);
+  h->sz = h->ref.s;
+  if (h->sz.n_bub > 64) throw McsError(MCS_ERR_UNSUPPORTED, "more than 64 bubble functions per element");
+  h->es = elem_sizes(h->sz);
+  const Sizes& s = h->sz;
+  // layout
+  Layout& L = h->L;
+  L.ne = m.ne;
+  L.nint = m.nint;
+  L.n_dd = m.nint * s.nF;
+  L.n_oo = m.ne * s.n_bub;
+  L.n_hat = m.nint * s.nhF;
+  L.n_pres = m.ne * s.n_p;
+  L.off_o = L.n_dd;
+  L.off_h = L.n_dd + L.n_oo;
+  L.off_p = L.off_h + L.n_hat;
+  L.ndof = L.off_p + L.n_pres;
+  // |det J|
+  std::vector<double> adet(m.ne);
+  h->total_adet = 0;
+  for (int64_t T = 0; T < m.ne; ++T) {
+    const int32_t* e = &m.elems[T * (d + 1)];
+    double J[9];
+    for (int a = 0; a < d; ++a)
+      for (int i = 0; i < d; ++i) J[a * d + i] = m.coords[e[i + 1] * d + a] - m.coords[e[0] * d + a];
+    double det = (d == 2) ? J[0] * J[3] - J[1] * J[2]
+                          : J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                                J[2] * (J[3] * J[7] - J[4] * J[6]);
+    adet[T] = std::fabs(det);
+    h->total_adet += adet[T];
+    if (adet[T] == 0.0) throw McsError(MCS_ERR_INVALID_ARG, "degenerate element");
+  }
+  // interior facet -> elements / local index
+  std::vector<int32_t> fel(m.nint * 2), floc(m.nint * 2);
+  for (int64_t r = 0; r < m.nint; ++r) {
+    int32_t F = m.int_facets[r];
+    fel[r * 2] = m.facet_elems[F * 2];
+    fel[r * 2 + 1] = m.facet_elems[F * 2 + 1];
+    floc[r * 2] = m.int_local[r * 2];
+    floc[r * 2 + 1] = m.int_local[r * 2 + 1];
+  }
+  DevMesh& dm = h->dm;
+  dm.d = d;
+  dm.ne = m.ne;
+  dm.nint = m.nint;
+  dm.coords = h->upload(m.coords);
+  dm.elems = h->upload(m.elems);
+  dm.elem_rank = h->upload(m.elem_rank);
+  dm.signs = h->upload(m.signs);
+  dm.adet = h->upload(adet);
+  dm.fel = h->upload(fel);
+  dm.floc = h->upload(floc);
+  // tables
+  DevTables& dt = h->dt;
+  const RefTables& R = h->ref;
+  dt.B0 = h->upload(R.B0);
+  dt.Rf = h->upload(R.Rf);
+  dt.Bh = h->upload(R.Bh);
+  dt.Ccon = h->upload(R.Ccon);
+  dt.Adiv = h->upload(R.Adiv);
+  dt.nhat = h->upload(R.nhat);
+  dt.Bp = h->upload(R.Bp);
+  dt.Mu = h->upload(R.Mu);
+  dt.phi_load = h->upload(R.phi_load);
+  dt.xq_load = h->upload(R.xq_load);
+  dt.wq_load = h->upload(R.wq_load);
+  dt.nq_load = R.nq_load;
+  // colouring
+  h->colour = colour_facets(m, &h->ncol);
+  std::vector<int32_t> clist;
+  h->colour_off.assign(h->ncol + 1, 0);
+  for (int c = 0; c < h->ncol; ++c) {
+    h->colour_off[c] = (int64_t)clist.size();
+    for (int64_t r = 0; r < m.nint; ++r)
+      if (h->colour[r] == c) clist.push_back((int32_t)r);
+  }
+  h->colour_off[h->ncol] = (int64_t)clist.size();
+  // conforming space and multigrid
+  std::vector<P1Space> sp;
+  std::vector<Csr> A, Pr, Rt;
+  for (size_t l = 0; l < levels.size(); ++l) {
+    sp.push_back(p1_space(levels[l]));
+    A.push_back(abar_matrix(levels[l], sp[l], h->nu));
+  }
+  Pr.resize(levels.size());
+  Rt.resize(levels.size());
+  for (size_t l = 1; l < levels.size(); ++l) {
+    Pr[l] = prolongation(d, h->level_N[l - 1], sp[l - 1], sp[l]);
+    Rt[l] = transpose(Pr[l]);
+  }
+  h->np1 = sp.back().n * d;
+  if (A[0].nrows > 6000) throw McsError(MCS_ERR_UNSUPPORTED, "coarsest multigrid level too large for a dense solve");
+  std::vector<double> cinv = spd_inverse(A[0]);
+  // E^d structures
+  std::vector<double> Eb = embedding_blocks(m, R);
+  const P1Space& p1 = sp.back();
+  std::vector<int32_t> fvr(m.nint * d);
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> inc(p1.n);
+  for (int64_t r = 0; r < m.nint; ++r) {
+    int32_t F = m.int_facets[r];
+    for (int w = 0; w < d; ++w) {
+      int32_t vr = p1.vrank[m.facets[F * d + w]];
+      fvr[r * d + w] = vr;
+      if (vr >= 0) inc[vr].push_back({(int32_t)r, w});
+    }
+  }
+  std::vector<int32_t> vf_ptr(p1.n + 1, 0), vf_idx;
+  for (int64_t v = 0; v < p1.n; ++v) {
+    for (auto& pr : inc[v]) {
+      vf_idx.push_back(pr.first);
+      vf_idx.push_back(pr.second);
+    }
+    vf_ptr[v + 1] = (int32_t)(vf_idx.size() / 2);
+  }
+  if (h->opt.precision == MCS_MIXED)
+    build_precision<float>(h, h->pf, A, Pr, Rt, cinv, Eb, fvr, vf_ptr, vf_idx, clist);
+  else
+    build_precision<double>(h, h->pd, A, Pr, Rt, cinv, Eb, fvr, vf_ptr, vf_idx, clist);
+  // condensed operator and Krylov work
+  h->AT = h->dalloc<double>(m.ne * (int64_t)s.n_A * (s.n_A + 1) / 2);
+  for (int i = 0; i < 10; ++i) h->kv[i] = h->dalloc<double>(L.ndof);
+  h->scratch = h->dalloc<double>(4096);
+  cuda_check(cudaMemset(h->scratch, 0, sizeof(double) * 4096), "memset");
+  h->S = h->dalloc<MinresScalars>(1);
+  cuda_check(cudaMallocHost(&h->S_host, sizeof(MinresScalars)), "cudaMallocHost");
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  h->cond_scratch_doubles = condense_scratch_doubles(h->es, nsm);
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (h->cond_scratch_doubles / ((int64_t)nsm * 8) * 8 > maxsm)
+    h->cond_scratch = h->dalloc<double>(h->cond_scratch_doubles);
+  cuda_check(cudaDeviceSynchronize(), "setup");
+}
+
+mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* stream) {
+  if (dim < 2 || dim > 3) throw McsError(MCS_ERR_UNSUPPORTED, "dim must be 2 or 3");
+  if (k < 2 || k > 6) throw McsError(MCS_ERR_UNSUPPORTED, "k must be in 2..6");
+  if (!(nu > 0)) throw McsError(MCS_ERR_INVALID_ARG, "nu must be positive");
+  auto h = std::make_unique<mcs_handle>();
+  h->d = dim;
+  h->k = k;
+  h->nu = nu;
+  if (opt) h->opt = *opt;
+  else mcs_default_options(&h->opt);
+  validate_options(h->opt);
+  h->stream = (cudaStream_t)stream;
+  cuda_check(cudaGetDevice(&h->device), "cudaGetDevice");
+  return h.release();
+}
+
+}  // namespace
+
+extern "C" {
+
+int mcs_version(void) { return 100; }
+
+const char* mcs_last_error(void) { return g_err.c_str(); }
+
+int mcs_default_options(mcs_options* o) {
+  if (!o) return MCS_ERR_INVALID_ARG;
+  o->precision = MCS_MIXED;
+  o->smooth_steps = 2;
+  o->gmg_levels = -1;
+  o->gmg_smooth = 2;
+  o->rtol = 1e-8;
+  o->maxit = 1000;
+  o->max_refine = 8;
+  o->inner_rtol = 1e-5;
+  return MCS_OK;
+}
+
+int mcs_setup_structured(int dim, int N, int k, double nu, const mcs_options* opt, void* stream,
+                         mcs_handle** out) {
+  return guarded([&]() -> int {
+    if (!out) throw McsError(MCS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > 4096) throw McsError(MCS_ERR_INVALID_ARG, "N out of range");
+    std::unique_ptr<mcs_handle> h(new_handle(dim, k, nu, opt, stream));
+    int levels = h->opt.gmg_levels;
+    if (levels < 0) {
+      const int target = (dim == 2) ? 16 : 4;
+      levels = 1;
+      int n = N;
+      while (n > target && n % 2 == 0) {
+        n /= 2;
+        ++levels;
+      }
+    }
+    if (levels < 1 || levels > 12) throw McsError(MCS_ERR_INVALID_ARG, "gmg_levels out of range");
+    if (N % (1 << (levels - 1)) != 0) throw McsError(MCS_ERR_INVALID_ARG, "N not divisible by 2^(levels-1)");
+    h->nlev = levels;
+    std::vector<HostMesh> lv;
+    for (int l = 0; l < levels; ++l) {
+      int Nl = N >> (levels - 1 - l);
+      h->level_N.push_back(Nl);
+      lv.push_back(l + 1 == levels ? structured_mesh(dim, N) : structured_mesh(dim, Nl));
+    }
+    h->mesh = lv.back();
+    finish_setup(h.get(), lv);
+    *out = h.release();
+    return MCS_OK;
+  });
+}
+
+int mcs_setup_mesh(int dim, int64_t nv, const double* coords, int64_t ne, const int32_t* elems, int k,
+                   double nu, const mcs_options* opt, void* stream, mcs_handle** out) {
+  return guarded([&]() -> int {
+    if (!out || !coords || !elems || nv < 1 || ne < 1) throw McsError(MCS_ERR_INVALID_ARG, "bad mesh arguments");
+    *out = nullptr;
+    std::unique_ptr<mcs_handle> h(new_handle(dim, k, nu, opt, stream));
+    HostMesh m;
+    m.d = dim;
+    m.nv = nv;
+    m.ne = ne;
+    m.coords.assign(coords, coords + nv * dim);
+    m.elems.assign(elems, elems + ne * (dim + 1));
+    for (int64_t T = 0; T < ne; ++T)
+      for (int v = 0; v <= dim; ++v) {
+        int32_t id = m.elems[T * (dim + 1) + v];
+        if (id < 0 || id >= nv) throw McsError(MCS_ERR_INVALID_ARG, "vertex id out of range");
+        if (v > 0 && id <= m.elems[T * (dim + 1) + v - 1])
+          throw McsError(MCS_ERR_INVALID_ARG, "element vertex ids must be ascending");
+      }
+    build_facets(m);
+    h->nlev = 1;
+    h->level_N.push_back(0);
+    std::vector<HostMesh> lv{m};
+    h->mesh = m;
+    finish_setup(h.get(), lv);
+    *out = h.release();
+    return MCS_OK;
+  });
+}
+
+int mcs_sizes(const mcs_handle* h, mcs_sizes_t* s) {
+  return guarded([&]() -> int {
+    if (!h || !s) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    const Layout& L = h->L;
+    s->ndof = L.ndof; s->n_dd = L.n_dd; s->n_oo = L.n_oo; s->n_hat = L.n_hat; s->n_pres = L.n_pres;
+    s->off_o = L.off_o; s->off_h = L.off_h; s->off_p = L.off_p;
+    s->ne = h->mesh.ne; s->nint = h->mesh.nint; s->nfacets = h->mesh.nf; s->nvertices = h->mesh.nv;
+    s->np1 = h->np1;
+    s->dim = h->d; s->k = h->k; s->nF = h->sz.nF; s->n_bub = h->sz.n_bub; s->nhF = h->sz.nhF;
+    s->n_p = h->sz.n_p; s->n_A = h->sz.n_A; s->n_c = h->sz.n_c; s->mF = h->sz.mF;
+    s->ncolours = h->ncol; s->gmg_levels = h->nlev;
+    s->nq_load = h->ref.nq_load;
+    s->bytes_resident = h->bytes;
+    return MCS_OK;
+  });
+}
+
+int mcs_export_mesh(const mcs_handle* h, int32_t* facets, int32_t* elem_facets, int8_t* signs, int32_t* colour) {
+  return guarded([&]() -> int {
+    if (!h) throw McsError(MCS_ERR_INVALID_ARG, "NULL handle");
+    const HostMesh& m = h->mesh;
+    if (facets) std::copy(m.facets.begin(), m.facets.end(), facets);
+    if (elem_facets) std::copy(m.elem_facets.begin(), m.elem_facets.end(), elem_facets);
+    if (signs) std::copy(m.signs.begin(), m.signs.end(), signs);
+    if (colour) std::copy(h->colour.begin(), h->colour.end(), colour);
+    return MCS_OK;
+  });
+}
+
+int mcs_export_dofmap(const mcs_handle* h, int64_t* out) {
+  return guarded([&]() -> int {
+    if (!h || !out) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    const Sizes& s = h->sz;
+    const Layout& L = h->L;
+    const int d = h->d;
+    const int nloc = s.n_A + s.n_p;
+    for (int64_t T = 0; T < h->mesh.ne; ++T) {
+      int64_t* o = out + T * nloc;
+      const int32_t* er = &h->mesh.elem_rank[T * (d + 1)];
+      for (int i = 0; i < s.n_A; ++i) {
+        const int nfd = (d + 1) * s.nF;
+        int64_t g;
+        if (i < nfd) {
+          int f = i / s.nF;
+          g = er[f] < 0 ? -1 : (int64_t)er[f] * s.nF + (i - f * s.nF);
+        } else if (i < s.n_u) {
+          g = L.off_o + T * s.n_bub + (i - nfd);
+        } else {
+          int q = i - s.n_u, f = q / s.nhF;
+          g = er[f] < 0 ? -1 : L.off_h + (int64_t)er[f] * s.nhF + (q - f * s.nhF);
+        }
+        o[i] = g;
+      }
+      for (int j = 0; j < s.n_p; ++j) o[s.n_A + j] = L.off_p + T * s.n_p + j;
+    }
+    return MCS_OK;
+  });
+}
+
+int mcs_export_pattern(const mcs_handle* h, int64_t* rowptr, int32_t* col) {
+  return guarded([&]() -> int {
+    if (!h || !rowptr) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    const Sizes& s = h->sz;
+    const int nloc = s.n_A + s.n_p;
+    std::vector<int64_t> dm(h->mesh.ne * nloc);
+    mcs_export_dofmap(h, dm.data());
+    const int64_t n = h->L.ndof;
+    // rows coupled through elements: velocity-velocity (A), velocity-pressure (B^T, B);
+    // p-p block is zero
+    std::vector<std::vector<int32_t>> rows(n);
+    for (int64_t T = 0; T < h->mesh.ne; ++T) {
+      const int64_t* o = &dm[T * nloc];
+      for (int i = 0; i < nloc; ++i) {
+        if (o[i] < 0) continue;
+        for (int j = 0; j < nloc; ++j) {
+          if (o[j] < 0) continue;
+          bool ip = i >= s.n_A, jp = j >= s.n_A;
+          if (ip && jp) continue;
+          if ((ip && j >= s.n_u) || (jp && i >= s.n_u)) continue;  // p couples to u only
+          rows[o[i]].push_back((int32_t)o[j]);
+        }
+      }
+    }
+    rowptr[0] = 0;
+    for (int64_t r = 0; r < n; ++r) {
+      auto& v = rows[r];
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+      rowptr[r + 1] = rowptr[r] + (int64_t)v.size();
+      if (col) std::copy(v.begin(), v.end(), col + rowptr[r]);
+    }
+    return MCS_OK;
+  });
+}
+
+int mcs_condense(mcs_handle* h) {
+  return guarded([&]() -> int {
+    if (!h) throw McsError(MCS_ERR_INVALID_ARG, "NULL handle");
+    if (h->opt.precision == MCS_MIXED) {
+      cuda_check(launch_condense<float>(h->es, h->dt, h->dm, h->nu, h->AT, (float*)h->pf.Ad, (float*)h->pf.G,
+                                        (float*)h->pf.Aoi, h->cond_scratch, h->cond_scratch_doubles, h->stream),
+                 "condense");
+      cuda_check(launch_facet_blocks<float>(h->es, h->dm, h->pf.Ad, (float*)h->pf.Dinv, h->stream), "facet blocks");
+    } else {
+      cuda_check(launch_condense<double>(h->es, h->dt, h->dm, h->nu, h->AT, (double*)h->pd.Ad, (double*)h->pd.G,
+                                         (double*)h->pd.Aoi, h->cond_scratch, h->cond_scratch_doubles, h->stream),
+                 "condense");
+      cuda_check(launch_facet_blocks<double>(h->es, h->dm, h->pd.Ad, (double*)h->pd.Dinv, h->stream),
+                 "facet blocks");
+    }
+    h->condensed = true;
+    return MCS_OK;
+  });
+}
+
+int mcs_copy_element_matrices(const mcs_handle* h, int64_t T0, int64_t count, double* out) {
+  return guarded([&]() -> int {
+    if (!h || !out || T0 < 0 || count < 0 || T0 + count > h->mesh.ne) throw McsError(MCS_ERR_INVALID_ARG, "range");
+    const int64_t np = (int64_t)h->sz.n_A * (h->sz.n_A + 1) / 2;
+    cuda_check(cudaStreamSynchronize(h->stream), "sync");
+    cuda_check(cudaMemcpy(out, h->AT + T0 * np, sizeof(double) * np * count, cudaMemcpyDeviceToHost), "copy");
+    return MCS_OK;
+  });
+}
+
+int mcs_copy_schur(const mcs_handle* h, int64_t T0, int64_t count, double* Ad_host, double* G_host) {
+  return guarded([&]() -> int {
+    if (!h || T0 < 0 || count < 0 || T0 + count > h->mesh.ne) throw McsError(MCS_ERR_INVALID_ARG, "range");
+    const Sizes& s = h->sz;
+    cuda_check(cudaStreamSynchronize(h->stream), "sync");
+    auto fetch = [&](const void* src, int64_t per, double* dst) {
+      if (!dst) return;
+      if (h->opt.precision == MCS_MIXED) {
+        std::vector<float> tmp(per * count);
+        cuda_check(cudaMemcpy(tmp.data(), (const float*)src + T0 * per, sizeof(float) * per * count,
+                              cudaMemcpyDeviceToHost), "copy");
+        for (int64_t i = 0; i < per * count; ++i) dst[i] = tmp[i];
+      } else {
+        cuda_check(cudaMemcpy(dst, (const double*)src + T0 * per, sizeof(double) * per * count,
+                              cudaMemcpyDeviceToHost), "copy");
+      }
+    };
+    const void* Ad = h->opt.precision == MCS_MIXED ? (const void*)h->pf.Ad : (const void*)h->pd.Ad;
+    const void* G = h->opt.precision == MCS_MIXED ? (const void*)h->pf.G : (const void*)h->pd.G;
+    fetch(Ad, (int64_t)s.n_c * s.n_c, Ad_host);
+    fetch(G, (int64_t)s.n_bub * s.n_c, G_host);
+    return MCS_OK;
+  });
+}
+
+int mcs_load_points(mcs_handle* h, double* xq) {
+  return guarded([&]() -> int {
+    if (!h || !xq) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    cuda_check(launch_load_points(h->es, h->dt, h->dm, xq, h->stream), "load points");
+    return MCS_OK;
+  });
+}
+
+int mcs_load_vector(mcs_handle* h, const double* fq, double* F) {
+  return guarded([&]() -> int {
+    if (!h || !fq || !F) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    cuda_check(launch_load(h->es, h->dt, h->dm, h->L, fq, F, h->stream), "load vector");
+    return MCS_OK;
+  });
+}
+
+int mcs_mass_velocity(mcs_handle* h, const double* c, double* F) {
+  return guarded([&]() -> int {
+    if (!h || !c || !F) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    cuda_check(launch_mass_u(h->es, h->dt, h->dm, h->L, c, F, h->stream), "mass");
+    return MCS_OK;
+  });
+}
+
+int mcs_apply(mcs_handle* h, const double* x, double* y) {
+  return guarded([&]() -> int {
+    if (!h || !x || !y) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    if (!h->condensed) throw McsError(MCS_ERR_INVALID_ARG, "mcs_condense has not been called");
+    cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, x, y, nullptr, h->stream), "apply");
+    return MCS_OK;
+  });
+}
+
+static void precond_any(mcs_handle* h, const double* r, double* z, const int* stop) {
+  cudaError_t e = (h->opt.precision == MCS_MIXED)
+                      ? launch_precond<float>(h->es, h->dt, h->dm, h->L, h->nu, h->pf, r, z, stop, h->stream)
+                      : launch_precond<double>(h->es, h->dt, h->dm, h->L, h->nu, h->pd, r, z, stop, h->stream);
+  cuda_check(e, "precond");
+}
+
+int mcs_precond(mcs_handle* h, const double* r, double* z) {
+  return guarded([&]() -> int {
+    if (!h || !r || !z) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    if (!h->condensed) throw McsError(MCS_ERR_INVALID_ARG, "mcs_condense has not been called");
+    precond_any(h, r, z, nullptr);
+    return MCS_OK;
+  });
+}
+
+namespace {
+
+// One MinRes cycle on K d = rhs from d = 0, accumulating d into x_acc.
+// g_first: preconditioned norm of the first cycle's residual (< 0 before the first cycle).
+void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double floor_rtol, int maxit, double g_first) {
+  const int64_t n = h->L.ndof;
+  cudaStream_t st = h->stream;
+  double *v_old = h->kv[0], *v = h->kv[1], *z = h->kv[2], *zn = h->kv[3];
+  double *w_old = h->kv[4], *w = h->kv[5], *Kz = h->kv[6];
+  MinresScalars* S = h->S;
+  MinresScalars init{};
+  init.rtol = h->opt.rtol;
+  init.floor_rtol = floor_rtol;
+  init.g_first = g_first;
+  init.maxit = maxit;
+  cuda_check(cudaMemcpyAsync(S, &init, sizeof(MinresScalars), cudaMemcpyHostToDevice, st), "init S");
+  cuda_check(cudaMemcpyAsync(v, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  cuda_check(cudaMemsetAsync(v_old, 0, sizeof(double) * n, st), "memset");
+  cuda_check(cudaMemsetAsync(w, 0, sizeof(double) * n, st), "memset");
+  cuda_check(cudaMemsetAsync(w_old, 0, sizeof(double) * n, st), "memset");
+  precond_any(h, v, z, nullptr);
+  cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, z, h->scratch, h->total_adet, nullptr, st), "mean");
+  cuda_check(launch_dot(z, v, n, h->scratch, &S->dot1, nullptr, st), "dot");
+  cuda_check(launch_minres_init(S, st), "init");
+  const int* stop = &S->stop;
+  const int check_every = 8;
+  while (true) {
+    cuda_check(cudaMemcpyAsync(h->S_host, S, sizeof(MinresScalars), cudaMemcpyDeviceToHost, st), "read S");
+    cuda_check(cudaStreamSynchronize(st), "sync");
+    if (h->S_host->stop) break;
+    for (int q = 0; q < check_every; ++q) {
+      cuda_check(launch_minres_scale(S, n, z, z, st), "scale");
+      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, z, Kz, stop, st), "apply");
+      cuda_check(launch_dot(Kz, z, n, h->scratch, &S->delta, stop, st), "dot");
+      cuda_check(launch_minres_lanczos(S, n, z, Kz, v, v_old, st), "lanczos");
+      precond_any(h, v_old, zn, stop);
+      cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, zn, h->scratch, h->total_adet, stop, st), "mean");
+      cuda_check(launch_dot(zn, v_old, n, h->scratch, &S->dot1, stop, st), "dot");
+      cuda_check(launch_minres_scalars(S, st), "scalars");
+      cuda_check(launch_minres_update(S, n, z, w, w_old, x_acc, st), "update");
+      std::swap(v_old, v);
+      std::swap(w_old, w);
+      std::swap(z, zn);
+    }
+  }
+}
+
+}  // namespace
+
+int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
+  return guarded([&]() -> int {
+    if (!h || !F || !x) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    if (!h->condensed) throw McsError(MCS_ERR_INVALID_ARG, "mcs_condense has not been called");
+    const int64_t n = h->L.ndof;
+    cudaStream_t st = h->stream;
+    double* r = h->kv[7];
+    const bool mixed = h->opt.precision == MCS_MIXED;
+    // FP64 form: one cycle to rtol plus a check of the true residual.  Mixed form: FP64
+    // iterative refinement, each cycle asked for at least inner_rtol reduction.
+    const int max_cycles = mixed ? std::max(2, h->opt.max_refine + 1) : 2;
+    const double floor_rtol = mixed ? h->opt.inner_rtol : 0.0;
+    int total_it = 0, cycles = 0, status = MCS_ERR_NOT_CONVERGED;
+    double g_first = -1.0, g_now = 0.0;
+    while (cycles < max_cycles) {
+      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, x, r, nullptr, st), "apply");
+      cuda_check(launch_axpby(n, 1.0, F, -1.0, r, st), "axpby");
+      minres_cycle(h, r, x, floor_rtol, std::max(1, h->opt.maxit - total_it), g_first);
+      const MinresScalars& Sh = *h->S_host;
+      g_first = Sh.g_first;
+      g_now = Sh.res0;
+      total_it += Sh.it;
+      ++cycles;
+      if (Sh.status == MCS_ERR_BREAKDOWN) {
+        status = MCS_ERR_BREAKDOWN;
+        break;
+      }
+      if (Sh.it == 0 && (g_now <= h->opt.rtol * g_first || g_now == 0.0)) {
+        status = MCS_OK;  // the recomputed residual meets the tolerance
+        break;
+      }
+      if (total_it >= h->opt.maxit) break;
+    }
+    cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, x, h->scratch, h->total_adet, nullptr, st), "mean");
+    if (info) {
+      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, x, r, nullptr, st), "apply");
+      cuda_check(launch_axpby(n, 1.0, F, -1.0, r, st), "axpby");
+      double* res = h->scratch + 3000;
+      cuda_check(launch_dot(r, r, n, h->scratch, res, nullptr, st), "dot");
+      cuda_check(launch_dot(F, F, n, h->scratch, res + 1, nullptr, st), "dot");
+      double hv[2];
+      cuda_check(cudaMemcpyAsync(hv, res, sizeof(hv), cudaMemcpyDeviceToHost, st), "copy");
+      cuda_check(cudaStreamSynchronize(st), "sync");
+      info->iterations = total_it;
+      info->refinements = cycles;
+      info->status = status;
+      info->rel_res_true = hv[1] > 0 ? std::sqrt(hv[0] / hv[1]) : 0.0;
+      info->rel_res_precond = g_first > 0 ? g_now / g_first : 0.0;
+    }
+    if (status != MCS_OK) g_err = status == MCS_ERR_BREAKDOWN ? "Krylov breakdown" : "not converged";
+    return status;
+  });
+}
+
+int mcs_solve_host(mcs_handle* h, const double* F_host, double* x_host, mcs_solve_info* info) {
+  return guarded([&]() -> int {
+    if (!h || !F_host || !x_host) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    const int64_t n = h->L.ndof;
+    double* F = h->kv[8];
+    double* x = h->kv[9];
+    cuda_check(cudaMemcpyAsync(F, F_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream), "h2d");
+    cuda_check(cudaMemcpyAsync(x, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream), "h2d");
+    int rc = mcs_solve(h, F, x, info);
+    cuda_check(cudaMemcpyAsync(x_host, x, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream), "d2h");
+    cuda_check(cudaStreamSynchronize(h->stream), "sync");
+    return rc;
+  });
+}
+
+int mcs_destroy(mcs_handle* h) {
+  return guarded([&]() -> int {
+    if (!h) return MCS_OK;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+    return MCS_OK;
+  });
+}
+
+}  // extern "C"

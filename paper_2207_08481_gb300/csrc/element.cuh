@@ -1,0 +1,437 @@
+// Element-level static condensation of the MCS method (host/device code).
+//
+// For one simplex T with vertex coordinates X (ascending global ids) this forms
+//
+//   A_T = A^div_T - B_sigma,T M_T^{-1} B_sigma,T^T          (arXiv 2207.08481 Sec. 4.2)
+//
+// where M_T is the local saddle-point block over Sigma_h(T) x W_h(T) of
+// eq. (bigfemSPmat).  Sigma_h(T) is represented in the raw trace-free basis
+// J^{-T}(psi_i E_s)J^T; its nt conditions (eq. fes_Sigma) and the rotation
+// constraints (B_omega sigma = 0) are eliminated together by Lagrange
+// multipliers:  with M_raw = (|det J|/nu) (I (x) g), g_st = tr(E_s^T G^{-1} E_t G),
+// G = J^T J, and all constraints C,
+//
+//   -(M^{-1})_{sigma sigma} = M_raw^{-1} - M_raw^{-1} C^T (C M_raw^{-1} C^T)^{-1} C M_raw^{-1},
+//
+// so A_T = A^div + Bt Bt^T - Z^T Z with Bt = B_raw (I (x) L) sqrt(nu/|det J|),
+// Ct = C (I (x) L), g^{-1} = L L^T, Sc = Ct Ct^T = Lc Lc^T, Z = Lc^{-1} Ct Bt^T.
+//
+// The geometric dependence of B_sigma (raw basis, u by the |det J| Piola map):
+//   B_u[i,j]  = B0[i,j] - sum_{f,a} w_{f,a} Rf[f,a][i,j],  w_{f,a} = (G^{-1} n_f)_a / (n_f^T G^{-1} n_f)
+//   B_uh[i,j] = |det J| Bh[i,j]
+//   B_omega   = |det J| (h (x) I_{P^{k-1}}),  h_rs = K_r : (J^{-T} E_s J^T)
+//   A^div     = nu / (d |det J|) Adiv_ref.
+//
+// All routines are written for `nl` cooperating lanes (a warp on the device, a
+// single lane on the host); `sync()` separates phases.
+#pragma once
+#include <cmath>
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
+namespace mcs {
+
+struct ElemSizes {
+  int d, k, nk, nF, nFm1, n_u, n_A, n_hat, nhF, n_p, n_s0, n_raw, n_con, n_w, n_wskew, n_cc;
+  int n_bub, n_c, mF;
+};
+
+struct ElemTables {
+  const double* B0;    // [n_u][n_raw]
+  const double* Rf;    // [d+1][d][nF][n_raw]
+  const double* Bh;    // [n_hat][n_raw]
+  const double* Ccon;  // [n_con][n_raw]
+  const double* Adiv;  // [n_u][n_u]
+  const double* nhat;  // [d+1][d]
+};
+
+// workspace layout (doubles), per element
+struct ElemWork {
+  double* geo;   // 128 scalars: L (8x8), h (3x8), w (4x3), adet
+  double* Bt;    // [n_A][n_raw]
+  double* Ct;    // [n_cc][n_raw]
+  double* V;     // [n_cc][n_A]
+  double* Sc;    // [n_cc][n_cc]
+  double* A;     // [n_A][n_A]
+};
+
+__host__ __device__ inline int elem_work_doubles(const ElemSizes& s) {
+  return 128 + s.n_A * s.n_raw + s.n_cc * s.n_raw + s.n_cc * s.n_A + s.n_cc * s.n_cc + s.n_A * s.n_A;
+}
+
+__host__ __device__ inline ElemWork elem_work_carve(const ElemSizes& s, double* base) {
+  ElemWork w;
+  w.geo = base;
+  w.Bt = base + 128;
+  w.Ct = w.Bt + s.n_A * s.n_raw;
+  w.V = w.Ct + s.n_cc * s.n_raw;
+  w.Sc = w.V + s.n_cc * s.n_A;
+  w.A = w.Sc + s.n_cc * s.n_cc;
+  return w;
+}
+
+// trace-free unit E_s entry (a, b) (same order as the host tables)
+__host__ __device__ inline double tf_unit(int d, int s, int a, int b) {
+  int noff = d * (d - 1);
+  if (s < noff) {
+    int cnt = 0;
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j)
+        if (i != j) {
+          if (cnt == s) return (a == i && b == j) ? 1.0 : 0.0;
+          ++cnt;
+        }
+    return 0.0;
+  }
+  int t = s - noff;
+  if (a != b) return 0.0;
+  if (a == t) return 1.0;
+  if (a == t + 1) return -1.0;
+  return 0.0;
+}
+
+// skew unit K_r = e_b e_a^T - e_a e_b^T for the r-th pair a < b: entry (i, j)
+__host__ __device__ inline double skew_unit(int d, int r, int i, int j) {
+  int cnt = 0;
+  for (int a = 0; a < d; ++a)
+    for (int b = a + 1; b < d; ++b) {
+      if (cnt == r) {
+        if (i == b && j == a) return 1.0;
+        if (i == a && j == b) return -1.0;
+        return 0.0;
+      }
+      ++cnt;
+    }
+  return 0.0;
+}
+
+__host__ __device__ inline void small_inverse(int n, double* A, double* Inv) {
+  // Gauss-Jordan with partial pivoting on an n x n (n <= 8) matrix; A is destroyed.
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Inv[i * n + j] = (i == j) ? 1.0 : 0.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r * n + c]) > fabs(A[p * n + c])) p = r;
+    if (p != c)
+      for (int j = 0; j < n; ++j) {
+        double t = A[c * n + j]; A[c * n + j] = A[p * n + j]; A[p * n + j] = t;
+        t = Inv[c * n + j]; Inv[c * n + j] = Inv[p * n + j]; Inv[p * n + j] = t;
+      }
+    double iv = 1.0 / A[c * n + c];
+    for (int j = 0; j < n; ++j) { A[c * n + j] *= iv; Inv[c * n + j] *= iv; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = A[r * n + c];
+      for (int j = 0; j < n; ++j) { A[r * n + j] -= f * A[c * n + j]; Inv[r * n + j] -= f * Inv[c * n + j]; }
+    }
+  }
+}
+
+// Geometric factors of one element (single lane).
+// geo: [0..63] L (n_s0 x n_s0, lower, g^{-1} = L L^T), [64..87] h (n_wskew x n_s0),
+//      [88..99] w (d+1 x d), [100] |det J|, [101] det J
+__host__ __device__ inline void elem_geometry(const ElemSizes& s, const double* X, const double* nhat, double* geo) {
+  const int d = s.d, ns0 = s.n_s0;
+  double J[9], Ji[9], G[9], Gi[9];
+  for (int a = 0; a < d; ++a)
+    for (int i = 0; i < d; ++i) J[a * d + i] = X[(i + 1) * d + a] - X[a];  // column i = x_{i+1} - x_0
+  double det;
+  if (d == 2) {
+    det = J[0] * J[3] - J[1] * J[2];
+    Ji[0] = J[3] / det; Ji[1] = -J[1] / det; Ji[2] = -J[2] / det; Ji[3] = J[0] / det;
+  } else {
+    det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+    Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+    Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+    Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+    Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+    Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+    Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+  }
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      double g = 0, gi = 0;
+      for (int c = 0; c < d; ++c) {
+        g += J[c * d + a] * J[c * d + b];
+        gi += Ji[a * d + c] * Ji[b * d + c];
+      }
+      G[a * d + b] = g;
+      Gi[a * d + b] = gi;
+    }
+  // g_st = tr(E_s^T Gi E_t G) = sum_{a,b,c,e} E_s[a,b] Gi[a,c] E_t[c,e] G[e,b]
+  double gm[64], gmc[64], ginv[64];
+  for (int s1 = 0; s1 < ns0; ++s1)
+    for (int t = 0; t < ns0; ++t) {
+      double v = 0;
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+          double es = tf_unit(d, s1, a, b);
+          if (es == 0.0) continue;
+          for (int c = 0; c < d; ++c)
+            for (int e = 0; e < d; ++e) {
+              double et = tf_unit(d, t, c, e);
+              if (et == 0.0) continue;
+              v += es * Gi[a * d + c] * et * G[e * d + b];
+            }
+        }
+      gm[s1 * ns0 + t] = v;
+    }
+  for (int i = 0; i < ns0 * ns0; ++i) gmc[i] = gm[i];
+  small_inverse(ns0, gmc, ginv);
+  // symmetrise and Cholesky g^{-1} = L L^T
+  double* L = geo;
+  for (int i = 0; i < 64; ++i) L[i] = 0.0;
+  for (int j = 0; j < ns0; ++j) {
+    double sdiag = 0.5 * (ginv[j * ns0 + j] + ginv[j * ns0 + j]);
+    for (int p = 0; p < j; ++p) sdiag -= L[j * ns0 + p] * L[j * ns0 + p];
+    double ljj = sqrt(sdiag);
+    L[j * ns0 + j] = ljj;
+    for (int i = j + 1; i < ns0; ++i) {
+      double v = 0.5 * (ginv[i * ns0 + j] + ginv[j * ns0 + i]);
+      for (int p = 0; p < j; ++p) v -= L[i * ns0 + p] * L[j * ns0 + p];
+      L[i * ns0 + j] = v / ljj;
+    }
+  }
+  // h_rs = K_r : (J^{-T} E_s J^T) = sum_{ij} K[i,j] (J^{-T} E_s J^T)[i,j]
+  double* h = geo + 64;
+  for (int r = 0; r < s.n_wskew; ++r)
+    for (int s1 = 0; s1 < ns0; ++s1) {
+      double v = 0;
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+          double K = skew_unit(d, r, i, j);
+          if (K == 0.0) continue;
+          double m = 0;  // (J^{-T} E J^T)[i,j] = sum_{a,b} Ji[a,i] E[a,b] J[j,b]
+          for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) m += Ji[a * d + i] * tf_unit(d, s1, a, b) * J[j * d + b];
+          v += K * m;
+        }
+      h[r * ns0 + s1] = v;
+    }
+  double* w = geo + 88;
+  for (int f = 0; f <= d; ++f) {
+    double gn[3] = {0, 0, 0}, nn = 0;
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) gn[a] += Gi[a * d + b] * nhat[f * d + b];
+    for (int a = 0; a < d; ++a) nn += gn[a] * nhat[f * d + a];
+    for (int a = 0; a < d; ++a) w[f * d + a] = gn[a] / nn;
+  }
+  geo[100] = fabs(det);
+  geo[101] = det;
+}
+
+// Lane-parallel Cholesky of the n x n SPD matrix A (row-major, lower factor in place).
+template <class Sync>
+__host__ __device__ inline void chol_inplace(int n, double* A, int lane, int nl, Sync sync) {
+  for (int j = 0; j < n; ++j) {
+    if (lane == 0) A[j * n + j] = sqrt(A[j * n + j]);
+    sync();
+    double ljj = A[j * n + j];
+    for (int i = j + 1 + lane; i < n; i += nl) A[i * n + j] /= ljj;
+    sync();
+    // trailing update of the lower triangle
+    int m = n - j - 1;
+    for (int t = lane; t < m * m; t += nl) {
+      int i = j + 1 + t / m, l = j + 1 + t % m;
+      if (l <= i) A[i * n + l] -= A[i * n + j] * A[l * n + j];
+    }
+    sync();
+  }
+}
+
+// Full condensation of one element: A_T (n_A x n_A, row-major) with the orientation
+// signs of the facet-BDM dofs applied.
+template <class Sync>
+__host__ __device__ inline void condense_element(const ElemSizes& s, const ElemTables& t, const double* X,
+                                                 const int* sgn, double nu, ElemWork w, int lane, int nl,
+                                                 Sync sync) {
+  const int nraw = s.n_raw, ns0 = s.n_s0, nA = s.n_A, nu_ = s.n_u, ncc = s.n_cc, d = s.d;
+  if (lane == 0) elem_geometry(s, X, t.nhat, w.geo);
+  sync();
+  const double* L = w.geo;
+  const double* h = w.geo + 64;
+  const double* wf = w.geo + 88;
+  const double adet = w.geo[100];
+  const double cB = sqrt(nu / adet);
+  // ---- Bt rows ----
+  for (int r = lane; r < nA; r += nl) {
+    double* row = w.Bt + r * nraw;
+    if (r < nu_) {
+      for (int j = 0; j < nraw; ++j) row[j] = t.B0[r * nraw + j];
+      if (r < (d + 1) * s.nF) {
+        int f = r / s.nF, jF = r % s.nF;
+        for (int a = 0; a < d; ++a) {
+          double wa = wf[f * d + a];
+          const double* R = t.Rf + ((f * d + a) * s.nF + jF) * nraw;
+          for (int j = 0; j < nraw; ++j) row[j] -= wa * R[j];
+        }
+      }
+    } else {
+      const double* Bh = t.Bh + (r - nu_) * nraw;
+      for (int j = 0; j < nraw; ++j) row[j] = adet * Bh[j];
+    }
+    // transform by (I (x) L) * cB
+    for (int i = 0; i < s.nk; ++i) {
+      double tmp[8];
+      for (int q = 0; q < ns0; ++q) tmp[q] = row[i * ns0 + q];
+      for (int q = 0; q < ns0; ++q) {
+        double v = 0;
+        for (int p = q; p < ns0; ++p) v += tmp[p] * L[p * ns0 + q];
+        row[i * ns0 + q] = cB * v;
+      }
+    }
+  }
+  // ---- Ct rows: nt constraints, then rotation constraints ----
+  for (int r = lane; r < ncc; r += nl) {
+    double* row = w.Ct + r * nraw;
+    if (r < s.n_con) {
+      const double* C = t.Ccon + r * nraw;
+      for (int i = 0; i < s.nk; ++i)
+        for (int q = 0; q < ns0; ++q) {
+          double v = 0;
+          for (int p = q; p < ns0; ++p) v += C[i * ns0 + p] * L[p * ns0 + q];
+          row[i * ns0 + q] = v;
+        }
+    } else {
+      int rr = r - s.n_con;
+      int kr = rr / s.n_p, ip = rr % s.n_p;
+      for (int j = 0; j < nraw; ++j) row[j] = 0.0;
+      for (int q = 0; q < ns0; ++q) {
+        double v = 0;
+        for (int p = q; p < ns0; ++p) v += h[kr * ns0 + p] * L[p * ns0 + q];
+        row[ip * ns0 + q] = v;
+      }
+    }
+  }
+  sync();
+  // ---- A = Adiv + Bt Bt^T (lower triangle), V = Ct Bt^T, Sc = Ct Ct^T (lower) ----
+  const double cdiv = nu / (d * adet);
+  for (int t2 = lane; t2 < nA * nA; t2 += nl) {
+    int i = t2 / nA, j = t2 % nA;
+    if (j > i) continue;
+    double v = 0;
+    const double* a = w.Bt + i * nraw;
+    const double* b = w.Bt + j * nraw;
+    for (int q = 0; q < nraw; ++q) v += a[q] * b[q];
+    if (i < nu_ && j < nu_) v += cdiv * t.Adiv[i * nu_ + j];
+    w.A[i * nA + j] = v;
+  }
+  for (int t2 = lane; t2 < ncc * nA; t2 += nl) {
+    int i = t2 / nA, j = t2 % nA;
+    double v = 0;
+    const double* a = w.Ct + i * nraw;
+    const double* b = w.Bt + j * nraw;
+    for (int q = 0; q < nraw; ++q) v += a[q] * b[q];
+    w.V[i * nA + j] = v;
+  }
+  for (int t2 = lane; t2 < ncc * ncc; t2 += nl) {
+    int i = t2 / ncc, j = t2 % ncc;
+    if (j > i) continue;
+    double v = 0;
+    const double* a = w.Ct + i * nraw;
+    const double* b = w.Ct + j * nraw;
+    for (int q = 0; q < nraw; ++q) v += a[q] * b[q];
+    w.Sc[i * ncc + j] = v;
+  }
+  sync();
+  chol_inplace(ncc, w.Sc, lane, nl, sync);
+  // ---- Z = Lc^{-1} V, column by column (each lane owns columns) ----
+  for (int c = lane; c < nA; c += nl) {
+    for (int i = 0; i < ncc; ++i) {
+      double v = w.V[i * nA + c];
+      for (int p = 0; p < i; ++p) v -= w.Sc[i * ncc + p] * w.V[p * nA + c];
+      w.V[i * nA + c] = v / w.Sc[i * ncc + i];
+    }
+  }
+  sync();
+  // ---- A -= Z^T Z, signs, symmetric fill ----
+  for (int t2 = lane; t2 < nA * nA; t2 += nl) {
+    int i = t2 / nA, j = t2 % nA;
+    if (j > i) continue;
+    double v = w.A[i * nA + j];
+    for (int q = 0; q < ncc; ++q) v -= w.V[q * nA + i] * w.V[q * nA + j];
+    int nfd = (d + 1) * s.nF;
+    double si = (i < nfd) ? (double)sgn[i / s.nF] : 1.0;
+    double sj = (j < nfd) ? (double)sgn[j / s.nF] : 1.0;
+    w.A[i * nA + j] = v * si * sj;
+  }
+  sync();
+  for (int t2 = lane; t2 < nA * nA; t2 += nl) {
+    int i = t2 / nA, j = t2 % nA;
+    if (j > i) w.A[i * nA + j] = w.A[j * nA + i];
+  }
+  sync();
+}
+
+// coupling index (facet-major: facet f, t < nF facet-BDM mode, t >= nF uhat mode) -> local A index
+__host__ __device__ inline int coupling_to_local(const ElemSizes& s, int c) {
+  int f = c / s.mF, t = c % s.mF;
+  return (t < s.nF) ? f * s.nF + t : s.n_u + f * s.nhF + (t - s.nF);
+}
+
+// Bubble ("double Schur") condensation of A (n_A x n_A, full, in/out scratch):
+//   Aoo^{-1} (n_o x n_o), G = Aoo^{-1} Aoc (n_o x n_c), Ad = Acc - Aoc^T G (n_c x n_c),
+// coupling dofs in facet-major order.  work needs n_o*n_o + n_o*n_c doubles.
+template <class Sync>
+__host__ __device__ inline void bubble_condense(const ElemSizes& s, const double* A, double* work, double* Ad,
+                                                double* G, double* Aoo_inv, int lane, int nl, Sync sync) {
+  const int no = s.n_bub, nc = s.n_c, nA = s.n_A, ob = (s.d + 1) * s.nF;
+  double* Lo = work;           // Cholesky of Aoo
+  double* Tm = work + no * no; // Lo^{-1} Aoc
+  for (int t = lane; t < no * no; t += nl) {
+    int i = t / no, j = t % no;
+    Lo[t] = A[(ob + i) * nA + ob + j];
+  }
+  for (int t = lane; t < no * nc; t += nl) {
+    int i = t / nc, c = t % nc;
+    Tm[t] = A[(ob + i) * nA + coupling_to_local(s, c)];
+  }
+  sync();
+  chol_inplace(no, Lo, lane, nl, sync);
+  // forward substitution Lo Y = Aoc (columns per lane)
+  for (int c = lane; c < nc; c += nl)
+    for (int i = 0; i < no; ++i) {
+      double v = Tm[i * nc + c];
+      for (int p = 0; p < i; ++p) v -= Lo[i * no + p] * Tm[p * nc + c];
+      Tm[i * nc + c] = v / Lo[i * no + i];
+    }
+  sync();
+  // Ad = Acc - Y^T Y
+  for (int t = lane; t < nc * nc; t += nl) {
+    int i = t / nc, j = t % nc;
+    double v = A[coupling_to_local(s, i) * nA + coupling_to_local(s, j)];
+    for (int p = 0; p < no; ++p) v -= Tm[p * nc + i] * Tm[p * nc + j];
+    Ad[t] = v;
+  }
+  // G = Lo^{-T} Y (back substitution, columns per lane)
+  for (int c = lane; c < nc; c += nl)
+    for (int i = no - 1; i >= 0; --i) {
+      double v = Tm[i * nc + c];
+      for (int p = i + 1; p < no; ++p) v -= Lo[p * no + i] * G[p * nc + c];
+      G[i * nc + c] = v / Lo[i * no + i];
+    }
+  // Aoo^{-1} = Lo^{-T} Lo^{-1}: column j solves
+  for (int j = lane; j < no; j += nl) {
+    double y[64];
+    for (int i = 0; i < no; ++i) {
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int p = 0; p < i; ++p) v -= Lo[i * no + p] * y[p];
+      y[i] = v / Lo[i * no + i];
+    }
+    for (int i = no - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int p = i + 1; p < no; ++p) v -= Lo[p * no + i] * Aoo_inv[p * no + j];
+      Aoo_inv[i * no + j] = v / Lo[i * no + i];
+    }
+  }
+  sync();
+}
+
+}  // namespace mcs

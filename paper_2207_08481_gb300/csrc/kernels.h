@@ -1,0 +1,150 @@
+// Device kernels of libmcs and their host launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "element.cuh"
+
+namespace mcs {
+
+// Dof layout of the condensed system [u_d | u_o | uhat | p] (dof contract).
+struct Layout {
+  int64_t ne, nint;
+  int64_t n_dd, n_oo, n_hat, n_pres, ndof;
+  int64_t off_o, off_h, off_p;
+};
+
+// Static mesh / table data resident on the device.
+struct DevMesh {
+  int d;
+  int64_t ne, nint;
+  const double* coords;      // [nv][d]
+  const int32_t* elems;      // [ne][d+1]
+  const int32_t* elem_rank;  // [ne][d+1]
+  const int8_t* signs;       // [ne][d+1]
+  const double* adet;        // [ne] |det J|
+  const int32_t* fel;        // [nint][2] the two elements of each interior facet
+  const int32_t* floc;       // [nint][2] local facet index in each element
+};
+
+struct DevTables {
+  const double* B0;
+  const double* Rf;
+  const double* Bh;
+  const double* Ccon;
+  const double* Adiv;
+  const double* nhat;
+  const double* Bp;        // [n_p][n_u]
+  const double* Mu;        // [d][d][n_u][n_u]
+  const double* phi_load;  // [nq][n_u][d]
+  const double* xq_load;   // [nq][d]
+  const double* wq_load;   // [nq]
+  int nq_load;
+};
+
+// ---------------------------------------------------------------- condensation
+// Forms A_T (packed lower FP64), A^d_T, G_T, A_oo^{-1} (precision R) for every element.
+template <class R>
+cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, double* AT,
+                            R* Ad, R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st);
+// Facet blocks D_F of A^d (sum of the two elements), inverted.
+template <class R>
+cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, const R* Ad, R* Dinv, cudaStream_t st);
+
+// ---------------------------------------------------------------- operators (FP64)
+// y = K x
+cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
+                           const double* AT, const double* x, double* y, const int* stop, cudaStream_t st);
+// F = M_u c (velocity mass) on the u part; zero elsewhere
+cudaError_t launch_mass_u(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
+                          const double* c, double* F, cudaStream_t st);
+// F_i = (f, phi_i) with f given at the load quadrature points [ne][nq][d]
+cudaError_t launch_load(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
+                        const double* fq, double* F, cudaStream_t st);
+// physical load quadrature points [ne][nq][d]
+cudaError_t launch_load_points(const ElemSizes& s, const DevTables& t, const DevMesh& m, double* xq,
+                               cudaStream_t st);
+
+// ---------------------------------------------------------------- preconditioner pieces (precision R)
+struct GmgLevel {
+  int64_t n;                 // dofs
+  const int32_t* rowptr;     // CSR of Abar
+  const int32_t* col;
+  const void* val;           // R
+  const void* dl1inv;        // R, 1 / sum_j |A_ij|
+  // prolongation to this level from the coarser one (fine rows, <= 2 entries each)
+  const int32_t* prow;       // [n+1]
+  const int32_t* pcol;
+  const void* pval;
+  // restriction (transpose)
+  const int32_t* rrow;       // [n_coarse+1]
+  const int32_t* rcol;
+  const void* rval;
+};
+
+template <class R>
+struct PrecData {
+  const R* Ad;
+  const R* G;
+  const R* Aoi;
+  const R* Dinv;
+  const R* Eb;              // [nint][mF][d*d]
+  const int32_t* fvr;       // [nint][d] P1 rank of each facet vertex (-1 on the boundary)
+  const int32_t* vf_ptr;    // P1 vertex -> (facet rank, facet-vertex index) list, CSR over P1 vertices
+  const int32_t* vf_idx;    // pairs (facet rank, col)
+  int64_t nP1;
+  const int32_t* colour_list;  // interior ranks sorted by colour
+  const int64_t* colour_off;   // host array [ncol+1]
+  int ncol;
+  int smooth;        // facet-block Gauss-Seidel sweeps before / after the coarse correction
+  int gmg_smooth;    // l1-Jacobi sweeps per level before / after the coarse-grid correction
+  int multiplicative;
+  int nlev;
+  GmgLevel lev[12];
+  const double* coarse_inv;    // [n0][n0] FP64
+  // work vectors (R), all length ndof unless noted
+  R *b, *x, *t, *rr, *zz;
+  R *pb[12], *px[12], *pr[12], *ptmp[12];  // GMG vectors per level
+  double* coarse_tmp;  // [n0]
+};
+
+template <class R>
+cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
+                           PrecData<R>& P, const double* r, double* z, const int* stop, cudaStream_t st);
+
+// Ahat^{-1} alone on the velocity part (for diagnostics / unit parity)
+template <class R>
+cudaError_t launch_ahat_inv(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* rin,
+                            R* out, const int* stop, cudaStream_t st);
+
+// ---------------------------------------------------------------- Krylov helpers (FP64)
+// out[0] = a.b, deterministic: fixed grid, block partials summed in index order by the last block.
+// scratch: >= 2100 doubles (partials, counters) per stream.
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* scratch, double* out, const int* stop,
+                       cudaStream_t st);
+// remove the mean of p_h: p_{T,0} -= (sum adet_T p_{T,0}) / (sum adet_T)
+cudaError_t launch_mean_zero(const DevMesh& m, const Layout& L, int n_p, double* x, double* scratch,
+                             double total_adet, const int* stop, cudaStream_t st);
+
+// MinRes state on the device
+// Inputs (set by the host before each cycle): rtol (relative to g_first), floor_rtol (least
+// relative reduction asked of one cycle), g_first (< 0: this is the first cycle), maxit.
+struct MinresScalars {
+  double gamma, gamma_old, eta, c, c_old, s, s_old, delta, res0, rtol, floor_rtol, g_first, rtol_cycle;
+  double a1, a2, a3, coef_x;   // w_new = (z - a3 w_old - a2 w)/a1, x += coef_x w_new
+  double dot1, dot2;           // dot results
+  int it, maxit, stop, status;
+};
+cudaError_t launch_minres_init(MinresScalars* S, cudaStream_t st);
+cudaError_t launch_minres_scalars(MinresScalars* S, cudaStream_t st);
+// v_old <- Kz - (delta/gamma) v - (gamma/gamma_old) v_old  (after z <- z/gamma inside)
+cudaError_t launch_minres_lanczos(MinresScalars* S, int64_t n, double* z, const double* Kz, const double* v,
+                                  double* v_old, cudaStream_t st);
+int64_t condense_scratch_doubles(const ElemSizes& s, int nsm);
+cudaError_t launch_minres_update(MinresScalars* S, int64_t n, const double* z, double* w, double* w_old,
+                                 double* x, cudaStream_t st);
+cudaError_t launch_minres_scale(MinresScalars* S, int64_t n, const double* zin, double* z, cudaStream_t st);
+cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
+
+}  // namespace mcs

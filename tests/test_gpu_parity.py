@@ -1,0 +1,181 @@
+"""GPU path (libmcs through its C-ABI) against the CPU oracle, element by element."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import workloads  # noqa: E402
+from oracle import manufactured, mesh, precond, system  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def mcs():
+    from paper_2207_08481_gb300 import build
+    build.build()
+    import paper_2207_08481_gb300.mcs as m
+    return m
+
+
+def _handle(mcs, d, N, k, nu, **kw):
+    h = mcs.Handle.structured(d, N, k, nu, **kw)
+    h.condense()
+    return h
+
+
+def _oracle(d, N, k, nu):
+    D = system.discretize(mesh.structured(d, N), k, nu)
+    return D, system.condense(D)
+
+
+CASES = [(2, 4, 2, 0.7), (2, 3, 3, 1.3), (3, 2, 2, 0.7), (3, 1, 3, 1.0)]
+
+
+@pytest.mark.parametrize("d,N,k,nu", CASES)
+def test_mesh_dofs_pattern_bit_exact(mcs, d, N, k, nu):
+    h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=1)
+    m = mesh.structured(d, N)
+    facets, ef, sg, col = h.export_mesh()
+    assert np.array_equal(facets, m.facets)
+    assert np.array_equal(ef, m.elem_facets)
+    assert np.array_equal(sg, m.signs)
+    assert np.array_equal(col, mesh.colouring(m))
+    D = system.discretize(m, k, nu)
+    dm = h.export_dofmap()
+    assert np.array_equal(dm[:, :D.sz["n_u"]], D.u_map)
+    assert np.array_equal(dm[:, D.sz["n_u"]:D.sz["n_A"]], D.h_map)
+    assert np.array_equal(dm[:, D.sz["n_A"]:], D.p_map)
+    rp, cl = h.export_pattern()
+    Kp = system.pattern(D)
+    assert np.array_equal(rp, Kp.indptr) and np.array_equal(cl, Kp.indices)
+    h.close()
+
+
+@pytest.mark.parametrize("d,N,k,nu", CASES)
+def test_condensed_element_matrices(mcs, d, N, k, nu):
+    """A_T (eq. femSPmat), A^d_T and G_T (eq. Hcoeffs) against the literal oracle condensation."""
+    h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=1)
+    D, AT = _oracle(d, N, k, nu)
+    ne, nA = AT.shape[0], AT.shape[1]
+    P = h.element_matrices(0, ne)
+    il = np.tril_indices(nA)
+    ref = AT[:, il[0], il[1]]
+    err = np.abs(P - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    assert err.max() < 1e-12, err.max()
+    Ad_o, G_o, _ = system.bubble_condense(D, AT)
+    Ad, G = h.schur(0, ne)
+    # GPU coupling order is facet-major; map to the oracle's [u_d | uhat] order
+    sz = D.sz
+    o, c = system.local_split(D)
+    pos = {v: i for i, v in enumerate(c)}
+    perm = []
+    for cc in range(h.sizes.n_c):
+        f, t = divmod(cc, h.sizes.mF)
+        perm.append(pos[f * sz["nF"] + t if t < sz["nF"] else sz["n_u"] + f * sz["n_hatF"] + (t - sz["nF"])])
+    Ado = Ad_o[:, perm][:, :, perm]
+    Go = G_o[:, :, perm]
+    assert (np.abs(Ad - Ado).max() / np.abs(Ado).max()) < 1e-11
+    assert (np.abs(G - Go).max() / np.abs(Go).max()) < 1e-10
+    h.close()
+
+
+@pytest.mark.parametrize("d,N,k,nu", CASES)
+def test_apply_matches_oracle(mcs, d, N, k, nu):
+    h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=1)
+    D, AT = _oracle(d, N, k, nu)
+    K = system.condensed_system(D, AT)
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        x = rng.standard_normal(D.ndof)
+        xt = torch.tensor(x, device="cuda")
+        y = torch.zeros_like(xt)
+        h.apply(xt, y)
+        yo = K @ x
+        assert np.abs(y.cpu().numpy() - yo).max() < 1e-12 * np.abs(yo).max()
+    h.close()
+
+
+@pytest.mark.parametrize("d,N,k,nu,lev", [(2, 8, 2, 0.7, 2), (2, 4, 3, 1.0, 1), (2, 8, 2, 1.0, 3), (3, 2, 2, 1.0, 1),
+                                          (3, 4, 2, 0.5, 2)])
+def test_precond_fp64_matches_oracle(mcs, d, N, k, nu, lev):
+    """Khat^{-1} (eq. mhatinvfactor with the multiplicative ASP of Sec. 6.1) step for step."""
+    h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=lev)
+    D, AT = _oracle(d, N, k, nu)
+    bp = precond.BlockPreconditioner(D, precond.ASP(D, AT, precond.GMG(d, N, lev, nu)))
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(D.ndof)
+    z = torch.zeros(D.ndof, dtype=torch.float64, device="cuda")
+    h.precond(torch.tensor(r, device="cuda"), z)
+    zo = bp.apply(r)
+    assert np.abs(z.cpu().numpy() - zo).max() < 1e-11 * np.abs(zo).max()
+    h.close()
+
+
+def test_precond_mixed_close_to_oracle(mcs):
+    h = _handle(mcs, 2, 8, 2, 1.0, precision=mcs.MCS_MIXED, gmg_levels=2)
+    D, AT = _oracle(2, 8, 2, 1.0)
+    bp = precond.BlockPreconditioner(D, precond.ASP(D, AT, precond.GMG(2, 8, 2, 1.0)))
+    r = np.random.default_rng(5).standard_normal(D.ndof)
+    z = torch.zeros(D.ndof, dtype=torch.float64, device="cuda")
+    h.precond(torch.tensor(r, device="cuda"), z)
+    zo = bp.apply(r)
+    assert np.abs(z.cpu().numpy() - zo).max() < 1e-4 * np.abs(zo).max()
+    h.close()
+
+
+def _manufactured_rhs(h, d, nu):
+    s = h.sizes
+    xq = torch.zeros((s.ne * s.nq_load, d), dtype=torch.float64, device="cuda")
+    h.load_points(xq)
+    F = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
+    h.load_vector(workloads.manufactured_f(d, nu, xq), F)
+    return F
+
+
+@pytest.mark.parametrize("d,N,k,nu", [(2, 8, 2, 1.0), (2, 4, 3, 0.01), (3, 2, 2, 1.0)])
+def test_load_vector(mcs, d, N, k, nu):
+    h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=1)
+    D = system.discretize(mesh.structured(d, N), k, nu)
+    Fo = system.load(D, manufactured.Manufactured(d, nu).f)
+    F = _manufactured_rhs(h, d, nu).cpu().numpy()
+    assert np.abs(F - Fo).max() < 1e-11 * np.abs(Fo).max()
+    h.close()
+
+
+def test_mass_velocity(mcs):
+    d, N, k = 2, 4, 3
+    h = _handle(mcs, d, N, k, 1.0, precision=mcs.MCS_FP64, gmg_levels=1)
+    D = system.discretize(mesh.structured(d, N), k, 1.0)
+    Mu = system.assemble(D.u_map, D.u_map, D.mats["Mu"], (D.ndof, D.ndof))
+    c = np.zeros(D.ndof)
+    c[:D.off_h] = workloads.random_coefficients(D.off_h, 3)
+    F = torch.zeros(D.ndof, dtype=torch.float64, device="cuda")
+    h.mass_velocity(torch.tensor(c, device="cuda"), F)
+    Fo = Mu @ c
+    assert np.abs(F.cpu().numpy() - Fo).max() < 1e-12 * np.abs(Fo).max()
+    h.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_solve_c1_matches_oracle(mcs, prec, tol):
+    """c1: 2D 8x8, k=2, nu=1, manufactured solution; relative error vs the oracle's direct solve."""
+    d, N, k, nu = 2, 8, 2, 1.0
+    p = mcs.MCS_FP64 if prec == "fp64" else mcs.MCS_MIXED
+    h = _handle(mcs, d, N, k, nu, precision=p, rtol=1e-12 if prec == "fp64" else 1e-10)
+    F = _manufactured_rhs(h, d, nu)
+    x = torch.zeros_like(F)
+    info = h.solve(F, x)
+    D = system.discretize(mesh.structured(d, N), k, nu)
+    Fo = system.load(D, manufactured.Manufactured(d, nu).f)
+    xo, _, _ = system.solve_full(D, Fo)
+    xo = system.mean_zero_pressure(D, xo)
+    xg = x.cpu().numpy()
+    n = D.off_p
+    eu = np.linalg.norm(xg[:n] - xo[:n]) / np.linalg.norm(xo[:n])
+    ep = np.linalg.norm(xg[n:] - xo[n:]) / np.linalg.norm(xo[n:])
+    assert eu < tol and ep < tol, (eu, ep, info.iterations)
+    assert info.status == 0 and info.iterations < 300
+    h.close()

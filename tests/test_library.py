@@ -1,0 +1,57 @@
+"""Host-side checks of the C-ABI library (no GPU compute)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2207_08481_gb300 import build
+    build.build()
+    import paper_2207_08481_gb300.mcs as mcs
+    return mcs
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "mcs.h")).read()
+    return sorted(set(re.findall(r"\b(mcs_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_declares_exactly_the_binding(lib):
+    assert _declared() == sorted(lib.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    for name in _declared():
+        assert name in syms, name
+        assert hasattr(lib.lib(), name)
+
+
+def test_host_entry_points(lib):
+    L = lib.lib()
+    assert L.mcs_version() >= 100
+    o = lib.default_options()
+    assert o.precision == lib.MCS_MIXED and o.smooth_steps == 2 and o.rtol == 1e-8
+    assert L.mcs_default_options(None) == lib.MCS_ERR_INVALID_ARG
+    assert isinstance(L.mcs_last_error(), bytes)
+
+
+def test_invalid_arguments_are_reported_not_raised(lib):
+    L = lib.lib()
+    h = ctypes.c_void_p()
+    o = lib.default_options()
+    # bad dimension / degree / viscosity are rejected before any device work
+    assert L.mcs_setup_structured(4, 8, 2, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
+    assert L.mcs_setup_structured(2, 8, 1, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
+    assert L.mcs_setup_structured(2, 8, 2, -1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
+    assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(o), None, None) == lib.MCS_ERR_INVALID_ARG
+    assert b"NULL" in L.mcs_last_error()
+    assert L.mcs_apply(None, None, None) == lib.MCS_ERR_INVALID_ARG
+    assert L.mcs_destroy(None) == lib.MCS_OK
