@@ -154,8 +154,11 @@ def _ref_rules(d, q):
     return xv, wv, s, ws
 
 
-def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None) -> ElementData:
-    """Physical bases of all spaces on the elements with vertex coordinates X[E, d+1, d]."""
+def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None,
+                 velocity_only: bool = False) -> ElementData:
+    """Physical bases of all spaces on the elements with vertex coordinates X[E, d+1, d].
+
+    velocity_only: only U, DU, divU and P are evaluated (the other fields are None)."""
     E_, dp1, d = X.shape
     sz = local_sizes(d, k)
     q = q if q is not None else k + 2
@@ -243,6 +246,8 @@ def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None)
     # ---------------- pressure ---------------------------------------------
     n_p = sz["n_p"]
     P = np.broadcast_to(psi[None, :, :n_p], (E_, nq, n_p)).copy()
+    if velocity_only:
+        return ElementData(detJ, wq, xq, U, DU, divU, P, None, None, None, fw, fx, fn, fU, None, None)
 
     # ---------------- Sigma(T): null space of the nt constraints -----------
     TF = trace_free_units(d)                                    # [ns0, d, d]
@@ -332,6 +337,6 @@ def element_matrices(X, signs, k, nu):
 
 def load_vector(X, signs, k, f, q=None):
     """F_i = (f, phi^u_i)_T on each element; f(x[..., d]) -> [..., d]."""
-    D = element_data(X, signs, k, q=q if q is not None else k + 8)
+    D = element_data(X, signs, k, q=q if q is not None else k + 8, velocity_only=True)
     fv = f(D.xq)
     return np.einsum("eq,eqa,eqia->ei", D.wq, fv, D.U)

@@ -172,14 +172,27 @@ def full_system(D: Discretization):
     return Kf, off
 
 
+def _solve_pinned(K: sp.spmatrix, rhs: np.ndarray, pin: int) -> np.ndarray:
+    """Direct solve of the singular saddle-point system whose kernel is the constant pressure:
+    the constant-mode coefficient `pin` is fixed to 0 (row and column removed); the caller
+    removes the pressure mean afterwards (pure Dirichlet boundary, reading R6)."""
+    n = K.shape[0]
+    keep = np.ones(n, dtype=bool)
+    keep[pin] = False
+    idx = np.nonzero(keep)[0]
+    Kr = K.tocsr()[idx][:, idx].tocsc()
+    sol = np.zeros(n)
+    sol[idx] = spla.spsolve(Kr, rhs[idx])
+    return sol
+
+
 def solve_full(D: Discretization, F: np.ndarray):
-    """Direct solve of the uncondensed system (plus int p = 0); returns (x_condensed_layout, sigma, omega)."""
+    """Direct solve of the uncondensed system; returns (x_condensed_layout, sigma, omega).
+    The pressure is determined up to a constant; use mean_zero_pressure on the result."""
     Kf, off = full_system(D)
-    c = np.concatenate([np.zeros(off), pressure_constraint(D)])
     n = Kf.shape[0]
-    Kc = sp.bmat([[Kf, sp.csr_matrix(c[:, None])], [sp.csr_matrix(c[None, :]), None]], format="csc")
-    rhs = np.concatenate([np.zeros(off), F, [0.0]])
-    sol = spla.spsolve(Kc, rhs)
+    rhs = np.concatenate([np.zeros(off), F])
+    sol = _solve_pinned(Kf, rhs, off + int(D.p_map[0, 0]))
     ne = D.mesh.elems.shape[0]
     ns, nw = D.sz["n_sigma"], D.sz["n_omega"]
     sigma = sol[:ne * ns].reshape(ne, ns)
@@ -215,11 +228,9 @@ def condensed_system(D: Discretization, AT: np.ndarray | None = None):
 
 
 def solve_condensed(D: Discretization, F: np.ndarray, AT=None):
+    """Direct solve of K x = F (eq. femSPmat); pressure up to a constant (see solve_full)."""
     K = condensed_system(D, AT)
-    c = pressure_constraint(D)
-    Kc = sp.bmat([[K, sp.csr_matrix(c[:, None])], [sp.csr_matrix(c[None, :]), None]], format="csc")
-    sol = spla.spsolve(Kc, np.concatenate([F, [0.0]]))
-    return sol[:-1]
+    return _solve_pinned(K, F, int(D.p_map[0, 0]))
 
 
 def local_split(D: Discretization):
