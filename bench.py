@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the MCS Stokes hot path on GB300: solves per second.
+
+One step = static condensation (mcs_condense) + the ASP-preconditioned MinRes solve
+(mcs_solve) to relative preconditioned residual 1e-8, on the workload c2: the unit
+square with 256x256 cells (131,072 triangles), k = 3, nu = 1e-2, manufactured
+solution, 5-level geometric multigrid (16^2 coarsest) for the conforming space.
+`value` is the mixed form (FP32 preconditioner, FP64 outer Krylov and operator);
+the FP64 form is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Under torchrun each rank solves its own copy of the workload (independent problems,
+"replicas": the path has no exchange between problems), value = total solves / max time.
+--impl reference times the CPU FP64 oracle (the test oracle of this repository) on a
+bounded sample of the same workload and scales it to the full problem size.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Stokes solves/s to rel. res 1e-8, mixed vs FP64 form; HBM roofline %; p50/p99"
+WORKLOAD = dict(dim=2, N=256, k=3, nu=1e-2, levels=5, rtol=1e-8)
+WORKLOAD_NAME = ("c2: 2D unit square, 256x256 cells split into 131,072 triangles (4 uniform refinements of "
+                 "16x16 for the multigrid), MCS k=3, nu=1e-2, manufactured solution")
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = sorted(float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit())
+        mx = max(float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for i, n in enumerate(names):
+                if len(s) > 5 + i and s[5 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_c2.txt")
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_launch:"):
+                return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def _make_handle(mcs, precision):
+    w = WORKLOAD
+    return mcs.Handle.structured(w["dim"], w["N"], w["k"], w["nu"], precision=precision, gmg_levels=w["levels"],
+                                 rtol=w["rtol"])
+
+
+def _rhs(h, torch, workloads):
+    w = WORKLOAD
+    s = h.sizes
+    xq = torch.zeros((s.ne * s.nq_load, w["dim"]), dtype=torch.float64, device="cuda")
+    h.load_points(xq)
+    F = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
+    h.load_vector(workloads.manufactured_f(w["dim"], w["nu"], xq), F)
+    del xq
+    return F
+
+
+def _count_launches(torch, fn):
+    """Our kernels launched by one call of fn (CUPTI via torch.profiler, outside the timed region)."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        n = 0
+        for e in prof.events():
+            nm = e.name or ""
+            if str(e.device_type).endswith("CUDA") and ("mcs::" in nm or "3mcs" in nm) and "emcpy" not in nm:
+                n += 1
+        return n
+    except Exception:
+        return None
+
+
+def run_gpu(args):
+    import torch
+
+    import workloads
+    from paper_2207_08481_gb300 import build
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # one rank compiles; the others wait for the library
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2207_08481_gb300.mcs as mcs
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(h, F, x, steps, profile=False):
+        def step():
+            h.condense()
+            x.zero_()
+            return h.solve(F, x)
+        for _ in range(args.warmup):
+            info = step()
+        if profile:
+            h.profile(True)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        its = []
+        for _ in range(steps):
+            info = step()
+            its.append(info.iterations)
+        ev1.record()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        stats = h.profile_read() if profile else None
+        if profile:
+            h.profile(False)
+        return ms, its, info, stats
+
+    # ---------------- mixed form (headline)
+    hm = _make_handle(mcs, mcs.MCS_MIXED)
+    F = _rhs(hm, torch, workloads)
+    x = torch.zeros_like(F)
+    ndof = hm.sizes.ndof
+    with ClockSampler(local) as clk:
+        ms_mixed, its_mixed, info_m, stats = timed(hm, F, x, args.steps, profile=True)
+    value = args.steps * world / (ms_mixed / 1e3)
+    # error of the solution against the exact one is not part of the metric; residuals are
+    resid_m = dict(precond=info_m.rel_res_precond, true=info_m.rel_res_true)
+
+    # ---------------- end to end through the host-buffer entry point
+    import numpy as np
+    Fh = F.cpu().numpy().copy()
+    xh = np.zeros_like(Fh)
+    for _ in range(args.warmup):
+        hm.condense()
+        xh[:] = 0.0
+        hm.solve_host(Fh, xh)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hm.condense()
+        xh[:] = 0.0
+        hm.solve_host(Fh, xh)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = args.steps * world / e2e_s
+
+    def one_step():
+        hm.condense()
+        x.zero_()
+        hm.solve(F, x)
+    launches = _count_launches(torch, one_step) if rank == 0 else None
+    hm.close()
+
+    # ---------------- FP64 form
+    hd = _make_handle(mcs, mcs.MCS_FP64)
+    xd = torch.zeros_like(F)
+    fp64_steps = max(1, args.steps // 2)
+    ms_fp64, its_fp64, info_d, _ = timed(hd, F, xd, fp64_steps)
+    value_fp64 = fp64_steps * world / (ms_fp64 / 1e3)
+    hd.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---------------- roofline of the dominant kernel class
+    peak, peak_kind = _peaks()
+    dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    name, st = dom
+    per_launch_ms = st["ms"] / max(st["launches"], 1)
+    if name in ("condense", "apply_K"):
+        achieved = st["flops"] / max(st["launches"], 1) / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": 1.20, "unit": "TFLOP/s",
+                "frac": achieved / 1.20, "traffic": None, "peak_kind": "measured FP64 FMA probe"}
+    else:
+        achieved = st["bytes"] / max(st["launches"], 1) / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": _traffic(name),
+                "algorithmic_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+                "avg_launch_us": round(per_launch_ms * 1e3, 2), "peak_kind": peak_kind}
+    share = {k: round(v["ms"] / sum(u["ms"] for u in stats.values()), 4) for k, v in stats.items() if v["launches"]}
+
+    cpu = _cpu_baseline(args) if not args.no_cpu_baseline else None
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_mixed / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer Krylov + K, f32 preconditioner",
+        "data": "synthetic (manufactured solution on a structured Kuhn mesh)",
+        "config": {"workload": WORKLOAD_NAME, "step": "mcs_condense + mcs_solve (MinRes, rel. preconditioned "
+                   "residual 1e-8)", "ndof": ndof, "form": "mixed", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (resident operators ~1.7 GB per problem)"},
+        "iterations": its_mixed[-1], "rel_res": resid_m,
+        "condensed_dofs_per_s": round(value * ndof, 1),
+        "fp64_form": {"value": round(value_fp64, 4), "unit": "solves/s", "ms_per_step": round(ms_fp64 / fp64_steps, 3),
+                      "steps": fp64_steps, "iterations": its_fp64[-1],
+                      "rel_res": dict(precond=info_d.rel_res_precond, true=info_d.rel_res_true)},
+        "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": 2 * ndof * 8,
+                "d2h_bytes_per_step": ndof * 8},
+        "roofline": roof, "kernel_time_share": share,
+        "gpu_launches": (launches * args.steps) if launches is not None else None,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(N: int):
+    """Oracle (CPU, FP64) on the c2 workload type at N cells per direction: discretize,
+    condense, load and direct solve.  Returns seconds."""
+    from oracle import manufactured, mesh, system
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    D = system.discretize(mesh.structured(w["dim"], N), w["k"], w["nu"])
+    AT = system.condense(D)
+    F = system.load(D, manufactured.Manufactured(w["dim"], w["nu"]).f)
+    x = system.solve_condensed(D, F, AT)
+    system.mean_zero_pressure(D, x)
+    return time.perf_counter() - t0
+
+
+def _cpu_baseline(args, N=48):
+    secs = _oracle_sample(N)
+    w = WORKLOAD
+    scale = (w["N"] / N) ** w["dim"]
+    est = secs * scale
+    return {"value": round(1.0 / est, 6), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle (discretize + condense + sparse direct solve) on the c2 workload type at "
+                      f"{N}x{N} cells ({2 * N * N} triangles) took {secs:.1f} s; scaled linearly by elements "
+                      f"(x{scale:.1f}) to 256x256"}
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    times = []
+    for _ in range(args.warmup):
+        _oracle_sample(args.ref_N)
+    for _ in range(args.steps):
+        times.append(_oracle_sample(args.ref_N))
+    w = WORKLOAD
+    scale = (w["N"] / args.ref_N) ** w["dim"]
+    per = sum(times) / len(times) * scale
+    value = 1.0 / per
+    cpu = {"value": round(value, 6), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"each step: oracle on {args.ref_N}x{args.ref_N} cells, scaled linearly by elements (x{scale:.0f})"}
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAME, "form": "oracle: direct solve of the condensed system"},
+           "cpu_baseline": cpu,
+           "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-N", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -167,6 +167,21 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info);
 /* Same as mcs_solve with HOST vectors F, x [ndof]: copies F and x in, solves, copies x out. */
 int mcs_solve_host(mcs_handle* h, const double* F_host, double* x_host, mcs_solve_info* info);
 
+/* Kernel timing (diagnostics): when enabled, the library brackets its main kernel classes
+ * with CUDA events on the handle's stream during mcs_condense / mcs_apply / mcs_precond /
+ * mcs_solve.  mcs_profile(h, 1) enables and clears, 0 disables.  mcs_profile_read fills up
+ * to max_n entries (one per kernel class: name, launches, total device ms, algorithmic bytes
+ * and flops of those launches) and returns their number; it synchronises the stream. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double bytes;
+  double flops;
+} mcs_kernel_stat;
+int mcs_profile(mcs_handle* h, int enable);
+int mcs_profile_read(mcs_handle* h, mcs_kernel_stat* out, int max_n);
+
 /* Releases the handle and its device memory (synchronises its stream). */
 int mcs_destroy(mcs_handle* h);
 

@@ -14,6 +14,7 @@
 #include "../../include/mcs.h"
 #include "kernels.h"
 #include "meshing.h"
+#include "profiler.h"
 #include "reference.h"
 
 using namespace mcs;
@@ -52,6 +53,13 @@ int guarded(F&& f) {
     return MCS_ERR_INVALID_ARG;
   }
 }
+
+// Installs the handle's profiler (if enabled) for the duration of an API call.
+struct ProfScope {
+  Profiler* prev;
+  explicit ProfScope(Profiler* p) : prev(g_prof) { g_prof = p; }
+  ~ProfScope() { g_prof = prev; }
+};
 
 ElemSizes elem_sizes(const Sizes& s) {
   ElemSizes e;
@@ -103,6 +111,7 @@ struct mcs_handle {
   MinresScalars* S_host = nullptr;  // pinned
   double* cond_scratch = nullptr;
   int64_t cond_scratch_doubles = 0;
+  std::unique_ptr<Profiler> prof;
 
   template <class T>
   T* dalloc(int64_t n) {
@@ -191,9 +200,9 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
                      const std::vector<int32_t>& clist) {
   const Sizes& s = h->sz;
   const int64_t ne = h->mesh.ne, nint = h->mesh.nint;
-  P.Ad = h->dalloc<R>(ne * s.n_c * s.n_c);
-  P.G = h->dalloc<R>(ne * s.n_bub * s.n_c);
-  P.Aoi = h->dalloc<R>(ne * s.n_bub * s.n_bub);
+  P.Ad = h->dalloc<R>(ne * (int64_t)(s.d + 1) * slab_pad(s));
+  P.G = h->dalloc<R>(ne * (int64_t)g_stride(s));
+  P.Aoi = h->dalloc<R>(ne * (int64_t)a_stride(s));
   P.Dinv = h->dalloc<R>(nint * s.mF * s.mF);
   P.Eb = h->upload(cast_vec<R>(Eb));
   P.fvr = h->upload(fvr);
@@ -298,6 +307,11 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   dm.adet = h->upload(adet);
   dm.fel = h->upload(fel);
   dm.floc = h->upload(floc);
+  std::vector<int32_t> fsr(m.nint * 2 * (d + 1));
+  for (int64_t r = 0; r < m.nint; ++r)
+    for (int side = 0; side < 2; ++side)
+      for (int f = 0; f <= d; ++f) fsr[(r * 2 + side) * (d + 1) + f] = m.elem_rank[fel[r * 2 + side] * (d + 1) + f];
+  dm.fsr = h->upload(fsr);
   // tables
   DevTables& dt = h->dt;
   const RefTables& R = h->ref;
@@ -365,7 +379,7 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   else
     build_precision<double>(h, h->pd, A, Pr, Rt, cinv, Eb, fvr, vf_ptr, vf_idx, clist);
   // condensed operator and Krylov work
-  h->AT = h->dalloc<double>(m.ne * (int64_t)s.n_A * (s.n_A + 1) / 2);
+  h->AT = h->dalloc<double>(m.ne * (int64_t)s.n_A * s.n_A);
   for (int i = 0; i < 10; ++i) h->kv[i] = h->dalloc<double>(L.ndof);
   h->scratch = h->dalloc<double>(4096);
   cuda_check(cudaMemset(h->scratch, 0, sizeof(double) * 4096), "memset");
@@ -579,6 +593,7 @@ int mcs_export_pattern(const mcs_handle* h, int64_t* rowptr, int32_t* col) {
 int mcs_condense(mcs_handle* h) {
   return guarded([&]() -> int {
     if (!h) throw McsError(MCS_ERR_INVALID_ARG, "NULL handle");
+    ProfScope ps(h->prof.get());
     if (h->opt.precision == MCS_MIXED) {
       cuda_check(launch_condense<float>(h->es, h->dt, h->dm, h->nu, h->AT, (float*)h->pf.Ad, (float*)h->pf.G,
                                         (float*)h->pf.Aoi, h->cond_scratch, h->cond_scratch_doubles, h->stream),
@@ -599,9 +614,15 @@ int mcs_condense(mcs_handle* h) {
 int mcs_copy_element_matrices(const mcs_handle* h, int64_t T0, int64_t count, double* out) {
   return guarded([&]() -> int {
     if (!h || !out || T0 < 0 || count < 0 || T0 + count > h->mesh.ne) throw McsError(MCS_ERR_INVALID_ARG, "range");
-    const int64_t np = (int64_t)h->sz.n_A * (h->sz.n_A + 1) / 2;
+    const int nA = h->sz.n_A;
+    const int64_t np = (int64_t)nA * (nA + 1) / 2, full = (int64_t)nA * nA;
     cuda_check(cudaStreamSynchronize(h->stream), "sync");
-    cuda_check(cudaMemcpy(out, h->AT + T0 * np, sizeof(double) * np * count, cudaMemcpyDeviceToHost), "copy");
+    std::vector<double> tmp(full * count);
+    cuda_check(cudaMemcpy(tmp.data(), h->AT + T0 * full, sizeof(double) * full * count, cudaMemcpyDeviceToHost),
+               "copy");
+    for (int64_t T = 0; T < count; ++T)
+      for (int i = 0; i < nA; ++i)
+        for (int j = 0; j <= i; ++j) out[T * np + (int64_t)i * (i + 1) / 2 + j] = tmp[T * full + (int64_t)i * nA + j];
     return MCS_OK;
   });
 }
@@ -612,7 +633,6 @@ int mcs_copy_schur(const mcs_handle* h, int64_t T0, int64_t count, double* Ad_ho
     const Sizes& s = h->sz;
     cuda_check(cudaStreamSynchronize(h->stream), "sync");
     auto fetch = [&](const void* src, int64_t per, double* dst) {
-      if (!dst) return;
       if (h->opt.precision == MCS_MIXED) {
         std::vector<float> tmp(per * count);
         cuda_check(cudaMemcpy(tmp.data(), (const float*)src + T0 * per, sizeof(float) * per * count,
@@ -625,8 +645,23 @@ int mcs_copy_schur(const mcs_handle* h, int64_t T0, int64_t count, double* Ad_ho
     };
     const void* Ad = h->opt.precision == MCS_MIXED ? (const void*)h->pf.Ad : (const void*)h->pd.Ad;
     const void* G = h->opt.precision == MCS_MIXED ? (const void*)h->pf.G : (const void*)h->pd.G;
-    fetch(Ad, (int64_t)s.n_c * s.n_c, Ad_host);
-    fetch(G, (int64_t)s.n_bub * s.n_c, G_host);
+    if (Ad_host) {
+      const int64_t per = (int64_t)(s.d + 1) * slab_pad(s), nc2 = (int64_t)s.n_c * s.n_c;
+      std::vector<double> tmp(per * count);
+      fetch(Ad, per, tmp.data());
+      for (int64_t T = 0; T < count; ++T)
+        for (int i = 0; i < s.n_c; ++i)
+          for (int c = 0; c < s.n_c; ++c)
+            Ad_host[T * nc2 + (int64_t)i * s.n_c + c] =
+                tmp[adw_index(s.d + 1, slab_pad(s), s.mF, T, i / s.mF, c, i % s.mF)];
+    }
+    if (G_host) {
+      const int64_t per = g_stride(s), ng = (int64_t)s.n_bub * s.n_c;
+      std::vector<double> tmp(per * count);
+      fetch(G, per, tmp.data());
+      for (int64_t T = 0; T < count; ++T)
+        for (int64_t q = 0; q < ng; ++q) G_host[T * ng + q] = tmp[T * per + q];
+    }
     return MCS_OK;
   });
 }
@@ -658,6 +693,7 @@ int mcs_mass_velocity(mcs_handle* h, const double* c, double* F) {
 int mcs_apply(mcs_handle* h, const double* x, double* y) {
   return guarded([&]() -> int {
     if (!h || !x || !y) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    ProfScope ps(h->prof.get());
     if (!h->condensed) throw McsError(MCS_ERR_INVALID_ARG, "mcs_condense has not been called");
     cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, x, y, nullptr, h->stream), "apply");
     return MCS_OK;
@@ -674,6 +710,7 @@ static void precond_any(mcs_handle* h, const double* r, double* z, const int* st
 int mcs_precond(mcs_handle* h, const double* r, double* z) {
   return guarded([&]() -> int {
     if (!h || !r || !z) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    ProfScope ps(h->prof.get());
     if (!h->condensed) throw McsError(MCS_ERR_INVALID_ARG, "mcs_condense has not been called");
     precond_any(h, r, z, nullptr);
     return MCS_OK;
@@ -732,6 +769,7 @@ void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double floor_
 int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
   return guarded([&]() -> int {
     if (!h || !F || !x) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    ProfScope ps(h->prof.get());
     if (!h->condensed) throw McsError(MCS_ERR_INVALID_ARG, "mcs_condense has not been called");
     const int64_t n = h->L.ndof;
     cudaStream_t st = h->stream;
@@ -795,6 +833,40 @@ int mcs_solve_host(mcs_handle* h, const double* F_host, double* x_host, mcs_solv
     cuda_check(cudaMemcpyAsync(x_host, x, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream), "d2h");
     cuda_check(cudaStreamSynchronize(h->stream), "sync");
     return rc;
+  });
+}
+
+int mcs_profile(mcs_handle* h, int enable) {
+  return guarded([&]() -> int {
+    if (!h) throw McsError(MCS_ERR_INVALID_ARG, "NULL handle");
+    if (enable) {
+      if (!h->prof) h->prof.reset(new Profiler());
+      h->prof->reset();
+    } else {
+      h->prof.reset();
+    }
+    return MCS_OK;
+  });
+}
+
+int mcs_profile_read(mcs_handle* h, mcs_kernel_stat* out, int max_n) {
+  return guarded([&]() -> int {
+    if (!h || !out || max_n < 0) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    if (!h->prof) return 0;
+    h->prof->collect();
+    static const char* names[PROF_NCLASS] = {"condense", "facet_blocks", "apply_K", "facet_gs_step",
+                                             "facet_residual", "elem_prologue", "elem_epilogue", "gmg_vcycle"};
+    int n = 0;
+    for (int c = 0; c < PROF_NCLASS && n < max_n; ++c) {
+      mcs_kernel_stat& o = out[n++];
+      std::memset(&o, 0, sizeof(o));
+      std::strncpy(o.name, names[c], sizeof(o.name) - 1);
+      o.launches = h->prof->launches[c];
+      o.total_ms = h->prof->ms[c];
+      o.bytes = h->prof->bytes[c];
+      o.flops = h->prof->flops[c];
+    }
+    return n;
   });
 }
 

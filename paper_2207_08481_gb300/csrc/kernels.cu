@@ -4,6 +4,7 @@
 #include <cstdio>
 
 #include "kernels.h"
+#include "profiler.h"
 
 namespace mcs {
 
@@ -14,50 +15,49 @@ struct WarpSync {
 };
 
 // ============================================================================ condensation
-// One warp per element (grid-stride).  Workspace in dynamic shared memory when it
-// fits, else in a global scratch slot per resident warp.
+struct BlockSync {
+  __device__ void operator()() const { __syncthreads(); }
+};
+
+// One thread block per element (grid-stride).  Workspace in dynamic shared memory when
+// it fits, else in a global scratch slot per resident block.
 template <class R, bool SMEM>
-__global__ void __launch_bounds__(128) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, double* AT, R* Ad,
+__global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, double* AT, R* Ad,
                                                   R* G, R* Aoi, double* gscratch, int64_t slot_doubles) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * wpb + wib, nw = (int64_t)gridDim.x * wpb;
-  double* base = SMEM ? smem + (int64_t)wib * slot_doubles : gscratch + gw * slot_doubles;
+  const int lane = threadIdx.x, nl = blockDim.x;
+  double* base = SMEM ? smem : gscratch + (int64_t)blockIdx.x * slot_doubles;
   ElemWork w = elem_work_carve(s, base);
-  double* bw = base + elem_work_doubles(s);         // bubble work
-  double* Xs = bw + s.n_bub * s.n_bub + s.n_bub * s.n_c;  // (d+1)*d coords
+  double* bw = base + elem_work_doubles(s);                // bubble work
+  double* Xs = bw + s.n_bub * s.n_bub + s.n_bub * s.n_c;   // (d+1)*d coords
   int* sg = (int*)(Xs + 16);
-  double* Adt = Xs + 24;                            // n_c*n_c + n_bub*n_c + n_bub*n_bub staging (FP64)
+  double* Adt = Xs + 24;                                   // staging (FP64)
   double* Gt = Adt + s.n_c * s.n_c;
   double* Ait = Gt + s.n_bub * s.n_c;
   ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat};
   const int d = s.d;
-  for (int64_t T = gw; T < m.ne; T += nw) {
+  for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) {
     if (lane < (d + 1) * d) {
       int v = lane / d, a = lane % d;
       Xs[lane] = m.coords[(int64_t)m.elems[T * (d + 1) + v] * d + a];
     }
     if (lane <= d) sg[lane] = m.signs[T * (d + 1) + lane];
-    __syncwarp();
-    condense_element(s, et, Xs, sg, nu, w, lane, MCS_WARP, WarpSync());
-    // packed lower triangle of A_T (FP64)
+    __syncthreads();
+    condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
+    // full A_T (FP64, symmetric: row-major = column-major)
     const int nA = s.n_A;
-    const int64_t np = (int64_t)nA * (nA + 1) / 2;
-    double* out = AT + T * np;
-    for (int64_t q = lane; q < np; q += MCS_WARP) {
-      int i = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
-      while ((int64_t)i * (i + 1) / 2 > q) --i;
-      while ((int64_t)(i + 1) * (i + 2) / 2 <= q) ++i;
-      int j = (int)(q - (int64_t)i * (i + 1) / 2);
-      out[q] = w.A[i * nA + j];
-    }
-    __syncwarp();
-    bubble_condense(s, w.A, bw, Adt, Gt, Ait, lane, MCS_WARP, WarpSync());
+    double* out = AT + T * (int64_t)nA * nA;
+    for (int q = lane; q < nA * nA; q += nl) out[q] = w.A[q];
+    __syncthreads();
+    bubble_condense(s, w.A, bw, Adt, Gt, Ait, lane, nl, BlockSync());
     const int nc = s.n_c, no = s.n_bub;
-    for (int q = lane; q < nc * nc; q += MCS_WARP) Ad[T * nc * nc + q] = (R)Adt[q];
-    for (int q = lane; q < no * nc; q += MCS_WARP) G[T * no * nc + q] = (R)Gt[q];
-    for (int q = lane; q < no * no; q += MCS_WARP) Aoi[T * no * no + q] = (R)Ait[q];
-    __syncwarp();
+    for (int q = lane; q < nc * nc; q += nl) {
+      int i = q / nc, c = q % nc;   // row i = f*mF + t
+      Ad[adw_index(d + 1, slab_pad(s), s.mF, T, i / s.mF, c, i % s.mF)] = (R)Adt[q];
+    }
+    for (int q = lane; q < no * nc; q += nl) G[T * g_stride(s) + q] = (R)Gt[q];
+    for (int q = lane; q < no * no; q += nl) Aoi[T * a_stride(s) + q] = (R)Ait[q];
+    __syncthreads();
   }
 }
 
@@ -67,6 +67,8 @@ static int64_t condense_slot_doubles(const ElemSizes& s) {
   return (v + 31) / 32 * 32;
 }
 
+static int condense_threads(const ElemSizes& s) { return s.d == 2 ? 128 : 256; }
+
 template <class R>
 cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, double* AT, R* Ad,
                             R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st) {
@@ -75,31 +77,34 @@ cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMes
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int64_t bytes_per_warp = slot * 8;
-  if (bytes_per_warp * 1 <= maxsm) {
-    int wpb = 4;
-    while (wpb > 1 && bytes_per_warp * wpb > maxsm) wpb >>= 1;
-    size_t sm = (size_t)(bytes_per_warp * wpb);
+  const int threads = condense_threads(s);
+  const int64_t bytes = slot * 8;
+  prof_begin(PROF_CONDENSE, st);
+  if (bytes <= maxsm) {
+    size_t sm = (size_t)bytes;
     cudaFuncSetAttribute(k_condense<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense<R, true>, wpb * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense<R, true>, threads, sm);
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)nsm * per_sm;
-    int64_t need = (m.ne + wpb - 1) / wpb;
-    if (blocks > need) blocks = need;
-    k_condense<R, true><<<(unsigned)blocks, wpb * 32, sm, st>>>(s, t, m, nu, AT, Ad, G, Aoi, nullptr, slot);
+    if (blocks > m.ne) blocks = m.ne;
+    k_condense<R, true><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, nu, AT, Ad, G, Aoi, nullptr, slot);
   } else {
-    int64_t slots = scratch_doubles / slot;
-    if (slots < 1) return cudaErrorMemoryAllocation;
-    int wpb = 4;
-    int64_t blocks = slots / wpb;
-    if (blocks < 1) {
-      wpb = 1;
-      blocks = slots;
-    }
-    int64_t need = (m.ne + wpb - 1) / wpb;
-    if (blocks > need) blocks = need;
-    k_condense<R, false><<<(unsigned)blocks, wpb * 32, 0, st>>>(s, t, m, nu, AT, Ad, G, Aoi, scratch, slot);
+    int64_t blocks = scratch_doubles / slot;
+    if (blocks < 1) return cudaErrorMemoryAllocation;
+    if (blocks > m.ne) blocks = m.ne;
+    k_condense<R, false><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, nu, AT, Ad, G, Aoi, scratch, slot);
+  }
+  {
+    // FP64 flops of the element condensation (products and factorisations, see element.cuh)
+    const double nA = s.n_A, nr = s.n_raw, nc = s.n_cc, no = s.n_bub, ncp = s.n_c;
+    const double f = 2.0 * (nA * (nA + 1) / 2 * nr + nc * nA * nr + nc * (nc + 1) / 2 * nr + nc * nc * nc / 6 +
+                            nc * nc * nA / 2 + nA * (nA + 1) / 2 * nc + no * no * no / 6 + no * no * ncp +
+                            ncp * ncp * no + no * no * no) +
+                     2.0 * nA * nr * s.n_s0;
+    const double out = (double)m.ne * (nA * nA * 8 + (double)((s.d + 1) * slab_pad(s) + g_stride(s) + a_stride(s)) *
+                                                         sizeof(R));
+    prof_end(PROF_CONDENSE, out, f * (double)m.ne, st);
   }
   return cudaGetLastError();
 }
@@ -123,7 +128,7 @@ __global__ void k_facet_blocks(ElemSizes s, DevMesh m, const R* Ad, R* Dinv) {
       for (int side = 0; side < 2; ++side) {
         int64_t T = m.fel[r * 2 + side];
         int f = m.floc[r * 2 + side];
-        v += (double)Ad[T * nc * nc + (int64_t)(f * mF + i) * nc + f * mF + j];
+        v += (double)Ad[adw_index(s.d + 1, slab_pad(s), mF, T, f, f * mF + j, i)];
       }
       A[q] = v;
       I[q] = (i == j) ? 1.0 : 0.0;
@@ -168,13 +173,15 @@ cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, const R* A
   cudaFuncSetAttribute(k_facet_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int64_t blocks = (m.nint + wpb - 1) / wpb;
   if (blocks > 65535 * 8) blocks = 65535 * 8;
+  prof_begin(PROF_FACET_BLOCKS, st);
   k_facet_blocks<R><<<(unsigned)blocks, wpb * 32, sm, st>>>(s, m, Ad, Dinv);
+  prof_end(PROF_FACET_BLOCKS, (double)m.nint * (2.0 * s.mF * s.mF + s.mF * s.mF) * sizeof(R), 0.0, st);
   return cudaGetLastError();
 }
 
 // ============================================================================ K apply (FP64)
-__device__ __forceinline__ int64_t local_to_global(const ElemSizes& s, const Layout& L, const int32_t* er, int64_t T,
-                                                   int i) {
+template <class S>
+__device__ __forceinline__ int64_t local_to_global(const S& s, const Layout& L, const int32_t* er, int64_t T, int i) {
   // local A index (u_d (f, j) | u_o | uhat (f, t)) -> global index, -1 if on a Dirichlet facet
   const int nfd = (s.d + 1) * s.nF;
   if (i < nfd) {
@@ -188,60 +195,88 @@ __device__ __forceinline__ int64_t local_to_global(const ElemSizes& s, const Lay
   return rk < 0 ? -1 : L.off_h + (int64_t)rk * s.nhF + (q - f * s.nhF);
 }
 
-__global__ void __launch_bounds__(128) k_apply_K(ElemSizes s, DevTables t, DevMesh m, Layout L, const double* AT,
-                                                 const double* x, double* y, const int* stop) {
+// y = K x element by element: the blocks A_T of EB elements are staged in shared memory with
+// coalesced loads (full symmetric storage), then one thread per row forms the product.
+template <class S>
+__global__ void __launch_bounds__(256) k_apply_K(S s, DevTables t, DevMesh m, Layout L,
+                                                 const double* __restrict__ AT, const double* __restrict__ x,
+                                                 double* y, int EB, const int* stop) {
   if (stop && *stop) return;
   extern __shared__ double sk[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d;
-  const int64_t npk = (int64_t)nA * (nA + 1) / 2;
-  double* A = sk + (int64_t)wib * (npk + 2 * nA + np_ + 8);
-  double* xa = A + npk;
-  double* ya = xa + nA;
-  double* xp = ya + nA;
-  int* er = (int*)(xp + np_);
-  for (int64_t T = (int64_t)blockIdx.x * wpb + wib; T < m.ne; T += (int64_t)gridDim.x * wpb) {
-    const double* src = AT + T * npk;
-    for (int64_t q = lane; q < npk; q += 32) A[q] = src[q];
-    if (lane <= d) er[lane] = m.elem_rank[T * (d + 1) + lane];
-    __syncwarp();
-    for (int i = lane; i < nA; i += 32) {
-      int64_t g = local_to_global(s, L, er, T, i);
-      xa[i] = g < 0 ? 0.0 : x[g];
+  const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d, nfd = (s.d + 1) * s.nF;
+  const int per = nA + np_, nA2 = nA * nA;
+  double* As = sk;                   // [EB][nA*nA]
+  double* xs = As + EB * nA2;        // [EB][nA + np]
+  int* er = (int*)(xs + EB * per);   // [EB][4]
+  float* sg = (float*)(er + EB * 4); // [EB][4]
+  const int tid = threadIdx.x;
+  const int64_t T0 = (int64_t)blockIdx.x * EB;
+  const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
+  if (tid < EB * 4) {
+    int e = tid >> 2, f = tid & 3;
+    int64_t T = T0 + e;
+    bool ok = e < nvalid && f <= d;
+    er[tid] = ok ? m.elem_rank[T * (d + 1) + f] : -1;
+    sg[tid] = ok ? (float)m.signs[T * (d + 1) + f] : 0.f;
+  }
+  {
+    const double2* src = reinterpret_cast<const double2*>(AT + T0 * nA2);
+    double2* dst = reinterpret_cast<double2*>(As);
+    const int cnt = nvalid * nA2;
+    if ((nA2 & 1) == 0) {
+      for (int q = tid; q < cnt / 2; q += blockDim.x) dst[q] = src[q];
+    } else {
+      for (int q = tid; q < cnt; q += blockDim.x) As[q] = AT[T0 * nA2 + q];
     }
-    for (int j = lane; j < np_; j += 32) xp[j] = x[L.off_p + T * np_ + j];
-    __syncwarp();
-    // B = -Bhat diag(sign) on the u columns
-    for (int i = lane; i < nA; i += 32) {
-      double v = 0;
-      for (int j = 0; j < nA; ++j) {
-        int64_t q = (i >= j) ? (int64_t)i * (i + 1) / 2 + j : (int64_t)j * (j + 1) / 2 + i;
-        v += A[q] * xa[j];
+  }
+  __syncthreads();
+  for (int q = tid; q < nvalid * per; q += blockDim.x) {
+    const int e = q / per, i = q - e * per;
+    const int64_t T = T0 + e;
+    double v;
+    if (i < nA) {
+      int64_t g = local_to_global(s, L, er + e * 4, T, i);
+      v = g < 0 ? 0.0 : x[g];
+    } else {
+      v = x[L.off_p + T * np_ + (i - nA)];
+    }
+    xs[q] = v;
+  }
+  __syncthreads();
+  for (int q = tid; q < nvalid * per; q += blockDim.x) {
+    const int e = q / per, i = q - e * per;
+    const int64_t T = T0 + e;
+    const double* xe = xs + e * per;
+    if (i < nA) {
+      const double* A = As + e * nA2 + i;
+      double v0 = 0.0, v1 = 0.0;
+      int j = 0;
+#pragma unroll 8
+      for (; j + 1 < nA; j += 2) {
+        v0 += A[j * nA] * xe[j];
+        v1 += A[(j + 1) * nA] * xe[j + 1];
       }
+      if (j < nA) v0 += A[j * nA] * xe[j];
+      double v = v0 + v1;
       if (i < nu_) {
-        double sgn = (i < (d + 1) * s.nF) ? (double)m.signs[T * (d + 1) + i / s.nF] : 1.0;
-        double bt = 0;
-        for (int j = 0; j < np_; ++j) bt += t.Bp[j * nu_ + i] * xp[j];
+        double sgn = i < nfd ? (double)sg[e * 4 + i / s.nF] : 1.0;
+        double bt = 0.0;
+        for (int p = 0; p < np_; ++p) bt += t.Bp[p * nu_ + i] * xe[nA + p];
         v -= sgn * bt;
       }
-      ya[i] = v;
-    }
-    for (int j = lane; j < np_; j += 32) {
-      double v = 0;
-      for (int i = 0; i < nu_; ++i) {
-        double sgn = (i < (d + 1) * s.nF) ? (double)m.signs[T * (d + 1) + i / s.nF] : 1.0;
-        v += t.Bp[j * nu_ + i] * sgn * xa[i];
-      }
-      y[L.off_p + T * np_ + j] = -v;
-    }
-    __syncwarp();
-    for (int i = lane; i < nA; i += 32) {
-      int64_t g = local_to_global(s, L, er, T, i);
+      int64_t g = local_to_global(s, L, er + e * 4, T, i);
       if (g < 0) continue;
-      if (i >= (d + 1) * s.nF && i < nu_) y[g] = ya[i];   // bubble: owned by T
-      else atomicAdd(&y[g], ya[i]);                       // facet dof: exactly two contributions into 0
+      if (i >= nfd && i < nu_) y[g] = v;     // bubble: owned by T
+      else atomicAdd(&y[g], v);             // facet dof: exactly two contributions into 0
+    } else {
+      const int jp = i - nA;
+      double v = 0.0;
+      for (int c = 0; c < nu_; ++c) {
+        double sgn = c < nfd ? (double)sg[e * 4 + c / s.nF] : 1.0;
+        v += t.Bp[jp * nu_ + c] * sgn * xe[c];
+      }
+      y[L.off_p + T * np_ + jp] = -v;
     }
-    __syncwarp();
   }
 }
 
@@ -266,26 +301,26 @@ static int sm_count() {
 cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
                            const double* AT, const double* x, double* y, const int* stop, cudaStream_t st) {
   k_zero_facet<<<sm_count() * 4, 256, 0, st>>>(L, y, stop);
-  static int maxsm = 0;
-  if (!maxsm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  }
-  int wpb = 4;
-  const int64_t npk = (int64_t)s.n_A * (s.n_A + 1) / 2;
-  const int64_t per_warp = (npk + 2 * s.n_A + s.n_p + 8) * (int64_t)sizeof(double);
-  while (wpb > 1 && per_warp * wpb > maxsm) wpb >>= 1;
-  if (per_warp > maxsm) return cudaErrorInvalidConfiguration;
-  size_t sm = (size_t)(per_warp * wpb);
-  cudaFuncSetAttribute(k_apply_K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_K, wpb * 32, sm);
-  if (per < 1) per = 1;
-  int64_t blocks = (int64_t)sm_count() * per;
-  int64_t need = (m.ne + wpb - 1) / wpb;
-  if (blocks > need) blocks = need;
-  k_apply_K<<<(unsigned)blocks, wpb * 32, sm, st>>>(s, t, m, L, AT, x, y, stop);
+  const int per = s.n_A + s.n_p;
+  const size_t per_bytes = ((size_t)s.n_A * s.n_A + per) * sizeof(double) + 4 * (sizeof(int) + sizeof(float));
+  int EB = (int)((40 * 1024) / per_bytes);
+  if (EB < 1) EB = 1;
+  if (EB > 16) EB = 16;
+  const int threads = EB * per <= 128 ? 128 : 256;
+  size_t sm = (size_t)EB * per_bytes + 64;
+  int64_t blocks = (m.ne + EB - 1) / EB;
+  dispatch_sizes(s, [&](auto sz) {
+    static bool set = false;
+    if (!set) {
+      cudaFuncSetAttribute(k_apply_K<decltype(sz)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set = true;
+    }
+    prof_begin(PROF_APPLY, st);
+    k_apply_K<decltype(sz)><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, AT, x, y, EB, stop);
+    // algorithmic: packed symmetric A_T, x read once, y written once; flops: full row products
+    prof_end(PROF_APPLY, (double)m.ne * s.n_A * (s.n_A + 1) / 2 * 8.0 + 16.0 * L.ndof,
+             2.0 * (double)m.ne * ((double)s.n_A * s.n_A + 2.0 * s.n_u * s.n_p), st);
+  });
   return cudaGetLastError();
 }
 
@@ -395,13 +430,13 @@ cudaError_t launch_load(const ElemSizes& s, const DevTables& t, const DevMesh& m
 
 // ============================================================================ preconditioner (precision R)
 // gather the coupling vector x_T (facet-major) of element T from an external-layout vector
-template <class R>
-__device__ __forceinline__ R coup_get(const ElemSizes& s, const Layout& L, const R* x, int32_t rk, int t) {
+template <class R, class S>
+__device__ __forceinline__ R coup_get(const S& s, const Layout& L, const R* x, int32_t rk, int t) {
   if (rk < 0) return (R)0;
   return (t < s.nF) ? x[(int64_t)rk * s.nF + t] : x[L.off_h + (int64_t)rk * s.nhF + (t - s.nF)];
 }
-template <class R>
-__device__ __forceinline__ int64_t coup_idx(const ElemSizes& s, const Layout& L, int32_t rk, int t) {
+template <class R, class S>
+__device__ __forceinline__ int64_t coup_idx(const S& s, const Layout& L, int32_t rk, int t) {
   return (t < s.nF) ? (int64_t)rk * s.nF + t : L.off_h + (int64_t)rk * s.nhF + (t - s.nF);
 }
 
@@ -420,102 +455,240 @@ __global__ void k_from_R(int64_t n, const R* a, double* b, const int* stop) {
     b[i] = (double)a[i];
 }
 
-// tb[c] = sum_T (G_T^T r_o)_c over the coupling dofs (two contributions each, into zero)
+// Copy n entries (n * sizeof(R) a multiple of 16, both pointers 16-byte aligned) with 16-byte loads.
 template <class R>
-__global__ void k_bubble_elim(ElemSizes s, DevMesh m, Layout L, const R* G, const R* r, R* tb, const int* stop) {
-  if (stop && *stop) return;
-  const int d = s.d, nc = s.n_c, no = s.n_bub;
-  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < m.ne * nc;
-       id += (int64_t)gridDim.x * blockDim.x) {
-    int64_t T = id / nc;
-    int c = (int)(id % nc);
-    int f = c / s.mF, tt = c % s.mF;
-    int32_t rk = m.elem_rank[T * (d + 1) + f];
-    if (rk < 0) continue;
-    const R* g = G + T * no * nc;
-    const R* ro = r + L.off_o + T * no;
-    R v = 0;
-    for (int o = 0; o < no; ++o) v += g[o * nc + c] * ro[o];
-    atomicAdd(&tb[coup_idx<R>(s, L, rk, tt)], v);
-  }
+__device__ __forceinline__ void vcopy16(R* dst, const R* __restrict__ src, int n, int tid, int nth) {
+  const int nv = n * (int)sizeof(R) / 16;
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  const uint4* sv = reinterpret_cast<const uint4*>(src);
+  for (int i = tid; i < nv; i += nth) d[i] = sv[i];
 }
 
-// x_o = Aoo^{-1} r_o - G x_c
-template <class R>
-__global__ void k_bubble_back(ElemSizes s, DevMesh m, Layout L, const R* G, const R* Aoi, const R* r, R* x,
-                              const int* stop) {
-  if (stop && *stop) return;
-  const int d = s.d, nc = s.n_c, no = s.n_bub;
-  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < m.ne * no;
-       id += (int64_t)gridDim.x * blockDim.x) {
-    int64_t T = id / no;
-    int o = (int)(id % no);
-    const R* ai = Aoi + T * no * no + o * no;
-    const R* ro = r + L.off_o + T * no;
-    R v = 0;
-    for (int p = 0; p < no; ++p) v += ai[p] * ro[p];
-    const R* g = G + T * no * nc + o * nc;
-    for (int c = 0; c < nc; ++c) {
-      int f = c / s.mF;
-      int32_t rk = m.elem_rank[T * (d + 1) + f];
-      v -= g[c] * coup_get<R>(s, L, x, rk, c % s.mF);
-    }
-    x[L.off_o + T * no + o] = v;
-  }
-}
-
-// Facet-centric block step: for facets in `list`, r_F = b_F - tb_F - sum_T (Ad_T x_T)|_F;
-// UPDATE: x_F += Dinv_F r_F; else rr_F = r_F.
-template <class R, bool UPDATE>
-__global__ void __launch_bounds__(128) k_facet_step(ElemSizes s, DevMesh m, Layout L, const R* Ad, const R* Dinv,
-                                                    const R* b, const R* tb, R* x, R* rr, const int32_t* list,
-                                                    int64_t nlist, const int* stop) {
+// ---------------------------------------------------------------- element-level preconditioner kernels
+// Prologue of one Ahat^{-1} application (bubble elimination, eq. factorSsigma):
+//   rin_o = r_o - (B^T z_p)_o                          (WITH_BT; else rin_o = r_o)
+//   tb   += (B^T z_p)_c + (G^T rin_o)_c                 (two contributions per facet dof, into zero)
+// B = -Bhat diag(sign) (reading R18), z_p read from zp (pressure layout of the full vector).
+template <class R, class S, bool WITH_BT>
+__global__ void __launch_bounds__(256) k_elem_prologue(S s, DevTables t, DevMesh m, Layout L,
+                                                       const R* __restrict__ G, const R* __restrict__ r,
+                                                       const R* __restrict__ zp, R* rin, R* tb, int EB,
+                                                       const int* stop) {
   if (stop && *stop) return;
   extern __shared__ unsigned char sraw[];
-  R* sh = (R*)sraw;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int d = s.d, nc = s.n_c, mF = s.mF;
-  R* xT = sh + (int64_t)wib * (nc + 2 * mF);
-  R* rF = xT + nc;
-  R* yF = rF + mF;
-  for (int64_t li = (int64_t)blockIdx.x * wpb + wib; li < nlist; li += (int64_t)gridDim.x * wpb) {
-    const int64_t r = list ? list[li] : li;
-    for (int t = lane; t < mF; t += 32) {
-      int64_t g = coup_idx<R>(s, L, (int32_t)r, t);
-      rF[t] = b[g] - (tb ? tb[g] : (R)0);
-    }
-    for (int side = 0; side < 2; ++side) {
-      const int64_t T = m.fel[r * 2 + side];
-      const int f = m.floc[r * 2 + side];
-      __syncwarp();
-      for (int c = lane; c < nc; c += 32) {
-        int ff = c / mF;
-        xT[c] = coup_get<R>(s, L, x, m.elem_rank[T * (d + 1) + ff], c % mF);
-      }
-      __syncwarp();
-      const R* A = Ad + T * nc * nc + (int64_t)f * mF * nc;
-      // each row t: lanes split the dot product
-      for (int t = 0; t < mF; ++t) {
+  const int d = s.d, nc = s.n_c, no = s.n_bub, nu_ = s.n_u, np_ = s.n_p, nfd = (s.d + 1) * s.nF;
+  const int gs = g_stride(s);
+  R* Gs = (R*)sraw;              // [EB][gs]
+  R* ro = Gs + EB * gs;          // [EB][no]
+  R* bt = ro + EB * no;          // [EB][nu]
+  R* zz = bt + EB * nu_;         // [EB][np]
+  const int64_t T0 = (int64_t)blockIdx.x * EB;
+  const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
+  const int tid = threadIdx.x;
+  vcopy16<R>(Gs, G + T0 * gs, nvalid * gs, tid, blockDim.x);
+  for (int q = tid; q < nvalid * no; q += blockDim.x) ro[q] = r[L.off_o + T0 * no + q];
+  if (WITH_BT)
+    for (int q = tid; q < nvalid * np_; q += blockDim.x) zz[q] = zp[L.off_p + T0 * np_ + q];
+  __syncthreads();
+  if (WITH_BT) {
+    for (int e = 0; e < nvalid; ++e) {
+      const int64_t T = T0 + e;
+      for (int i = tid; i < nu_; i += blockDim.x) {
+        R sg = i < nfd ? (R)m.signs[T * (d + 1) + i / s.nF] : (R)1;
         R v = 0;
-        for (int c = lane; c < nc; c += 32) v += A[(int64_t)t * nc + c] * xT[c];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) rF[t] -= v;
+        for (int j = 0; j < np_; ++j) v += (R)t.Bp[j * nu_ + i] * zz[e * np_ + j];
+        bt[e * nu_ + i] = -sg * v;
       }
     }
-    __syncwarp();
-    if (UPDATE) {
-      const R* Di = Dinv + r * mF * mF;
-      for (int t = lane; t < mF; t += 32) {
-        R v = 0;
-        for (int j = 0; j < mF; ++j) v += Di[t * mF + j] * rF[j];
-        yF[t] = v;
+    __syncthreads();
+    for (int e = 0; e < nvalid; ++e)
+      for (int o = tid; o < no; o += blockDim.x) ro[e * no + o] -= bt[e * nu_ + nfd + o];
+    __syncthreads();
+  }
+  for (int q = tid; q < nvalid * no; q += blockDim.x) rin[L.off_o + T0 * no + q] = ro[q];
+  for (int e = 0; e < nvalid; ++e) {
+    const int64_t T = T0 + e;
+    for (int c = tid; c < nc; c += blockDim.x) {
+      const int f = c / s.mF, tt = c - f * s.mF;
+      const int32_t rk = m.elem_rank[T * (d + 1) + f];
+      if (rk < 0) continue;
+      R v = 0;
+      const R* g = Gs + e * gs + c;
+      const R* rv = ro + e * no;
+#pragma unroll 4
+      for (int o = 0; o < no; ++o) v += g[o * nc] * rv[o];
+      if (WITH_BT && tt < s.nF) v += bt[e * nu_ + f * s.nF + tt];
+      atomicAdd(&tb[coup_idx<R>(s, L, rk, tt)], v);
+    }
+  }
+}
+
+// Epilogue of one Ahat^{-1} application (back substitution, eq. factorSsigma):
+//   x_o = A_oo^{-1} rin_o - G x_c
+// WITH_P (first application of eq. mhatinvfactor): also z_p = Shat_p^{-1}(r_p - B a), a = (x_c, x_o),
+// Shat_p = M_p = nu^{-1}(p, q)  ->  z_p = nu/|det J| (r_p - B a).
+template <class R, class S, bool WITH_P>
+__global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh m, Layout L, double nu,
+                                                       const R* __restrict__ G, const R* __restrict__ Aoi,
+                                                       const R* __restrict__ rin, const R* __restrict__ r, R* x,
+                                                       R* zp, int EB, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ unsigned char sraw[];
+  const int d = s.d, nc = s.n_c, no = s.n_bub, nu_ = s.n_u, np_ = s.n_p, nfd = (s.d + 1) * s.nF, mF = s.mF;
+  const int gs = g_stride(s), as_ = a_stride(s);
+  R* Gs = (R*)sraw;              // [EB][gs]
+  R* As = Gs + EB * gs;          // [EB][as]
+  R* xc = As + EB * as_;         // [EB][nc]
+  R* ro = xc + EB * nc;          // [EB][no]
+  R* xo = ro + EB * no;          // [EB][no]
+  const int64_t T0 = (int64_t)blockIdx.x * EB;
+  const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
+  const int tid = threadIdx.x;
+  vcopy16<R>(Gs, G + T0 * gs, nvalid * gs, tid, blockDim.x);
+  vcopy16<R>(As, Aoi + T0 * as_, nvalid * as_, tid, blockDim.x);
+  for (int q = tid; q < nvalid * no; q += blockDim.x) ro[q] = rin[L.off_o + T0 * no + q];
+  for (int e = 0; e < nvalid; ++e) {
+    const int64_t T = T0 + e;
+    for (int c = tid; c < nc; c += blockDim.x) {
+      const int f = c / mF;
+      xc[e * nc + c] = coup_get<R>(s, L, x, m.elem_rank[T * (d + 1) + f], c - f * mF);
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < nvalid * no; q += blockDim.x) {
+    const int e = q / no, o = q - e * no;
+    R v = 0;
+    const R* a = As + e * as_ + o * no;
+    const R* rv = ro + e * no;
+#pragma unroll 4
+    for (int p = 0; p < no; ++p) v += a[p] * rv[p];
+    const R* g = Gs + e * gs + o * nc;
+    const R* xv = xc + e * nc;
+#pragma unroll 4
+    for (int c = 0; c < nc; ++c) v -= g[c] * xv[c];
+    xo[q] = v;
+    x[L.off_o + T0 * no + q] = v;
+  }
+  if (WITH_P) {
+    __syncthreads();
+    for (int q = tid; q < nvalid * np_; q += blockDim.x) {
+      const int e = q / np_, j = q - e * np_;
+      const int64_t T = T0 + e;
+      double v = 0;  // sum_i Bhat[j][i] sign_i a_i over the velocity dofs
+      for (int i = 0; i < nu_; ++i) {
+        double ai;
+        if (i < nfd) {
+          const int f = i / s.nF;
+          ai = (double)m.signs[T * (d + 1) + f] * (double)xc[e * nc + f * mF + (i - f * s.nF)];
+        } else {
+          ai = (double)xo[e * no + i - nfd];
+        }
+        v += t.Bp[j * nu_ + i] * ai;
       }
-      __syncwarp();
-      for (int t = lane; t < mF; t += 32) x[coup_idx<R>(s, L, (int32_t)r, t)] += yF[t];
+      const int64_t gp = L.off_p + T * np_ + j;
+      zp[gp] = (R)(nu / m.adet[T] * ((double)r[gp] + v));
+    }
+  }
+}
+
+// Facet-centric block step: for facets in `list` (interior ranks; NULL = all),
+//   r_F = b_F - tb_F - sum_{T in F} (A^d_T x_T)|_F,
+// UPDATE: x_F += D_F^{-1} r_F (block Gauss-Seidel within one colour); else rr_F = r_F.
+// FB facets per block: the A^d slabs of both sides are staged in shared memory (one warp per
+// slab, coalesced), then one thread per (facet, side, row) forms the product.
+template <class R, class S, bool UPDATE>
+__global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, const R* __restrict__ Ad,
+                                                    const R* __restrict__ Dinv, const R* __restrict__ b,
+                                                    const R* __restrict__ tb, R* x, R* rr,
+                                                    const int32_t* __restrict__ list, int64_t nlist, int FB,
+                                                    const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ unsigned char sraw[];
+  const int d = s.d, nc = s.n_c, mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s);
+  R* As = (R*)sraw;                  // [FB][2][slab]
+  R* xT = As + FB * 2 * slab;        // [FB][2][nc]
+  R* yS = xT + FB * 2 * nc;          // [FB][2][mF]
+  R* rF = yS + FB * 2 * mF;          // [FB][mF]
+  int* rk = (int*)(rF + FB * mF);    // [FB]
+  int* TT = rk + FB;                 // [FB][2]
+  int* ff = TT + 2 * FB;             // [FB][2]
+  const int64_t base = (int64_t)blockIdx.x * FB;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  if (tid < FB) {
+    int64_t li = base + tid;
+    int r = -1;
+    if (li < nlist) r = list ? list[li] : (int)li;
+    rk[tid] = r;
+    if (r >= 0) {
+      TT[2 * tid] = m.fel[2 * r];
+      TT[2 * tid + 1] = m.fel[2 * r + 1];
+      ff[2 * tid] = m.floc[2 * r];
+      ff[2 * tid + 1] = m.floc[2 * r + 1];
+    }
+  }
+  __syncthreads();
+  // stage the slabs: warp w copies slab fs = w, w + nwarp, ...
+  for (int fs = warp; fs < FB * 2; fs += nwarp) {
+    const int fb = fs >> 1, side = fs & 1;
+    R* dst = As + fs * slab;
+    if (rk[fb] >= 0) {
+      const R* src = Ad + adw_index(dp1, slab, mF, TT[2 * fb + side], ff[2 * fb + side], 0, 0);
+      vcopy16<R>(dst, src, slab, lane, 32);
     } else {
-      for (int t = lane; t < mF; t += 32) rr[coup_idx<R>(s, L, (int32_t)r, t)] = rF[t];
+      for (int idx = lane; idx < slab; idx += 32) dst[idx] = (R)0;
     }
-    __syncwarp();
+  }
+  // gather x_T of both sides: warp per (facet, side)
+  for (int fs = warp; fs < FB * 2; fs += nwarp) {
+    const int fb = fs >> 1, side = fs & 1;
+    const int r = rk[fb];
+    for (int c = lane; c < nc; c += 32) {
+      R v = 0;
+      if (r >= 0) {
+        const int f = c / mF;
+        const int32_t g = m.fsr[((int64_t)r * 2 + side) * dp1 + f];
+        v = coup_get<R>(s, L, x, g, c - f * mF);
+      }
+      xT[fs * nc + c] = v;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < FB * 2 * mF; q += blockDim.x) {
+    const int fs = q / mF, t = q - fs * mF;
+    const R* A = As + fs * slab + t;
+    const R* xv = xT + fs * nc;
+    R v0 = 0, v1 = 0;
+    int c = 0;
+#pragma unroll 4
+    for (; c + 1 < nc; c += 2) {
+      v0 += A[c * mF] * xv[c];
+      v1 += A[(c + 1) * mF] * xv[c + 1];
+    }
+    if (c < nc) v0 += A[c * mF] * xv[c];
+    yS[q] = v0 + v1;
+  }
+  __syncthreads();
+  for (int q = tid; q < FB * mF; q += blockDim.x) {
+    const int fb = q / mF, t = q - fb * mF;
+    const int r = rk[fb];
+    if (r < 0) continue;
+    const int64_t gi = coup_idx<R>(s, L, r, t);
+    R v = b[gi] - (tb ? tb[gi] : (R)0) - yS[(fb * 2) * mF + t] - yS[(fb * 2 + 1) * mF + t];
+    if (UPDATE) rF[q] = v;
+    else rr[gi] = v;
+  }
+  if (UPDATE) {
+    __syncthreads();
+    for (int q = tid; q < FB * mF; q += blockDim.x) {
+      const int fb = q / mF, t = q - fb * mF;
+      const int r = rk[fb];
+      if (r < 0) continue;
+      const R* Di = Dinv + (int64_t)r * mF * mF + t * mF;
+      const R* rv = rF + fb * mF;
+      R v = 0;
+      for (int j = 0; j < mF; ++j) v += Di[j] * rv[j];
+      x[coup_idx<R>(s, L, r, t)] += v;
+    }
   }
 }
 
@@ -646,118 +819,135 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
                               const R* tb, R* x, R* rr, const int32_t* list, int64_t n, bool update,
                               const int* stop, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const int wpb = 4;
-  size_t sm = (size_t)wpb * (s.n_c + 2 * s.mF) * sizeof(R);
-  int64_t blocks = (n + wpb - 1) / wpb;
-  if (blocks > (int64_t)sm_count() * 16) blocks = (int64_t)sm_count() * 16;
-  if (update)
-    k_facet_step<R, true><<<(unsigned)blocks, wpb * 32, sm, st>>>(s, m, L, P.Ad, P.Dinv, b, tb, x, rr, list, n, stop);
-  else
-    k_facet_step<R, false><<<(unsigned)blocks, wpb * 32, sm, st>>>(s, m, L, P.Ad, P.Dinv, b, tb, x, rr, list, n, stop);
+  const int slab = slab_pad(s);
+  int FB = 256 / (2 * s.mF);
+  const int budget = 48 * 1024;
+  while (FB > 1 && (size_t)FB * 2 * slab * sizeof(R) > (size_t)budget) --FB;
+  if (FB < 1) FB = 1;
+  const int threads = 256;
+  size_t sm = (size_t)FB * (2 * slab + 2 * s.n_c + 2 * s.mF + s.mF) * sizeof(R) + (size_t)FB * 5 * sizeof(int) + 16;
+  int64_t blocks = (n + FB - 1) / FB;
+  dispatch_sizes(s, [&](auto sz) {
+    using SZ = decltype(sz);
+    static bool set = false;
+    if (!set) {
+      cudaFuncSetAttribute(k_facet_step<R, SZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(k_facet_step<R, SZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set = true;
+    }
+    const int cls = update ? PROF_FACET_GS : PROF_FACET_RES;
+    prof_begin(cls, st);
+    if (update)
+      k_facet_step<R, SZ, true><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, list, n,
+                                                                        FB, stop);
+    else
+      k_facet_step<R, SZ, false><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, list, n,
+                                                                         FB, stop);
+    // algorithmic bytes per facet: the facet's rows of A^d from both elements, D_F^{-1}, b, tb,
+    // x_F read and written (update) or rr_F written (residual)
+    const double per = update ? (2.0 * s.mF * s.n_c + (double)s.mF * s.mF + 4.0 * s.mF)
+                              : (2.0 * s.mF * s.n_c + 3.0 * s.mF);
+    prof_end(cls, (double)n * per * sizeof(R), 2.0 * (double)n * (2.0 * s.mF * s.n_c + (update ? s.mF * s.mF : 0)), st);
+  });
   return cudaGetLastError();
 }
 
-// Ahat^{-1}: rin (external layout, velocity part) -> out (velocity part), precision R
+static int elem_batch(size_t per_elem_bytes) {
+  int EB = (int)((32 * 1024) / per_elem_bytes);
+  if (EB < 1) EB = 1;
+  if (EB > 32) EB = 32;
+  return EB;
+}
+
+template <class R, bool WITH_BT>
+static void elem_prologue(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, PrecData<R>& P,
+                          const R* r, const R* zp, R* rin, R* tb, const int* stop, cudaStream_t st) {
+  const size_t per = (size_t)(g_stride(s) + s.n_bub + s.n_u + s.n_p) * sizeof(R);
+  const int EB = elem_batch(per);
+  const size_t sm = per * EB + 16;
+  const int64_t blocks = (m.ne + EB - 1) / EB;
+  dispatch_sizes(s, [&](auto sz) {
+    using SZ = decltype(sz);
+    static bool set = false;
+    if (!set) {
+      cudaFuncSetAttribute(k_elem_prologue<R, SZ, WITH_BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set = true;
+    }
+    prof_begin(PROF_PROLOGUE, st);
+    k_elem_prologue<R, SZ, WITH_BT><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, P.G, r, zp, rin, tb, EB, stop);
+    prof_end(PROF_PROLOGUE, (double)m.ne * (s.n_bub * s.n_c + 2 * s.n_bub + s.n_c + (WITH_BT ? s.n_p : 0)) * sizeof(R),
+             2.0 * (double)m.ne * s.n_bub * s.n_c, st);
+  });
+}
+
+template <class R, bool WITH_P>
+static void elem_epilogue(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
+                          PrecData<R>& P, const R* rin, const R* r, R* x, R* zp, const int* stop, cudaStream_t st) {
+  const size_t per = (size_t)(g_stride(s) + a_stride(s) + s.n_c + 2 * s.n_bub) * sizeof(R);
+  const int EB = elem_batch(per);
+  const size_t sm = per * EB + 16;
+  const int64_t blocks = (m.ne + EB - 1) / EB;
+  dispatch_sizes(s, [&](auto sz) {
+    using SZ = decltype(sz);
+    static bool set = false;
+    if (!set) {
+      cudaFuncSetAttribute(k_elem_epilogue<R, SZ, WITH_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set = true;
+    }
+    prof_begin(PROF_EPILOGUE, st);
+    k_elem_epilogue<R, SZ, WITH_P><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, nu, P.G, P.Aoi, rin, r, x, zp, EB,
+                                                                       stop);
+    prof_end(PROF_EPILOGUE, (double)m.ne * (s.n_bub * s.n_c + s.n_bub * s.n_bub + 2 * s.n_bub + s.n_c +
+                                             (WITH_P ? 2 * s.n_p : 0)) * sizeof(R),
+             2.0 * (double)m.ne * (s.n_bub * s.n_c + s.n_bub * s.n_bub), st);
+  });
+}
+
+// Multiplicative ASP on A^d (Sec. 5.2 / 6.1): x_c from the right-hand side b_c - tb_c.
 template <class R>
-cudaError_t launch_ahat_inv(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* rin,
-                            R* out, const int* stop, cudaStream_t st) {
+static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* b, const R* tb,
+                     R* x, const int* stop, cudaStream_t st) {
   const int bs = 256;
   const unsigned g = (unsigned)(sm_count() * 8);
-  // tb = G^T r_o (coupling), x = 0
-  cudaMemsetAsync(P.t, 0, sizeof(R) * L.ndof, st);
-  cudaMemsetAsync(out, 0, sizeof(R) * L.off_p, st);
-  k_bubble_elim<R><<<g, bs, 0, st>>>(s, m, L, P.G, rin, P.t, stop);
+  cudaMemsetAsync(x, 0, sizeof(R) * L.n_dd, st);
+  cudaMemsetAsync(x + L.off_h, 0, sizeof(R) * L.n_hat, st);
   const int64_t* co = P.colour_off;
-  const bool mult = P.multiplicative != 0;
-  if (mult) {
-    for (int sw = 0; sw < P.smooth; ++sw)
-      for (int c = 0; c < P.ncol; ++c)
-        facet_step<R>(s, m, L, P, rin, P.t, out, nullptr, P.colour_list + co[c], co[c + 1] - co[c], true, stop, st);
-  }
-  // residual over all facets
-  facet_step<R>(s, m, L, P, rin, P.t, out, P.rr, nullptr, L.nint, false, stop, st);
-  // coarse correction: E^d C^{-1} E^d^T rr
+  for (int sw = 0; sw < P.smooth; ++sw)
+    for (int c = 0; c < P.ncol; ++c)
+      facet_step<R>(s, m, L, P, b, tb, x, nullptr, P.colour_list + co[c], co[c + 1] - co[c], true, stop, st);
+  facet_step<R>(s, m, L, P, b, tb, x, P.rr, nullptr, L.nint, false, stop, st);
   const int top = P.nlev - 1;
+  prof_begin(PROF_GMG, st);
   k_embed_T<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.vf_ptr, P.vf_idx, P.nP1, P.rr, P.pb[top], stop);
   vcycle<R>(P, top, stop, st);
-  k_embed<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.fvr, L.nint, P.px[top], out, stop);
-  if (mult) {
-    for (int sw = 0; sw < P.smooth; ++sw)
-      for (int c = P.ncol - 1; c >= 0; --c)
-        facet_step<R>(s, m, L, P, rin, P.t, out, nullptr, P.colour_list + co[c], co[c + 1] - co[c], true, stop, st);
-  }
-  k_bubble_back<R><<<g, bs, 0, st>>>(s, m, L, P.G, P.Aoi, rin, out, stop);
-  return cudaGetLastError();
+  k_embed<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.fvr, L.nint, P.px[top], x, stop);
+  prof_end(PROF_GMG, 0.0, 0.0, st);
+  for (int sw = 0; sw < P.smooth; ++sw)
+    for (int c = P.ncol - 1; c >= 0; --c)
+      facet_step<R>(s, m, L, P, b, tb, x, nullptr, P.colour_list + co[c], co[c + 1] - co[c], true, stop, st);
 }
 
-// B a  and  M_p^{-1}:  zp = (nu / |det J|) (r_p - B a),   B = -Bhat diag(sign)
-template <class R>
-__global__ void k_schur_p(ElemSizes s, DevTables t, DevMesh m, Layout L, double nu, const R* rR, const R* a, R* z,
-                          const int* stop) {
-  if (stop && *stop) return;
-  const int d = s.d, nu_ = s.n_u, np_ = s.n_p;
-  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < m.ne * np_;
-       id += (int64_t)gridDim.x * blockDim.x) {
-    int64_t T = id / np_;
-    int j = (int)(id % np_);
-    const int32_t* er = m.elem_rank + T * (d + 1);
-    double v = 0;
-    for (int i = 0; i < nu_; ++i) {
-      int64_t g = local_to_global(s, L, er, T, i);
-      if (g < 0) continue;
-      double sg = (i < (d + 1) * s.nF) ? (double)m.signs[T * (d + 1) + i / s.nF] : 1.0;
-      v += t.Bp[j * nu_ + i] * sg * (double)a[g];
-    }
-    const int64_t gp = L.off_p + T * np_ + j;
-    z[gp] = (R)(nu / m.adet[T] * ((double)rR[gp] + v));
-  }
-}
-// tt = r - B^T z_p on the velocity part (facet dofs: two contributions, computed into zero first)
-template <class R>
-__global__ void k_bt(ElemSizes s, DevTables t, DevMesh m, Layout L, const R* z, R* acc, const int* stop) {
-  if (stop && *stop) return;
-  const int d = s.d, nu_ = s.n_u, np_ = s.n_p;
-  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < m.ne * nu_;
-       id += (int64_t)gridDim.x * blockDim.x) {
-    int64_t T = id / nu_;
-    int i = (int)(id % nu_);
-    const int32_t* er = m.elem_rank + T * (d + 1);
-    int64_t g = local_to_global(s, L, er, T, i);
-    if (g < 0) continue;
-    double sg = (i < (d + 1) * s.nF) ? (double)m.signs[T * (d + 1) + i / s.nF] : 1.0;
-    double v = 0;
-    for (int j = 0; j < np_; ++j) v += t.Bp[j * nu_ + i] * (double)z[L.off_p + T * np_ + j];
-    // (B^T z)_i = -sign_i * sum_j Bhat[j][i] z_j
-    R bt = (R)(-sg * v);
-    if (i >= (d + 1) * s.nF) acc[g] = bt;
-    else atomicAdd(&acc[g], bt);
-  }
-}
-template <class R>
-__global__ void k_sub(int64_t n, const R* a, const R* b, R* c, const int* stop) {
-  if (stop && *stop) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    c[i] = a[i] - b[i];
-}
-
+// z = Khat^{-1} r (eq. mhatinvfactor, two applications of Ahat^{-1}, reading R3).
 template <class R>
 cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
                            PrecData<R>& P, const double* r, double* z, const int* stop, cudaStream_t st) {
   const int bs = 256;
   const unsigned g = (unsigned)(sm_count() * 8);
-  // rR = r in precision R  (P.b)
+  // b = r in precision R
   if (sizeof(R) == 4) k_to_R_f<<<g, bs, 0, st>>>(L.ndof, r, (float*)P.b);
   else k_to_R_d<<<g, bs, 0, st>>>(L.ndof, r, (double*)P.b);
-  // a = Ahat^{-1} r_u  -> P.zz
-  launch_ahat_inv<R>(s, m, L, P, P.b, P.zz, stop, st);
-  // zp = Sp^{-1}(r_p - B a) -> stored in P.x (p part)
-  k_schur_p<R><<<g, bs, 0, st>>>(s, t, m, L, nu, P.b, P.zz, P.x, stop);
-  // acc = B^T zp (velocity part) into P.rr (zeroed), then tt = r_u - acc -> P.zz
-  cudaMemsetAsync(P.rr, 0, sizeof(R) * L.off_p, st);
-  k_bt<R><<<g, bs, 0, st>>>(s, t, m, L, P.x, P.rr, stop);
-  k_sub<R><<<g, bs, 0, st>>>(L.off_p, P.b, P.rr, P.zz, stop);
-  // z_u = Ahat^{-1} tt -> P.x (velocity part; p part already there)
-  launch_ahat_inv<R>(s, m, L, P, P.zz, P.x, stop, st);
+  // first Ahat^{-1}: a = Ahat^{-1} r_u  (a in P.zz), then z_p = Shat_p^{-1}(r_p - B a) (P.x, p part)
+  cudaMemsetAsync(P.t, 0, sizeof(R) * L.n_dd, st);
+  cudaMemsetAsync(P.t + L.off_h, 0, sizeof(R) * L.n_hat, st);
+  elem_prologue<R, false>(s, t, m, L, P, P.b, nullptr, P.zz, P.t, stop, st);
+  asp_core<R>(s, m, L, P, P.b, P.t, P.zz, stop, st);
+  elem_epilogue<R, true>(s, t, m, L, nu, P, P.zz, P.b, P.zz, P.x, stop, st);
+  // second Ahat^{-1}: z_u = Ahat^{-1}(r_u - B^T z_p)  (P.x velocity part)
+  cudaMemsetAsync(P.t, 0, sizeof(R) * L.n_dd, st);
+  cudaMemsetAsync(P.t + L.off_h, 0, sizeof(R) * L.n_hat, st);
+  elem_prologue<R, true>(s, t, m, L, P, P.b, P.x, P.x, P.t, stop, st);
+  asp_core<R>(s, m, L, P, P.b, P.t, P.x, stop, st);
+  elem_epilogue<R, false>(s, t, m, L, nu, P, P.x, P.b, P.x, nullptr, stop, st);
   k_from_R<R><<<g, bs, 0, st>>>(L.ndof, P.x, z, stop);
   return cudaGetLastError();
 }
@@ -983,9 +1173,15 @@ template cudaError_t launch_precond<float>(const ElemSizes&, const DevTables&, c
                                            PrecData<float>&, const double*, double*, const int*, cudaStream_t);
 template cudaError_t launch_precond<double>(const ElemSizes&, const DevTables&, const DevMesh&, const Layout&, double,
                                             PrecData<double>&, const double*, double*, const int*, cudaStream_t);
-template cudaError_t launch_ahat_inv<float>(const ElemSizes&, const DevMesh&, const Layout&, PrecData<float>&,
-                                            const float*, float*, const int*, cudaStream_t);
-template cudaError_t launch_ahat_inv<double>(const ElemSizes&, const DevMesh&, const Layout&, PrecData<double>&,
-                                             const double*, double*, const int*, cudaStream_t);
+
+// ---------------------------------------------------------------- profiler
+thread_local Profiler* g_prof = nullptr;
+
+void prof_begin(int cls, cudaStream_t st) {
+  if (g_prof) g_prof->begin(cls, st);
+}
+void prof_end(int cls, double bytes, double flops, cudaStream_t st) {
+  if (g_prof) g_prof->end(cls, bytes, flops, st);
+}
 
 }  // namespace mcs

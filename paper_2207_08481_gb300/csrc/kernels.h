@@ -8,6 +8,16 @@
 
 namespace mcs {
 
+// Optional per-class kernel timing with CUDA events on the launching stream.  The API entry
+// points install the handle's profiler for the duration of a call; launchers bracket their
+// main kernel with prof_begin / prof_end (no-ops when no profiler is installed).
+enum ProfClass { PROF_CONDENSE = 0, PROF_FACET_BLOCKS, PROF_APPLY, PROF_FACET_GS, PROF_FACET_RES, PROF_PROLOGUE,
+                 PROF_EPILOGUE, PROF_GMG, PROF_NCLASS };
+struct Profiler;
+extern thread_local Profiler* g_prof;
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, double bytes, double flops, cudaStream_t st);
+
 // Dof layout of the condensed system [u_d | u_o | uhat | p] (dof contract).
 struct Layout {
   int64_t ne, nint;
@@ -26,7 +36,46 @@ struct DevMesh {
   const double* adet;        // [ne] |det J|
   const int32_t* fel;        // [nint][2] the two elements of each interior facet
   const int32_t* floc;       // [nint][2] local facet index in each element
+  const int32_t* fsr;        // [nint][2][d+1] interior ranks of the facets of each side element
 };
+
+// Compile-time element sizes for the (d, k) combinations with specialised kernels; the
+// members mirror ElemSizes so kernels can take either (runtime sizes as the fallback).
+__host__ __device__ constexpr int ct_npoly(int n, int k) {
+  return k < 0 ? 0 : (n == 1 ? k + 1 : (n == 2 ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 2) * (k + 3) / 6));
+}
+template <int D, int K>
+struct Ct {
+  static constexpr int d = D, k = K;
+  static constexpr int nk = ct_npoly(D, K), nF = ct_npoly(D - 1, K), nFm1 = ct_npoly(D - 1, K - 1);
+  static constexpr int n_u = D * nk, n_bub = n_u - (D + 1) * nF, nhF = (D - 1) * nFm1, n_hat = (D + 1) * nhF;
+  static constexpr int n_A = n_u + n_hat, n_p = ct_npoly(D, K - 1), mF = nF + nhF, n_c = (D + 1) * mF;
+};
+
+// Calls f(sizes) with compile-time sizes when a specialisation exists, else with s.
+template <class F>
+inline void dispatch_sizes(const ElemSizes& s, F&& f) {
+  if (s.d == 2 && s.k == 2) f(Ct<2, 2>{});
+  else if (s.d == 2 && s.k == 3) f(Ct<2, 3>{});
+  else if (s.d == 2 && s.k == 4) f(Ct<2, 4>{});
+  else if (s.d == 3 && s.k == 2) f(Ct<3, 2>{});
+  else if (s.d == 3 && s.k == 3) f(Ct<3, 3>{});
+  else f(s);
+}
+
+// Per-element device arrays are padded to multiples of 4 entries so that every slab and
+// element block starts on a 16-byte boundary (vector loads into shared memory).
+__host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
+template <class S> __host__ __device__ inline int slab_pad(const S& s) { return pad4(s.n_c * s.mF); }
+template <class S> __host__ __device__ inline int g_stride(const S& s) { return pad4(s.n_bub * s.n_c); }
+template <class S> __host__ __device__ inline int a_stride(const S& s) { return pad4(s.n_bub * s.n_bub); }
+
+// A^d_T storage: per element, facet slab f (rows f*mF .. f*mF+mF-1) stored column-major,
+// Ad[(T*(d+1) + f)*slab_pad + c*mF + t] = A^d_T[f*mF + t][c], so the rows of one facet are one
+// contiguous, aligned block.
+__host__ __device__ inline int64_t adw_index(int dp1, int slabp, int mF, int64_t T, int f, int c, int t) {
+  return (T * dp1 + f) * (int64_t)slabp + (int64_t)c * mF + t;
+}
 
 struct DevTables {
   const double* B0;
@@ -112,11 +161,6 @@ struct PrecData {
 template <class R>
 cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
                            PrecData<R>& P, const double* r, double* z, const int* stop, cudaStream_t st);
-
-// Ahat^{-1} alone on the velocity part (for diagnostics / unit parity)
-template <class R>
-cudaError_t launch_ahat_inv(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* rin,
-                            R* out, const int* stop, cudaStream_t st);
 
 // ---------------------------------------------------------------- Krylov helpers (FP64)
 // out[0] = a.b, deterministic: fixed grid, block partials summed in index order by the last block.

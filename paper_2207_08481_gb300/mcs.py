@@ -28,7 +28,8 @@ MCS_MIXED = 1
 EXPORTED = ["mcs_version", "mcs_last_error", "mcs_default_options", "mcs_setup_structured", "mcs_setup_mesh",
             "mcs_sizes", "mcs_export_mesh", "mcs_export_dofmap", "mcs_export_pattern", "mcs_condense",
             "mcs_copy_element_matrices", "mcs_copy_schur", "mcs_load_points", "mcs_load_vector",
-            "mcs_mass_velocity", "mcs_apply", "mcs_precond", "mcs_solve", "mcs_solve_host", "mcs_destroy"]
+            "mcs_mass_velocity", "mcs_apply", "mcs_precond", "mcs_solve", "mcs_solve_host", "mcs_profile",
+            "mcs_profile_read", "mcs_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -48,6 +49,11 @@ class Sizes(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("status", ctypes.c_int),
                 ("rel_res_precond", ctypes.c_double), ("rel_res_true", ctypes.c_double)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 class McsError(RuntimeError):
@@ -86,6 +92,8 @@ def lib() -> ctypes.CDLL:
         L.mcs_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveInfo)]
         L.mcs_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(SolveInfo)]
         L.mcs_destroy.argtypes = [vp]
+        L.mcs_profile.argtypes = [vp, ctypes.c_int]
+        L.mcs_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.c_int]
         L.mcs_default_options.argtypes = [ctypes.POINTER(Options)]
         del i32p
         _lib = L
@@ -222,6 +230,17 @@ class Handle:
         if check and rc not in (MCS_OK,):
             raise McsError(rc, lib().mcs_last_error().decode())
         return info
+
+    def profile(self, enable: bool):
+        _check(lib().mcs_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        buf = (KernelStat * 16)()
+        n = lib().mcs_profile_read(self._h, buf, 16)
+        if n < 0:
+            _check(n)
+        return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].total_ms, bytes=buf[i].bytes,
+                                             flops=buf[i].flops) for i in range(n)}
 
     def solve_host(self, F: np.ndarray, x: np.ndarray, check=True):
         info = SolveInfo()
