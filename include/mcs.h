@@ -182,6 +182,23 @@ typedef struct {
 int mcs_profile(mcs_handle* h, int enable);
 int mcs_profile_read(mcs_handle* h, mcs_kernel_stat* out, int max_n);
 
+/* Condensed element matrices without any device allocation, for callers that cannot let the
+ * library allocate at call time (work enqueued during CUDA-graph stream capture, where
+ * cudaMalloc is not allowed; applications that own the whole device through their own pool
+ * or run under a fixed memory budget).  The paper has no counterpart: this is a deployment
+ * variant of the condensation of Sec. 4.2.
+ *   AT_out: device buffer [count][n_A][n_A] (FP64, full symmetric, local order u_d | u_o | uhat,
+ *           orientation signs applied) receiving A_T of elements T0 .. T0+count-1 of the handle.
+ * Workspace: a file-scope 4 MiB device array, held by every GPU that loads the library until
+ * the process exits; one element's workspace must fit in it (3D k = 4 needs 1.1 MiB, the
+ * largest supported case), else MCS_ERR_UNSUPPORTED.  Nothing is allocated or freed: no cudaMalloc, no allocating library
+ * routine.  The first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share the array, so
+ * calls whose kernels overlap on the GPU (other streams, other host threads) race: order them
+ * on one stream.  The current device must be the handle's device.  Asynchronous on the handle's
+ * stream.  Errors: INVALID_ARG (NULL, range, wrong device), UNSUPPORTED, CUDA. */
+int mcs_condense_noalloc(mcs_handle* h, int64_t T0, int64_t count, double* AT_out);
+
 /* Releases the handle and its device memory (synchronises its stream). */
 int mcs_destroy(mcs_handle* h);
 

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmcs.so")
-SOURCES = ["reference.cpp", "meshing.cpp", "kernels.cu", "api.cu"]
+SOURCES = ["reference.cpp", "meshing.cpp", "kernels.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

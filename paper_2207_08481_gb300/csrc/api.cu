@@ -11,29 +11,13 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mcs.h"
-#include "kernels.h"
-#include "meshing.h"
-#include "profiler.h"
-#include "reference.h"
+#include "handle.h"
 
 using namespace mcs;
 
 namespace {
 
 thread_local std::string g_err = "no error";
-
-struct McsError : std::runtime_error {
-  int code;
-  McsError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
-};
-
-void cuda_check(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) {
-    int code = (e == cudaErrorMemoryAllocation) ? MCS_ERR_OOM : MCS_ERR_CUDA;
-    throw McsError(code, std::string(what) + ": " + cudaGetErrorString(e));
-  }
-}
 
 template <class F>
 int guarded(F&& f) {
@@ -70,69 +54,6 @@ ElemSizes elem_sizes(const Sizes& s) {
 }
 
 }  // namespace
-
-struct PrecBundle {
-  // device storage of one precision
-  void *Ad = nullptr, *G = nullptr, *Aoi = nullptr, *Dinv = nullptr, *Eb = nullptr;
-  std::vector<void*> lev_val, lev_dl1, lev_pval, lev_rval;
-};
-
-struct mcs_handle {
-  int d = 0, k = 0;
-  double nu = 1.0;
-  mcs_options opt{};
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  HostMesh mesh;
-  RefTables ref;
-  Sizes sz{};
-  ElemSizes es{};
-  Layout L{};
-  double total_adet = 0;
-  int ncol = 0;
-  std::vector<int32_t> colour;          // per interior rank
-  std::vector<int64_t> colour_off;      // host offsets into colour_list
-  int nlev = 0;
-  std::vector<int> level_N;
-  int64_t np1 = 0;
-  std::vector<void*> allocs;
-  int64_t bytes = 0;
-  // device data
-  DevMesh dm{};
-  DevTables dt{};
-  double* AT = nullptr;
-  PrecData<float> pf{};
-  PrecData<double> pd{};
-  bool condensed = false;
-  // Krylov work
-  double *kv[10] = {nullptr};
-  double* scratch = nullptr;
-  MinresScalars* S = nullptr;
-  MinresScalars* S_host = nullptr;  // pinned
-  double* cond_scratch = nullptr;
-  int64_t cond_scratch_doubles = 0;
-  std::unique_ptr<Profiler> prof;
-
-  template <class T>
-  T* dalloc(int64_t n) {
-    if (n <= 0) n = 1;
-    void* p = nullptr;
-    cuda_check(cudaMalloc(&p, sizeof(T) * n), "cudaMalloc");
-    allocs.push_back(p);
-    bytes += (int64_t)sizeof(T) * n;
-    return (T*)p;
-  }
-  template <class T>
-  T* upload(const std::vector<T>& v) {
-    T* p = dalloc<T>((int64_t)v.size());
-    if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice), "upload");
-    return p;
-  }
-  ~mcs_handle() {
-    for (void* p : allocs) cudaFree(p);
-    if (S_host) cudaFreeHost(S_host);
-  }
-};
 
 namespace {
 
@@ -413,9 +334,13 @@ mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* 
 
 }  // namespace
 
+void mcs::set_last_error(const char* msg) { g_err = msg ? msg : "unknown error"; }
+
 extern "C" {
 
 int mcs_version(void) { return 100; }
+
+
 
 const char* mcs_last_error(void) { return g_err.c_str(); }
 

@@ -29,7 +29,7 @@ EXPORTED = ["mcs_version", "mcs_last_error", "mcs_default_options", "mcs_setup_s
             "mcs_sizes", "mcs_export_mesh", "mcs_export_dofmap", "mcs_export_pattern", "mcs_condense",
             "mcs_copy_element_matrices", "mcs_copy_schur", "mcs_load_points", "mcs_load_vector",
             "mcs_mass_velocity", "mcs_apply", "mcs_precond", "mcs_solve", "mcs_solve_host", "mcs_profile",
-            "mcs_profile_read", "mcs_destroy"]
+            "mcs_profile_read", "mcs_condense_noalloc", "mcs_destroy"]
 
 
 class Options(ctypes.Structure):
@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         L.mcs_destroy.argtypes = [vp]
         L.mcs_profile.argtypes = [vp, ctypes.c_int]
         L.mcs_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.c_int]
+        L.mcs_condense_noalloc.argtypes = [vp, i64, i64, vp]
         L.mcs_default_options.argtypes = [ctypes.POINTER(Options)]
         del i32p
         _lib = L
@@ -241,6 +242,10 @@ class Handle:
             _check(n)
         return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].total_ms, bytes=buf[i].bytes,
                                              flops=buf[i].flops) for i in range(n)}
+
+    def condense_noalloc(self, T0, count, AT_out):
+        """A_T of elements T0 .. T0+count-1 into the device tensor AT_out [count, n_A, n_A] (no allocation)."""
+        _check(lib().mcs_condense_noalloc(self._h, T0, count, _dptr(AT_out)))
 
     def solve_host(self, F: np.ndarray, x: np.ndarray, check=True):
         info = SolveInfo()
