@@ -124,7 +124,8 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   P.Ad = h->dalloc<R>(ne * (int64_t)(s.d + 1) * slab_pad(s));
   P.G = h->dalloc<R>(ne * (int64_t)g_stride(s));
   P.Aoi = h->dalloc<R>(ne * (int64_t)a_stride(s));
-  P.Dinv = h->dalloc<R>(nint * s.mF * s.mF);
+  P.Dinv = h->dalloc<R>(nint * (int64_t)dinv_stride(s));
+  cuda_check(cudaMemset((void*)P.Dinv, 0, sizeof(R) * nint * (int64_t)dinv_stride(s)), "memset");
   P.Eb = h->upload(cast_vec<R>(Eb));
   P.fvr = h->upload(fvr);
   P.vf_ptr = h->upload(vf_ptr);
@@ -243,6 +244,15 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   dt.Adiv = h->upload(R.Adiv);
   dt.nhat = h->upload(R.nhat);
   dt.Bp = h->upload(R.Bp);
+  {
+    std::vector<float> hi(R.Bp.size()), lo(R.Bp.size());
+    for (size_t i = 0; i < R.Bp.size(); ++i) {
+      hi[i] = (float)R.Bp[i];
+      lo[i] = (float)(R.Bp[i] - (double)hi[i]);
+    }
+    dt.Bp_hi = h->upload(hi);
+    dt.Bp_lo = h->upload(lo);
+  }
   dt.Mu = h->upload(R.Mu);
   dt.phi_load = h->upload(R.phi_load);
   dt.xq_load = h->upload(R.xq_load);
@@ -258,6 +268,22 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
       if (h->colour[r] == c) clist.push_back((int32_t)r);
   }
   h->colour_off[h->ncol] = (int64_t)clist.size();
+  {
+    // facet records in colour order
+    std::vector<int32_t> rec(clist.size() * 16, -1);
+    for (size_t li = 0; li < clist.size(); ++li) {
+      const int32_t r = clist[li];
+      int32_t* o = &rec[li * 16];
+      o[0] = r;
+      o[1] = fel[r * 2];
+      o[2] = fel[r * 2 + 1];
+      o[3] = floc[r * 2];
+      o[4] = floc[r * 2 + 1];
+      for (int side = 0; side < 2; ++side)
+        for (int f = 0; f <= d; ++f) o[5 + side * (d + 1) + f] = fsr[(r * 2 + side) * (d + 1) + f];
+    }
+    dm.frec = reinterpret_cast<const int4*>(h->upload(rec));
+  }
   // conforming space and multigrid
   std::vector<P1Space> sp;
   std::vector<Csr> A, Pr, Rt;
@@ -300,8 +326,14 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   else
     build_precision<double>(h, h->pd, A, Pr, Rt, cinv, Eb, fvr, vf_ptr, vf_idx, clist);
   // condensed operator and Krylov work
-  h->AT = h->dalloc<double>(m.ne * (int64_t)s.n_A * s.n_A);
-  for (int i = 0; i < 10; ++i) h->kv[i] = h->dalloc<double>(L.ndof);
+  if (h->opt.precision == MCS_MIXED) {
+    h->K.Ahi = h->dalloc<float>(m.ne * (int64_t)packed_pad(s));
+    h->K.Alo = h->dalloc<float>(m.ne * (int64_t)packed_pad(s));
+  } else {
+    h->K.AT = h->dalloc<double>(m.ne * (int64_t)s.n_A * s.n_A);
+  }
+  for (int i = 0; i < 11; ++i) h->kv[i] = h->dalloc<double>(L.ndof);
+  cuda_check(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   h->scratch = h->dalloc<double>(4096);
   cuda_check(cudaMemset(h->scratch, 0, sizeof(double) * 4096), "memset");
   h->S = h->dalloc<MinresScalars>(1);
@@ -520,12 +552,12 @@ int mcs_condense(mcs_handle* h) {
     if (!h) throw McsError(MCS_ERR_INVALID_ARG, "NULL handle");
     ProfScope ps(h->prof.get());
     if (h->opt.precision == MCS_MIXED) {
-      cuda_check(launch_condense<float>(h->es, h->dt, h->dm, h->nu, h->AT, (float*)h->pf.Ad, (float*)h->pf.G,
+      cuda_check(launch_condense<float>(h->es, h->dt, h->dm, h->nu, h->K, (float*)h->pf.Ad, (float*)h->pf.G,
                                         (float*)h->pf.Aoi, h->cond_scratch, h->cond_scratch_doubles, h->stream),
                  "condense");
       cuda_check(launch_facet_blocks<float>(h->es, h->dm, h->pf.Ad, (float*)h->pf.Dinv, h->stream), "facet blocks");
     } else {
-      cuda_check(launch_condense<double>(h->es, h->dt, h->dm, h->nu, h->AT, (double*)h->pd.Ad, (double*)h->pd.G,
+      cuda_check(launch_condense<double>(h->es, h->dt, h->dm, h->nu, h->K, (double*)h->pd.Ad, (double*)h->pd.G,
                                          (double*)h->pd.Aoi, h->cond_scratch, h->cond_scratch_doubles, h->stream),
                  "condense");
       cuda_check(launch_facet_blocks<double>(h->es, h->dm, h->pd.Ad, (double*)h->pd.Dinv, h->stream),
@@ -542,12 +574,22 @@ int mcs_copy_element_matrices(const mcs_handle* h, int64_t T0, int64_t count, do
     const int nA = h->sz.n_A;
     const int64_t np = (int64_t)nA * (nA + 1) / 2, full = (int64_t)nA * nA;
     cuda_check(cudaStreamSynchronize(h->stream), "sync");
-    std::vector<double> tmp(full * count);
-    cuda_check(cudaMemcpy(tmp.data(), h->AT + T0 * full, sizeof(double) * full * count, cudaMemcpyDeviceToHost),
-               "copy");
-    for (int64_t T = 0; T < count; ++T)
-      for (int i = 0; i < nA; ++i)
-        for (int j = 0; j <= i; ++j) out[T * np + (int64_t)i * (i + 1) / 2 + j] = tmp[T * full + (int64_t)i * nA + j];
+    if (h->K.AT) {
+      std::vector<double> tmp(full * count);
+      cuda_check(cudaMemcpy(tmp.data(), h->K.AT + T0 * full, sizeof(double) * full * count, cudaMemcpyDeviceToHost),
+                 "copy");
+      for (int64_t T = 0; T < count; ++T)
+        for (int i = 0; i < nA; ++i)
+          for (int j = 0; j <= i; ++j)
+            out[T * np + (int64_t)i * (i + 1) / 2 + j] = tmp[T * full + (int64_t)i * nA + j];
+    } else {
+      const int64_t pp = packed_pad(h->sz);
+      std::vector<float> hi(pp * count), lo(pp * count);
+      cuda_check(cudaMemcpy(hi.data(), h->K.Ahi + T0 * pp, sizeof(float) * pp * count, cudaMemcpyDeviceToHost), "copy");
+      cuda_check(cudaMemcpy(lo.data(), h->K.Alo + T0 * pp, sizeof(float) * pp * count, cudaMemcpyDeviceToHost), "copy");
+      for (int64_t T = 0; T < count; ++T)
+        for (int64_t q = 0; q < np; ++q) out[T * np + q] = (double)hi[T * pp + q] + (double)lo[T * pp + q];
+    }
     return MCS_OK;
   });
 }
@@ -620,15 +662,16 @@ int mcs_apply(mcs_handle* h, const double* x, double* y) {
     if (!h || !x || !y) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
     ProfScope ps(h->prof.get());
     if (!h->condensed) throw McsError(MCS_ERR_INVALID_ARG, "mcs_condense has not been called");
-    cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, x, y, nullptr, h->stream), "apply");
+    cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->K, x, y, nullptr, h->stream), "apply");
     return MCS_OK;
   });
 }
 
-static void precond_any(mcs_handle* h, const double* r, double* z, const int* stop) {
+static void precond_any(mcs_handle* h, const double* r, double* z, const int* stop, cudaStream_t st = nullptr) {
+  if (!st) st = h->stream;
   cudaError_t e = (h->opt.precision == MCS_MIXED)
-                      ? launch_precond<float>(h->es, h->dt, h->dm, h->L, h->nu, h->pf, r, z, stop, h->stream)
-                      : launch_precond<double>(h->es, h->dt, h->dm, h->L, h->nu, h->pd, r, z, stop, h->stream);
+                      ? launch_precond<float>(h->es, h->dt, h->dm, h->L, h->nu, h->pf, r, z, stop, st)
+                      : launch_precond<double>(h->es, h->dt, h->dm, h->L, h->nu, h->pd, r, z, stop, st);
   cuda_check(e, "precond");
 }
 
@@ -643,6 +686,49 @@ int mcs_precond(mcs_handle* h, const double* r, double* z) {
 }
 
 namespace {
+
+// One preconditioned MinRes iteration (all scalars stay on the device; kernels return early once
+// the state says stop).  The vector roles rotate: after two iterations they are back in place.
+void minres_iteration(mcs_handle* h, cudaStream_t st, double*& v_old, double*& v, double*& z, double*& zn,
+                      double*& w_old, double*& w, double* Kz, double* x_acc) {
+  const int64_t n = h->L.ndof;
+  MinresScalars* S = h->S;
+  const int* stop = &S->stop;
+  cuda_check(launch_minres_scale(S, n, z, z, st), "scale");
+  cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->K, z, Kz, stop, st), "apply");
+  cuda_check(launch_dot(Kz, z, n, h->scratch, &S->delta, stop, st), "dot");
+  cuda_check(launch_minres_lanczos(S, n, z, Kz, v, v_old, st), "lanczos");
+  precond_any(h, v_old, zn, stop, st);
+  cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, zn, h->scratch, h->total_adet, stop, st), "mean");
+  cuda_check(launch_dot(zn, v_old, n, h->scratch, &S->dot1, stop, st), "dot");
+  cuda_check(launch_minres_scalars(S, st), "scalars");
+  cuda_check(launch_minres_update(S, n, z, w, w_old, x_acc, st), "update");
+  std::swap(v_old, v);
+  std::swap(w_old, w);
+  std::swap(z, zn);
+}
+
+// Captures two iterations (one full rotation of the vector roles) as a CUDA graph on the
+// handle's capture stream; the graph is later launched on the handle's stream.
+void capture_iterations(mcs_handle* h, double* x_acc) {
+  double *v_old = h->kv[0], *v = h->kv[1], *z = h->kv[2], *zn = h->kv[3];
+  double *w_old = h->kv[4], *w = h->kv[5], *Kz = h->kv[6];
+  cudaStream_t cs = h->cap_stream;
+  cuda_check(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  cudaGraph_t g = nullptr;
+  try {
+    minres_iteration(h, cs, v_old, v, z, zn, w_old, w, Kz, x_acc);
+    minres_iteration(h, cs, v_old, v, z, zn, w_old, w, Kz, x_acc);
+  } catch (...) {
+    cudaStreamEndCapture(cs, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  cuda_check(cudaStreamEndCapture(cs, &g), "cudaStreamEndCapture");
+  cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+  cudaGraphDestroy(g);
+  cuda_check(e, "cudaGraphInstantiate");
+}
 
 // One MinRes cycle on K d = rhs from d = 0, accumulating d into x_acc.
 // g_first: preconditioned norm of the first cycle's residual (< 0 before the first cycle).
@@ -667,24 +753,17 @@ void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double floor_
   cuda_check(launch_dot(z, v, n, h->scratch, &S->dot1, nullptr, st), "dot");
   cuda_check(launch_minres_init(S, st), "init");
   const int* stop = &S->stop;
-  const int check_every = 8;
+  const bool graphs = h->use_graphs && !h->prof;
+  if (graphs && !h->gexec) capture_iterations(h, x_acc);
+  const int check_every = 8;  // iterations between reads of the convergence state
   while (true) {
     cuda_check(cudaMemcpyAsync(h->S_host, S, sizeof(MinresScalars), cudaMemcpyDeviceToHost, st), "read S");
     cuda_check(cudaStreamSynchronize(st), "sync");
     if (h->S_host->stop) break;
-    for (int q = 0; q < check_every; ++q) {
-      cuda_check(launch_minres_scale(S, n, z, z, st), "scale");
-      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, z, Kz, stop, st), "apply");
-      cuda_check(launch_dot(Kz, z, n, h->scratch, &S->delta, stop, st), "dot");
-      cuda_check(launch_minres_lanczos(S, n, z, Kz, v, v_old, st), "lanczos");
-      precond_any(h, v_old, zn, stop);
-      cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, zn, h->scratch, h->total_adet, stop, st), "mean");
-      cuda_check(launch_dot(zn, v_old, n, h->scratch, &S->dot1, stop, st), "dot");
-      cuda_check(launch_minres_scalars(S, st), "scalars");
-      cuda_check(launch_minres_update(S, n, z, w, w_old, x_acc, st), "update");
-      std::swap(v_old, v);
-      std::swap(w_old, w);
-      std::swap(z, zn);
+    if (graphs) {
+      for (int q = 0; q < check_every / 2; ++q) cuda_check(cudaGraphLaunch(h->gexec, st), "cudaGraphLaunch");
+    } else {
+      for (int q = 0; q < check_every; ++q) minres_iteration(h, st, v_old, v, z, zn, w_old, w, Kz, x_acc);
     }
   }
 }
@@ -699,6 +778,8 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
     const int64_t n = h->L.ndof;
     cudaStream_t st = h->stream;
     double* r = h->kv[7];
+    double* xi = h->kv[10];  // the iterate (fixed address for the captured iterations)
+    cuda_check(cudaMemcpyAsync(xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy x");
     const bool mixed = h->opt.precision == MCS_MIXED;
     // FP64 form: one cycle to rtol plus a check of the true residual.  Mixed form: FP64
     // iterative refinement, each cycle asked for at least inner_rtol reduction.
@@ -707,9 +788,9 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
     int total_it = 0, cycles = 0, status = MCS_ERR_NOT_CONVERGED;
     double g_first = -1.0, g_now = 0.0;
     while (cycles < max_cycles) {
-      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, x, r, nullptr, st), "apply");
+      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->K, xi, r, nullptr, st), "apply");
       cuda_check(launch_axpby(n, 1.0, F, -1.0, r, st), "axpby");
-      minres_cycle(h, r, x, floor_rtol, std::max(1, h->opt.maxit - total_it), g_first);
+      minres_cycle(h, r, xi, floor_rtol, std::max(1, h->opt.maxit - total_it), g_first);
       const MinresScalars& Sh = *h->S_host;
       g_first = Sh.g_first;
       g_now = Sh.res0;
@@ -725,9 +806,10 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       }
       if (total_it >= h->opt.maxit) break;
     }
-    cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, x, h->scratch, h->total_adet, nullptr, st), "mean");
+    cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, xi, h->scratch, h->total_adet, nullptr, st), "mean");
+    cuda_check(cudaMemcpyAsync(x, xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy x");
     if (info) {
-      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->AT, x, r, nullptr, st), "apply");
+      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->K, x, r, nullptr, st), "apply");
       cuda_check(launch_axpby(n, 1.0, F, -1.0, r, st), "axpby");
       double* res = h->scratch + 3000;
       cuda_check(launch_dot(r, r, n, h->scratch, res, nullptr, st), "dot");

@@ -60,12 +60,15 @@ struct mcs_handle {
   // device data
   DevMesh dm{};
   DevTables dt{};
-  double* AT = nullptr;
+  KOp K{nullptr, nullptr, nullptr};   // A_T: FP64 (MCS_FP64) or float pairs (MCS_MIXED)
   PrecData<float> pf{};
   PrecData<double> pd{};
   bool condensed = false;
   // Krylov work
-  double *kv[10] = {nullptr};
+  double *kv[11] = {nullptr};  // Krylov vectors; kv[10] is the iterate the captured graph updates
+  cudaStream_t cap_stream = nullptr;   // non-default stream for graph capture
+  cudaGraphExec_t gexec = nullptr;     // two MinRes iterations
+  bool use_graphs = true;
   double* scratch = nullptr;
   MinresScalars* S = nullptr;
   MinresScalars* S_host = nullptr;  // pinned
@@ -89,6 +92,8 @@ struct mcs_handle {
     return p;
   }
   ~mcs_handle() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (void* p : allocs) cudaFree(p);
     if (S_host) cudaFreeHost(S_host);
   }

@@ -10,6 +10,23 @@ namespace mcs {
 
 #define MCS_WARP 32
 
+// Copy n entries (n * sizeof(R) a multiple of 16, both pointers 16-byte aligned) with 16-byte loads.
+template <class R>
+__device__ __forceinline__ void vcopy16(R* dst, const R* __restrict__ src, int n, int tid, int nth) {
+  const int nv = n * (int)sizeof(R) / 16;
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  const uint4* sv = reinterpret_cast<const uint4*>(src);
+  for (int i = tid; i < nv; i += nth) d[i] = sv[i];
+}
+
+// Asynchronous 16-byte global -> shared copies (no register staging; completion by
+// cp.async.wait_all, a hardware wait).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 struct WarpSync {
   __device__ void operator()() const { __syncwarp(); }
 };
@@ -22,7 +39,7 @@ struct BlockSync {
 // One thread block per element (grid-stride).  Workspace in dynamic shared memory when
 // it fits, else in a global scratch slot per resident block.
 template <class R, bool SMEM>
-__global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, double* AT, R* Ad,
+__global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, KOp K, R* Ad,
                                                   R* G, R* Aoi, double* gscratch, int64_t slot_doubles) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x, nl = blockDim.x;
@@ -44,10 +61,23 @@ __global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevM
     if (lane <= d) sg[lane] = m.signs[T * (d + 1) + lane];
     __syncthreads();
     condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
-    // full A_T (FP64, symmetric: row-major = column-major)
     const int nA = s.n_A;
-    double* out = AT + T * (int64_t)nA * nA;
-    for (int q = lane; q < nA * nA; q += nl) out[q] = w.A[q];
+    if (K.AT) {  // full A_T (FP64, symmetric: row-major = column-major)
+      double* out = K.AT + T * (int64_t)nA * nA;
+      for (int q = lane; q < nA * nA; q += nl) out[q] = w.A[q];
+    }
+    if (K.Ahi) {  // packed lower triangle as float pairs, hi = fl(a), lo = fl(a - hi)
+      const int pp = packed_pad(s);
+      float* oh = K.Ahi + T * (int64_t)pp;
+      float* ol = K.Alo + T * (int64_t)pp;
+      for (int i = lane; i < nA; i += nl)
+        for (int j = 0; j <= i; ++j) {
+          const double a = w.A[i * nA + j];
+          const float hi = (float)a;
+          oh[i * (i + 1) / 2 + j] = hi;
+          ol[i * (i + 1) / 2 + j] = (float)(a - (double)hi);
+        }
+    }
     __syncthreads();
     bubble_condense(s, w.A, bw, Adt, Gt, Ait, lane, nl, BlockSync());
     const int nc = s.n_c, no = s.n_bub;
@@ -70,7 +100,7 @@ static int64_t condense_slot_doubles(const ElemSizes& s) {
 static int condense_threads(const ElemSizes& s) { return s.d == 2 ? 128 : 256; }
 
 template <class R>
-cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, double* AT, R* Ad,
+cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K, R* Ad,
                             R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st) {
   const int64_t slot = condense_slot_doubles(s);
   int dev = 0, nsm = 0, maxsm = 0;
@@ -88,12 +118,12 @@ cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMes
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)nsm * per_sm;
     if (blocks > m.ne) blocks = m.ne;
-    k_condense<R, true><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, nu, AT, Ad, G, Aoi, nullptr, slot);
+    k_condense<R, true><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, nu, K, Ad, G, Aoi, nullptr, slot);
   } else {
     int64_t blocks = scratch_doubles / slot;
     if (blocks < 1) return cudaErrorMemoryAllocation;
     if (blocks > m.ne) blocks = m.ne;
-    k_condense<R, false><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, nu, AT, Ad, G, Aoi, scratch, slot);
+    k_condense<R, false><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, nu, K, Ad, G, Aoi, scratch, slot);
   }
   {
     // FP64 flops of the element condensation (products and factorisations, see element.cuh)
@@ -102,8 +132,8 @@ cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMes
                             nc * nc * nA / 2 + nA * (nA + 1) / 2 * nc + no * no * no / 6 + no * no * ncp +
                             ncp * ncp * no + no * no * no) +
                      2.0 * nA * nr * s.n_s0;
-    const double out = (double)m.ne * (nA * nA * 8 + (double)((s.d + 1) * slab_pad(s) + g_stride(s) + a_stride(s)) *
-                                                         sizeof(R));
+    const double out = (double)m.ne * ((K.AT ? nA * nA * 8 : 0.0) + (K.Ahi ? 8.0 * packed_pad(s) : 0.0) +
+                                       (double)((s.d + 1) * slab_pad(s) + g_stride(s) + a_stride(s)) * sizeof(R));
     prof_end(PROF_CONDENSE, out, f * (double)m.ne, st);
   }
   return cudaGetLastError();
@@ -160,7 +190,7 @@ __global__ void k_facet_blocks(ElemSizes s, DevMesh m, const R* Ad, R* Dinv) {
         if (rr != c) A[rr * mF + c] = 0.0;
       __syncwarp();
     }
-    for (int q = lane; q < mF * mF; q += 32) Dinv[r * mF * mF + q] = (R)(0.5 * (I[q] + I[(q % mF) * mF + q / mF]));
+    for (int q = lane; q < mF * mF; q += 32) Dinv[r * dinv_stride(s) + q] = (R)(0.5 * (I[q] + I[(q % mF) * mF + q / mF]));
     __syncwarp();
   }
 }
@@ -280,6 +310,103 @@ __global__ void __launch_bounds__(256) k_apply_K(S s, DevTables t, DevMesh m, La
   }
 }
 
+// Double-float helpers (Dekker / Knuth error-free transformations): the product of two floats
+// is split exactly into p + e with one fma; sums are accumulated with TwoSum.
+struct DF {
+  float hi, lo, c;  // value hi + lo, plus first-order corrections c
+};
+__device__ __forceinline__ void df_mac(DF& a, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  const float e = __fmaf_rn(xh, yh, -p);
+  const float s = __fadd_rn(a.hi, p);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(err, e));
+  a.c = __fmaf_rn(xh, yl, a.c);
+  a.c = __fmaf_rn(xl, yh, a.c);
+}
+__device__ __forceinline__ double df_value(const DF& a) { return (double)a.hi + ((double)a.lo + (double)a.c); }
+
+// y = K x with A_T as packed-lower float pairs and double-float arithmetic (mixed form).
+template <class S>
+__global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m, Layout L,
+                                                    const float* __restrict__ Ahi, const float* __restrict__ Alo,
+                                                    const double* __restrict__ x, double* y, int EB, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ float skf[];
+  const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d, nfd = (s.d + 1) * s.nF;
+  const int per = nA + np_, pp = packed_pad(s);
+  float* Ah = skf;                    // [EB][pp]
+  float* Al = Ah + EB * pp;           // [EB][pp]
+  float* xh = Al + EB * pp;           // [EB][per]
+  float* xl = xh + EB * per;          // [EB][per]
+  int* er = (int*)(xl + EB * per);    // [EB][4]
+  float* sg = (float*)(er + EB * 4);  // [EB][4]
+  const int tid = threadIdx.x;
+  const int64_t T0 = (int64_t)blockIdx.x * EB;
+  const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
+  if (tid < EB * 4) {
+    int e = tid >> 2, f = tid & 3;
+    int64_t T = T0 + e;
+    bool ok = e < nvalid && f <= d;
+    er[tid] = ok ? m.elem_rank[T * (d + 1) + f] : -1;
+    sg[tid] = ok ? (float)m.signs[T * (d + 1) + f] : 0.f;
+  }
+  vcopy16<float>(Ah, Ahi + T0 * pp, nvalid * pp, tid, blockDim.x);
+  vcopy16<float>(Al, Alo + T0 * pp, nvalid * pp, tid, blockDim.x);
+  __syncthreads();
+  for (int q = tid; q < nvalid * per; q += blockDim.x) {
+    const int e = q / per, i = q - e * per;
+    const int64_t T = T0 + e;
+    double v;
+    if (i < nA) {
+      int64_t g = local_to_global(s, L, er + e * 4, T, i);
+      v = g < 0 ? 0.0 : x[g];
+    } else {
+      v = x[L.off_p + T * np_ + (i - nA)];
+    }
+    const float h = (float)v;
+    xh[q] = h;
+    xl[q] = (float)(v - (double)h);
+  }
+  __syncthreads();
+  for (int q = tid; q < nvalid * per; q += blockDim.x) {
+    const int e = q / per, i = q - e * per;
+    const int64_t T = T0 + e;
+    const float* xe = xh + e * per;
+    const float* xle = xl + e * per;
+    DF acc{0.f, 0.f, 0.f};
+    if (i < nA) {
+      const float* ah = Ah + e * pp;
+      const float* al = Al + e * pp;
+      const int row = i * (i + 1) / 2;
+      for (int j = 0; j <= i; ++j) df_mac(acc, ah[row + j], al[row + j], xe[j], xle[j]);
+      for (int j = i + 1; j < nA; ++j) {
+        const int idx = j * (j + 1) / 2 + i;
+        df_mac(acc, ah[idx], al[idx], xe[j], xle[j]);
+      }
+      if (i < nu_) {  // (B^T x_p)_i = -s_i sum_j Bhat[j][i] x_p[j]
+        const float sgn = i < nfd ? sg[e * 4 + i / s.nF] : 1.f;
+        for (int p = 0; p < np_; ++p)
+          df_mac(acc, -sgn * t.Bp_hi[p * nu_ + i], -sgn * t.Bp_lo[p * nu_ + i], xe[nA + p], xle[nA + p]);
+      }
+      const double v = df_value(acc);
+      int64_t g = local_to_global(s, L, er + e * 4, T, i);
+      if (g < 0) continue;
+      if (i >= nfd && i < nu_) y[g] = v;     // bubble: owned by T
+      else atomicAdd(&y[g], v);             // facet dof: exactly two contributions into 0
+    } else {
+      const int jp = i - nA;
+      for (int c = 0; c < nu_; ++c) {
+        const float sgn = c < nfd ? sg[e * 4 + c / s.nF] : 1.f;
+        df_mac(acc, -sgn * t.Bp_hi[jp * nu_ + c], -sgn * t.Bp_lo[jp * nu_ + c], xe[c], xle[c]);
+      }
+      y[L.off_p + T * np_ + jp] = df_value(acc);
+    }
+  }
+}
+
 __global__ void k_zero_facet(const Layout L, double* y, const int* stop) {
   if (stop && *stop) return;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -299,9 +426,32 @@ static int sm_count() {
 }
 
 cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
-                           const double* AT, const double* x, double* y, const int* stop, cudaStream_t st) {
+                           KOp K, const double* x, double* y, const int* stop, cudaStream_t st) {
   k_zero_facet<<<sm_count() * 4, 256, 0, st>>>(L, y, stop);
   const int per = s.n_A + s.n_p;
+  // algorithmic: packed symmetric A_T, x read once, y written once; flops: full row products
+  const double alg_bytes = (double)m.ne * s.n_A * (s.n_A + 1) / 2 * 8.0 + 16.0 * L.ndof;
+  const double alg_flops = 2.0 * (double)m.ne * ((double)s.n_A * s.n_A + 2.0 * s.n_u * s.n_p);
+  if (K.Ahi) {
+    const size_t per_bytes = (2 * (size_t)packed_pad(s) + 2 * per) * sizeof(float) + 4 * (sizeof(int) + sizeof(float));
+    int EB = (int)((40 * 1024) / per_bytes);
+    if (EB < 1) EB = 1;
+    if (EB > 16) EB = 16;
+    const int threads = EB * per <= 128 ? 128 : 256;
+    const size_t sm = (size_t)EB * per_bytes + 64;
+    const int64_t blocks = (m.ne + EB - 1) / EB;
+    dispatch_sizes(s, [&](auto sz) {
+      static bool set = false;
+      if (!set) {
+        cudaFuncSetAttribute(k_apply_K_df<decltype(sz)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        set = true;
+      }
+      prof_begin(PROF_APPLY, st);
+      k_apply_K_df<decltype(sz)><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.Ahi, K.Alo, x, y, EB, stop);
+      prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
+    });
+    return cudaGetLastError();
+  }
   const size_t per_bytes = ((size_t)s.n_A * s.n_A + per) * sizeof(double) + 4 * (sizeof(int) + sizeof(float));
   int EB = (int)((40 * 1024) / per_bytes);
   if (EB < 1) EB = 1;
@@ -316,10 +466,8 @@ cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh
       set = true;
     }
     prof_begin(PROF_APPLY, st);
-    k_apply_K<decltype(sz)><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, AT, x, y, EB, stop);
-    // algorithmic: packed symmetric A_T, x read once, y written once; flops: full row products
-    prof_end(PROF_APPLY, (double)m.ne * s.n_A * (s.n_A + 1) / 2 * 8.0 + 16.0 * L.ndof,
-             2.0 * (double)m.ne * ((double)s.n_A * s.n_A + 2.0 * s.n_u * s.n_p), st);
+    k_apply_K<decltype(sz)><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.AT, x, y, EB, stop);
+    prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
   });
   return cudaGetLastError();
 }
@@ -455,15 +603,6 @@ __global__ void k_from_R(int64_t n, const R* a, double* b, const int* stop) {
     b[i] = (double)a[i];
 }
 
-// Copy n entries (n * sizeof(R) a multiple of 16, both pointers 16-byte aligned) with 16-byte loads.
-template <class R>
-__device__ __forceinline__ void vcopy16(R* dst, const R* __restrict__ src, int n, int tid, int nth) {
-  const int nv = n * (int)sizeof(R) / 16;
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  const uint4* sv = reinterpret_cast<const uint4*>(src);
-  for (int i = tid; i < nv; i += nth) d[i] = sv[i];
-}
-
 // ---------------------------------------------------------------- element-level preconditioner kernels
 // Prologue of one Ahat^{-1} application (bubble elimination, eq. factorSsigma):
 //   rin_o = r_o - (B^T z_p)_o                          (WITH_BT; else rin_o = r_o)
@@ -491,35 +630,35 @@ __global__ void __launch_bounds__(256) k_elem_prologue(S s, DevTables t, DevMesh
     for (int q = tid; q < nvalid * np_; q += blockDim.x) zz[q] = zp[L.off_p + T0 * np_ + q];
   __syncthreads();
   if (WITH_BT) {
-    for (int e = 0; e < nvalid; ++e) {
+    for (int q = tid; q < nvalid * nu_; q += blockDim.x) {
+      const int e = q / nu_, i = q - e * nu_;
       const int64_t T = T0 + e;
-      for (int i = tid; i < nu_; i += blockDim.x) {
-        R sg = i < nfd ? (R)m.signs[T * (d + 1) + i / s.nF] : (R)1;
-        R v = 0;
-        for (int j = 0; j < np_; ++j) v += (R)t.Bp[j * nu_ + i] * zz[e * np_ + j];
-        bt[e * nu_ + i] = -sg * v;
-      }
+      R sg = i < nfd ? (R)m.signs[T * (d + 1) + i / s.nF] : (R)1;
+      R v = 0;
+      for (int j = 0; j < np_; ++j) v += (R)t.Bp[j * nu_ + i] * zz[e * np_ + j];
+      bt[q] = -sg * v;
     }
     __syncthreads();
-    for (int e = 0; e < nvalid; ++e)
-      for (int o = tid; o < no; o += blockDim.x) ro[e * no + o] -= bt[e * nu_ + nfd + o];
+    for (int q = tid; q < nvalid * no; q += blockDim.x) {
+      const int e = q / no, o = q - e * no;
+      ro[q] -= bt[e * nu_ + nfd + o];
+    }
     __syncthreads();
   }
   for (int q = tid; q < nvalid * no; q += blockDim.x) rin[L.off_o + T0 * no + q] = ro[q];
-  for (int e = 0; e < nvalid; ++e) {
+  for (int q = tid; q < nvalid * nc; q += blockDim.x) {
+    const int e = q / nc, c = q - e * nc;
     const int64_t T = T0 + e;
-    for (int c = tid; c < nc; c += blockDim.x) {
-      const int f = c / s.mF, tt = c - f * s.mF;
-      const int32_t rk = m.elem_rank[T * (d + 1) + f];
-      if (rk < 0) continue;
-      R v = 0;
-      const R* g = Gs + e * gs + c;
-      const R* rv = ro + e * no;
+    const int f = c / s.mF, tt = c - f * s.mF;
+    const int32_t rk = m.elem_rank[T * (d + 1) + f];
+    if (rk < 0) continue;
+    R v = 0;
+    const R* g = Gs + e * gs + c;
+    const R* rv = ro + e * no;
 #pragma unroll 4
-      for (int o = 0; o < no; ++o) v += g[o * nc] * rv[o];
-      if (WITH_BT && tt < s.nF) v += bt[e * nu_ + f * s.nF + tt];
-      atomicAdd(&tb[coup_idx<R>(s, L, rk, tt)], v);
-    }
+    for (int o = 0; o < no; ++o) v += g[o * nc] * rv[o];
+    if (WITH_BT && tt < s.nF) v += bt[e * nu_ + f * s.nF + tt];
+    atomicAdd(&tb[coup_idx<R>(s, L, rk, tt)], v);
   }
 }
 
@@ -547,12 +686,11 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
   vcopy16<R>(Gs, G + T0 * gs, nvalid * gs, tid, blockDim.x);
   vcopy16<R>(As, Aoi + T0 * as_, nvalid * as_, tid, blockDim.x);
   for (int q = tid; q < nvalid * no; q += blockDim.x) ro[q] = rin[L.off_o + T0 * no + q];
-  for (int e = 0; e < nvalid; ++e) {
+  for (int q = tid; q < nvalid * nc; q += blockDim.x) {
+    const int e = q / nc, c = q - e * nc;
     const int64_t T = T0 + e;
-    for (int c = tid; c < nc; c += blockDim.x) {
-      const int f = c / mF;
-      xc[e * nc + c] = coup_get<R>(s, L, x, m.elem_rank[T * (d + 1) + f], c - f * mF);
-    }
+    const int f = c / mF;
+    xc[q] = coup_get<R>(s, L, x, m.elem_rank[T * (d + 1) + f], c - f * mF);
   }
   __syncthreads();
   for (int q = tid; q < nvalid * no; q += blockDim.x) {
@@ -591,67 +729,76 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
   }
 }
 
-// Facet-centric block step: for facets in `list` (interior ranks; NULL = all),
+// Facet-centric block step over the facet records rec[0..n) (colour order):
 //   r_F = b_F - tb_F - sum_{T in F} (A^d_T x_T)|_F,
 // UPDATE: x_F += D_F^{-1} r_F (block Gauss-Seidel within one colour); else rr_F = r_F.
-// FB facets per block: the A^d slabs of both sides are staged in shared memory (one warp per
-// slab, coalesced), then one thread per (facet, side, row) forms the product.
+// FB facets per block.  Two dependent rounds of loads: the 64-byte facet records, then
+// everything else at once (A^d slabs and D_F^{-1} staged in shared memory with 16-byte
+// loads, x of both elements, b, tb); then one thread per (facet, side, row) forms the product.
 template <class R, class S, bool UPDATE>
 __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, const R* __restrict__ Ad,
                                                     const R* __restrict__ Dinv, const R* __restrict__ b,
                                                     const R* __restrict__ tb, R* x, R* rr,
-                                                    const int32_t* __restrict__ list, int64_t nlist, int FB,
+                                                    const int4* __restrict__ rec, int64_t n, int FB,
                                                     const int* stop) {
   if (stop && *stop) return;
-  extern __shared__ unsigned char sraw[];
-  const int d = s.d, nc = s.n_c, mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s);
-  R* As = (R*)sraw;                  // [FB][2][slab]
-  R* xT = As + FB * 2 * slab;        // [FB][2][nc]
+  extern __shared__ __align__(16) unsigned char sraw[];
+  const int nc = s.n_c, mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), ds = dinv_stride(s);
+  int* rc = (int*)sraw;              // [FB][16] facet records
+  R* As = (R*)(rc + FB * 16);        // [FB][2][slab]  (16-byte aligned)
+  R* Di = As + FB * 2 * slab;        // [FB][ds]
+  R* xT = Di + FB * ds;              // [FB][2][nc]
   R* yS = xT + FB * 2 * nc;          // [FB][2][mF]
   R* rF = yS + FB * 2 * mF;          // [FB][mF]
-  int* rk = (int*)(rF + FB * mF);    // [FB]
-  int* TT = rk + FB;                 // [FB][2]
-  int* ff = TT + 2 * FB;             // [FB][2]
   const int64_t base = (int64_t)blockIdx.x * FB;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  if (tid < FB) {
-    int64_t li = base + tid;
-    int r = -1;
-    if (li < nlist) r = list ? list[li] : (int)li;
-    rk[tid] = r;
-    if (r >= 0) {
-      TT[2 * tid] = m.fel[2 * r];
-      TT[2 * tid + 1] = m.fel[2 * r + 1];
-      ff[2 * tid] = m.floc[2 * r];
-      ff[2 * tid + 1] = m.floc[2 * r + 1];
-    }
+  for (int q = tid; q < FB * 4; q += blockDim.x) {
+    const int fb = q >> 2;
+    int4 v = make_int4(-1, -1, -1, -1);
+    if (base + fb < n) v = rec[(base + fb) * 4 + (q & 3)];
+    reinterpret_cast<int4*>(rc)[q] = v;
   }
   __syncthreads();
-  // stage the slabs: warp w copies slab fs = w, w + nwarp, ...
-  for (int fs = warp; fs < FB * 2; fs += nwarp) {
-    const int fb = fs >> 1, side = fs & 1;
-    R* dst = As + fs * slab;
-    if (rk[fb] >= 0) {
-      const R* src = Ad + adw_index(dp1, slab, mF, TT[2 * fb + side], ff[2 * fb + side], 0, 0);
-      vcopy16<R>(dst, src, slab, lane, 32);
-    } else {
-      for (int idx = lane; idx < slab; idx += 32) dst[idx] = (R)0;
-    }
-  }
-  // gather x_T of both sides: warp per (facet, side)
-  for (int fs = warp; fs < FB * 2; fs += nwarp) {
-    const int fb = fs >> 1, side = fs & 1;
-    const int r = rk[fb];
-    for (int c = lane; c < nc; c += 32) {
-      R v = 0;
-      if (r >= 0) {
-        const int f = c / mF;
-        const int32_t g = m.fsr[((int64_t)r * 2 + side) * dp1 + f];
-        v = coup_get<R>(s, L, x, g, c - f * mF);
+  // slabs and D_F^{-1}: asynchronous 16-byte copies, all issued before any is awaited
+  {
+    constexpr int V = 16 / (int)sizeof(R);
+    const int cs = slab / V, cd = ds / V;           // 16-byte chunks per slab / per D_F^{-1}
+    const int nsl = FB * 2 * cs;
+    const int ntot = nsl + (UPDATE ? FB * cd : 0);
+    for (int q = tid; q < ntot; q += blockDim.x) {
+      if (q < nsl) {
+        const int fs = q / cs, ch = q - fs * cs, fb = fs >> 1, side = fs & 1;
+        const int* rr_ = rc + fb * 16;
+        if (rr_[0] >= 0)
+          cp_async16(As + fs * slab + ch * V, Ad + adw_index(dp1, slab, mF, rr_[1 + side], rr_[3 + side], 0, 0) + ch * V);
+      } else {
+        const int qq = q - nsl, fb = qq / cd, ch = qq - fb * cd;
+        const int r = rc[fb * 16];
+        if (r >= 0) cp_async16(Di + fb * ds + ch * V, Dinv + (int64_t)r * ds + ch * V);
       }
-      xT[fs * nc + c] = v;
     }
   }
+  for (int q = tid; q < FB * 2 * nc; q += blockDim.x) {
+    const int fs = q / nc, c = q - fs * nc, fb = fs >> 1, side = fs & 1;
+    const int* rr_ = rc + fb * 16;
+    R v = 0;
+    if (rr_[0] >= 0) {
+      const int f = c / mF;
+      v = coup_get<R>(s, L, x, rr_[5 + side * dp1 + f], c - f * mF);
+    }
+    xT[q] = v;
+  }
+  for (int q = tid; q < FB * mF; q += blockDim.x) {
+    const int fb = q / mF, t = q - fb * mF;
+    const int r = rc[fb * 16];
+    R v = 0;
+    if (r >= 0) {
+      const int64_t gi = coup_idx<R>(s, L, r, t);
+      v = b[gi] - (tb ? tb[gi] : (R)0);
+    }
+    rF[q] = v;
+  }
+  cp_async_wait_all();
   __syncthreads();
   for (int q = tid; q < FB * 2 * mF; q += blockDim.x) {
     const int fs = q / mF, t = q - fs * mF;
@@ -670,23 +817,21 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
   __syncthreads();
   for (int q = tid; q < FB * mF; q += blockDim.x) {
     const int fb = q / mF, t = q - fb * mF;
-    const int r = rk[fb];
-    if (r < 0) continue;
-    const int64_t gi = coup_idx<R>(s, L, r, t);
-    R v = b[gi] - (tb ? tb[gi] : (R)0) - yS[(fb * 2) * mF + t] - yS[(fb * 2 + 1) * mF + t];
+    const int r = rc[fb * 16];
+    const R v = rF[q] - yS[(fb * 2) * mF + t] - yS[(fb * 2 + 1) * mF + t];
     if (UPDATE) rF[q] = v;
-    else rr[gi] = v;
+    else if (r >= 0) rr[coup_idx<R>(s, L, r, t)] = v;
   }
   if (UPDATE) {
     __syncthreads();
     for (int q = tid; q < FB * mF; q += blockDim.x) {
       const int fb = q / mF, t = q - fb * mF;
-      const int r = rk[fb];
+      const int r = rc[fb * 16];
       if (r < 0) continue;
-      const R* Di = Dinv + (int64_t)r * mF * mF + t * mF;
+      const R* Dr = Di + fb * ds + t * mF;
       const R* rv = rF + fb * mF;
       R v = 0;
-      for (int j = 0; j < mF; ++j) v += Di[j] * rv[j];
+      for (int j = 0; j < mF; ++j) v += Dr[j] * rv[j];
       x[coup_idx<R>(s, L, r, t)] += v;
     }
   }
@@ -816,17 +961,18 @@ static void vcycle(PrecData<R>& P, int l, const int* stop, cudaStream_t st) {
 
 template <class R>
 static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* b,
-                              const R* tb, R* x, R* rr, const int32_t* list, int64_t n, bool update,
+                              const R* tb, R* x, R* rr, int64_t first, int64_t n, bool update,
                               const int* stop, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const int slab = slab_pad(s);
+  const int slab = slab_pad(s), ds = dinv_stride(s);
   int FB = 256 / (2 * s.mF);
   const int budget = 48 * 1024;
-  while (FB > 1 && (size_t)FB * 2 * slab * sizeof(R) > (size_t)budget) --FB;
+  while (FB > 1 && (size_t)FB * (2 * slab + ds) * sizeof(R) > (size_t)budget) --FB;
   if (FB < 1) FB = 1;
   const int threads = 256;
-  size_t sm = (size_t)FB * (2 * slab + 2 * s.n_c + 2 * s.mF + s.mF) * sizeof(R) + (size_t)FB * 5 * sizeof(int) + 16;
+  size_t sm = (size_t)FB * (2 * slab + ds + 2 * s.n_c + 2 * s.mF + s.mF) * sizeof(R) + (size_t)FB * 16 * sizeof(int) + 32;
   int64_t blocks = (n + FB - 1) / FB;
+  const int4* rec = m.frec + first * 4;
   dispatch_sizes(s, [&](auto sz) {
     using SZ = decltype(sz);
     static bool set = false;
@@ -838,10 +984,10 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
     const int cls = update ? PROF_FACET_GS : PROF_FACET_RES;
     prof_begin(cls, st);
     if (update)
-      k_facet_step<R, SZ, true><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, list, n,
-                                                                        FB, stop);
+      k_facet_step<R, SZ, true><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, rec, n, FB,
+                                                                        stop);
     else
-      k_facet_step<R, SZ, false><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, list, n,
+      k_facet_step<R, SZ, false><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, rec, n,
                                                                          FB, stop);
     // algorithmic bytes per facet: the facet's rows of A^d from both elements, D_F^{-1}, b, tb,
     // x_F read and written (update) or rr_F written (residual)
@@ -914,8 +1060,8 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   const int64_t* co = P.colour_off;
   for (int sw = 0; sw < P.smooth; ++sw)
     for (int c = 0; c < P.ncol; ++c)
-      facet_step<R>(s, m, L, P, b, tb, x, nullptr, P.colour_list + co[c], co[c + 1] - co[c], true, stop, st);
-  facet_step<R>(s, m, L, P, b, tb, x, P.rr, nullptr, L.nint, false, stop, st);
+      facet_step<R>(s, m, L, P, b, tb, x, nullptr, co[c], co[c + 1] - co[c], true, stop, st);
+  facet_step<R>(s, m, L, P, b, tb, x, P.rr, 0, L.nint, false, stop, st);
   const int top = P.nlev - 1;
   prof_begin(PROF_GMG, st);
   k_embed_T<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.vf_ptr, P.vf_idx, P.nP1, P.rr, P.pb[top], stop);
@@ -924,7 +1070,7 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   prof_end(PROF_GMG, 0.0, 0.0, st);
   for (int sw = 0; sw < P.smooth; ++sw)
     for (int c = P.ncol - 1; c >= 0; --c)
-      facet_step<R>(s, m, L, P, b, tb, x, nullptr, P.colour_list + co[c], co[c + 1] - co[c], true, stop, st);
+      facet_step<R>(s, m, L, P, b, tb, x, nullptr, co[c], co[c + 1] - co[c], true, stop, st);
 }
 
 // z = Khat^{-1} r (eq. mhatinvfactor, two applications of Ahat^{-1}, reading R3).
@@ -1162,9 +1308,9 @@ cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double*
 }
 
 // ---------------------------------------------------------------- explicit instantiations
-template cudaError_t launch_condense<float>(const ElemSizes&, const DevTables&, const DevMesh&, double, double*,
+template cudaError_t launch_condense<float>(const ElemSizes&, const DevTables&, const DevMesh&, double, KOp,
                                             float*, float*, float*, double*, int64_t, cudaStream_t);
-template cudaError_t launch_condense<double>(const ElemSizes&, const DevTables&, const DevMesh&, double, double*,
+template cudaError_t launch_condense<double>(const ElemSizes&, const DevTables&, const DevMesh&, double, KOp,
                                              double*, double*, double*, double*, int64_t, cudaStream_t);
 template cudaError_t launch_facet_blocks<float>(const ElemSizes&, const DevMesh&, const float*, float*, cudaStream_t);
 template cudaError_t launch_facet_blocks<double>(const ElemSizes&, const DevMesh&, const double*, double*,

@@ -37,7 +37,12 @@ struct DevMesh {
   const int32_t* fel;        // [nint][2] the two elements of each interior facet
   const int32_t* floc;       // [nint][2] local facet index in each element
   const int32_t* fsr;        // [nint][2][d+1] interior ranks of the facets of each side element
+  // facet records in colour order (64 bytes each): [0] interior rank r, [1..2] the two elements,
+  // [3..4] local facet indices, [5..] interior ranks of the facets of element 0 (d+1), then of
+  // element 1 (d+1); unused entries -1
+  const int4* frec;
 };
+
 
 // Compile-time element sizes for the (d, k) combinations with specialised kernels; the
 // members mirror ElemSizes so kernels can take either (runtime sizes as the fallback).
@@ -69,6 +74,7 @@ __host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
 template <class S> __host__ __device__ inline int slab_pad(const S& s) { return pad4(s.n_c * s.mF); }
 template <class S> __host__ __device__ inline int g_stride(const S& s) { return pad4(s.n_bub * s.n_c); }
 template <class S> __host__ __device__ inline int a_stride(const S& s) { return pad4(s.n_bub * s.n_bub); }
+template <class S> __host__ __device__ inline int dinv_stride(const S& s) { return pad4(s.mF * s.mF); }
 
 // A^d_T storage: per element, facet slab f (rows f*mF .. f*mF+mF-1) stored column-major,
 // Ad[(T*(d+1) + f)*slab_pad + c*mF + t] = A^d_T[f*mF + t][c], so the rows of one facet are one
@@ -85,6 +91,8 @@ struct DevTables {
   const double* Adiv;
   const double* nhat;
   const double* Bp;        // [n_p][n_u]
+  const float* Bp_hi;      // Bp split into float pairs (Bp = hi + lo to ~2^-48)
+  const float* Bp_lo;
   const double* Mu;        // [d][d][n_u][n_u]
   const double* phi_load;  // [nq][n_u][d]
   const double* xq_load;   // [nq][d]
@@ -94,8 +102,17 @@ struct DevTables {
 
 // ---------------------------------------------------------------- condensation
 // Forms A_T (packed lower FP64), A^d_T, G_T, A_oo^{-1} (precision R) for every element.
+// The operator K: A_T either in FP64 (full symmetric, AT) or as packed-lower float pairs
+// (Ahi + Alo = A_T to ~2^-48; double-float arithmetic in the apply).
+struct KOp {
+  double* AT;
+  float* Ahi;
+  float* Alo;
+};
+template <class S> __host__ __device__ inline int packed_pad(const S& s) { return pad4(s.n_A * (s.n_A + 1) / 2); }
+
 template <class R>
-cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, double* AT,
+cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K,
                             R* Ad, R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st);
 // Facet blocks D_F of A^d (sum of the two elements), inverted.
 template <class R>
@@ -104,7 +121,7 @@ cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, const R* A
 // ---------------------------------------------------------------- operators (FP64)
 // y = K x
 cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
-                           const double* AT, const double* x, double* y, const int* stop, cudaStream_t st);
+                           KOp K, const double* x, double* y, const int* stop, cudaStream_t st);
 // F = M_u c (velocity mass) on the u part; zero elsewhere
 cudaError_t launch_mass_u(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
                           const double* c, double* F, cudaStream_t st);

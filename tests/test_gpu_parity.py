@@ -98,6 +98,24 @@ def test_apply_matches_oracle(mcs, d, N, k, nu):
     h.close()
 
 
+@pytest.mark.parametrize("d,N,k,nu", [(2, 4, 2, 0.7), (2, 3, 3, 1.3), (3, 2, 2, 0.7)])
+def test_apply_mixed_double_float(mcs, d, N, k, nu):
+    """Mixed form: A_T as float pairs with double-float arithmetic, within 1e-12 of the FP64 K x."""
+    h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_MIXED, gmg_levels=1)
+    D, AT = _oracle(d, N, k, nu)
+    K = system.condensed_system(D, AT)
+    x = np.random.default_rng(2).standard_normal(D.ndof)
+    y = torch.zeros(D.ndof, dtype=torch.float64, device="cuda")
+    h.apply(torch.tensor(x, device="cuda"), y)
+    yo = K @ x
+    assert np.abs(y.cpu().numpy() - yo).max() < 1e-12 * np.abs(yo).max()
+    # stored element matrices reconstruct A_T to double-float accuracy
+    P = h.element_matrices(0, AT.shape[0])
+    il = np.tril_indices(AT.shape[1])
+    assert np.abs(P - AT[:, il[0], il[1]]).max() < 1e-13 * np.abs(AT).max()
+    h.close()
+
+
 @pytest.mark.parametrize("d,N,k,nu,lev", [(2, 8, 2, 0.7, 2), (2, 4, 3, 1.0, 1), (2, 8, 2, 1.0, 3), (3, 2, 2, 1.0, 1),
                                           (3, 4, 2, 0.5, 2)])
 def test_precond_fp64_matches_oracle(mcs, d, N, k, nu, lev):
