@@ -172,6 +172,8 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   P.rr = h->dalloc<R>(n);
   P.zz = h->dalloc<R>(n);
   P.coarse_tmp = nullptr;
+  P.err = h->dalloc<int>(1);
+  cuda_check(cudaMemset(P.err, 0, sizeof(int)), "memset");
 }
 
 void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
@@ -823,7 +825,22 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       info->rel_res_true = hv[1] > 0 ? std::sqrt(hv[0] / hv[1]) : 0.0;
       info->rel_res_precond = g_first > 0 ? g_now / g_first : 0.0;
     }
-    if (status != MCS_OK) g_err = status == MCS_ERR_BREAKDOWN ? "Krylov breakdown" : "not converged";
+    {
+      // a bounded wait inside the preconditioner that gave up marks the solve as timed out
+      int* errp = h->opt.precision == MCS_MIXED ? h->pf.err : h->pd.err;
+      int herr = 0;
+      cuda_check(cudaMemcpyAsync(&herr, errp, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
+      cuda_check(cudaStreamSynchronize(st), "sync");
+      if (herr) {
+        cuda_check(cudaMemsetAsync(errp, 0, sizeof(int), st), "memset");
+        status = MCS_ERR_TIMEOUT;
+        if (info) info->status = status;
+      }
+    }
+    if (status != MCS_OK)
+      g_err = status == MCS_ERR_BREAKDOWN ? "Krylov breakdown"
+              : status == MCS_ERR_TIMEOUT ? "an asynchronous copy in the preconditioner did not complete"
+                                          : "not converged";
     return status;
   });
 }

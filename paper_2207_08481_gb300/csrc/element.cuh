@@ -58,16 +58,20 @@ struct ElemWork {
   double* A;     // [n_A][n_A]
 };
 
+// Row stride of Bt and Ct in the workspace: odd, so that threads reading different rows of
+// 8-byte words hit different shared-memory banks.
+__host__ __device__ inline int raw_stride(const ElemSizes& s) { return s.n_raw | 1; }
+
 __host__ __device__ inline int elem_work_doubles(const ElemSizes& s) {
-  return 128 + s.n_A * s.n_raw + s.n_cc * s.n_raw + s.n_cc * s.n_A + s.n_cc * s.n_cc + s.n_A * s.n_A;
+  return 128 + s.n_A * raw_stride(s) + s.n_cc * raw_stride(s) + s.n_cc * s.n_A + s.n_cc * s.n_cc + s.n_A * s.n_A;
 }
 
 __host__ __device__ inline ElemWork elem_work_carve(const ElemSizes& s, double* base) {
   ElemWork w;
   w.geo = base;
   w.Bt = base + 128;
-  w.Ct = w.Bt + s.n_A * s.n_raw;
-  w.V = w.Ct + s.n_cc * s.n_raw;
+  w.Ct = w.Bt + s.n_A * raw_stride(s);
+  w.V = w.Ct + s.n_cc * raw_stride(s);
   w.Sc = w.V + s.n_cc * s.n_A;
   w.A = w.Sc + s.n_cc * s.n_cc;
   return w;
@@ -227,6 +231,15 @@ __host__ __device__ inline void elem_geometry(const ElemSizes& s, const double* 
   geo[101] = det;
 }
 
+// Row i and column j (j <= i) of packed lower-triangle position q = i(i+1)/2 + j.
+__host__ __device__ inline void packed_ij(int q, int& i, int& j) {
+  int r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > q) --r;
+  while ((r + 1) * (r + 2) / 2 <= q) ++r;
+  i = r;
+  j = q - r * (r + 1) / 2;
+}
+
 // Lane-parallel Cholesky of the n x n SPD matrix A (row-major, lower factor in place).
 template <class Sync>
 __host__ __device__ inline void chol_inplace(int n, double* A, int lane, int nl, Sync sync) {
@@ -252,7 +265,7 @@ template <class Sync>
 __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemTables& t, const double* X,
                                                  const int* sgn, double nu, ElemWork w, int lane, int nl,
                                                  Sync sync) {
-  const int nraw = s.n_raw, ns0 = s.n_s0, nA = s.n_A, nu_ = s.n_u, ncc = s.n_cc, d = s.d;
+  const int nraw = s.n_raw, ns0 = s.n_s0, nA = s.n_A, nu_ = s.n_u, ncc = s.n_cc, d = s.d, rs = raw_stride(s);
   if (lane == 0) elem_geometry(s, X, t.nhat, w.geo);
   sync();
   const double* L = w.geo;
@@ -262,7 +275,7 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
   const double cB = sqrt(nu / adet);
   // ---- Bt rows ----
   for (int r = lane; r < nA; r += nl) {
-    double* row = w.Bt + r * nraw;
+    double* row = w.Bt + r * rs;
     if (r < nu_) {
       for (int j = 0; j < nraw; ++j) row[j] = t.B0[r * nraw + j];
       if (r < (d + 1) * s.nF) {
@@ -290,7 +303,7 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
   }
   // ---- Ct rows: nt constraints, then rotation constraints ----
   for (int r = lane; r < ncc; r += nl) {
-    double* row = w.Ct + r * nraw;
+    double* row = w.Ct + r * rs;
     if (r < s.n_con) {
       const double* C = t.Ccon + r * nraw;
       for (int i = 0; i < s.nk; ++i)
@@ -311,34 +324,40 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
     }
   }
   sync();
-  // ---- A = Adiv + Bt Bt^T (lower triangle), V = Ct Bt^T, Sc = Ct Ct^T (lower) ----
+  // ---- one pass over A = Adiv + Bt Bt^T (lower), V = Ct Bt^T, Sc = Ct Ct^T (lower) ----
   const double cdiv = nu / (d * adet);
-  for (int t2 = lane; t2 < nA * nA; t2 += nl) {
-    int i = t2 / nA, j = t2 % nA;
-    if (j > i) continue;
-    double v = 0;
-    const double* a = w.Bt + i * nraw;
-    const double* b = w.Bt + j * nraw;
-    for (int q = 0; q < nraw; ++q) v += a[q] * b[q];
-    if (i < nu_ && j < nu_) v += cdiv * t.Adiv[i * nu_ + j];
-    w.A[i * nA + j] = v;
-  }
-  for (int t2 = lane; t2 < ncc * nA; t2 += nl) {
-    int i = t2 / nA, j = t2 % nA;
-    double v = 0;
-    const double* a = w.Ct + i * nraw;
-    const double* b = w.Bt + j * nraw;
-    for (int q = 0; q < nraw; ++q) v += a[q] * b[q];
-    w.V[i * nA + j] = v;
-  }
-  for (int t2 = lane; t2 < ncc * ncc; t2 += nl) {
-    int i = t2 / ncc, j = t2 % ncc;
-    if (j > i) continue;
-    double v = 0;
-    const double* a = w.Ct + i * nraw;
-    const double* b = w.Ct + j * nraw;
-    for (int q = 0; q < nraw; ++q) v += a[q] * b[q];
-    w.Sc[i * ncc + j] = v;
+  const int PA = nA * (nA + 1) / 2, PV = ncc * nA, PS = ncc * (ncc + 1) / 2;
+  for (int q = lane; q < PA + PV + PS; q += nl) {
+    const double *a, *b;
+    double* out;
+    double add = 0.0;
+    if (q < PA) {
+      int i, j;
+      packed_ij(q, i, j);
+      a = w.Bt + i * rs;
+      b = w.Bt + j * rs;
+      out = w.A + i * nA + j;
+      if (i < nu_) add = cdiv * t.Adiv[i * nu_ + j];
+    } else if (q < PA + PV) {
+      const int qq = q - PA, i = qq / nA, j = qq - i * nA;
+      a = w.Ct + i * rs;
+      b = w.Bt + j * rs;
+      out = w.V + i * nA + j;
+    } else {
+      int i, j;
+      packed_ij(q - PA - PV, i, j);
+      a = w.Ct + i * rs;
+      b = w.Ct + j * rs;
+      out = w.Sc + i * ncc + j;
+    }
+    double v0 = 0.0, v1 = 0.0;
+    int k2 = 0;
+    for (; k2 + 1 < nraw; k2 += 2) {
+      v0 += a[k2] * b[k2];
+      v1 += a[k2 + 1] * b[k2 + 1];
+    }
+    if (k2 < nraw) v0 += a[k2] * b[k2];
+    *out = v0 + v1 + add;
   }
   sync();
   chol_inplace(ncc, w.Sc, lane, nl, sync);
@@ -351,21 +370,18 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
     }
   }
   sync();
-  // ---- A -= Z^T Z, signs, symmetric fill ----
-  for (int t2 = lane; t2 < nA * nA; t2 += nl) {
-    int i = t2 / nA, j = t2 % nA;
-    if (j > i) continue;
+  // ---- A -= Z^T Z (packed lower), signs, symmetric fill ----
+  const int nfd = (d + 1) * s.nF;
+  for (int q = lane; q < PA; q += nl) {
+    int i, j;
+    packed_ij(q, i, j);
     double v = w.A[i * nA + j];
-    for (int q = 0; q < ncc; ++q) v -= w.V[q * nA + i] * w.V[q * nA + j];
-    int nfd = (d + 1) * s.nF;
-    double si = (i < nfd) ? (double)sgn[i / s.nF] : 1.0;
-    double sj = (j < nfd) ? (double)sgn[j / s.nF] : 1.0;
-    w.A[i * nA + j] = v * si * sj;
-  }
-  sync();
-  for (int t2 = lane; t2 < nA * nA; t2 += nl) {
-    int i = t2 / nA, j = t2 % nA;
-    if (j > i) w.A[i * nA + j] = w.A[j * nA + i];
+    for (int p = 0; p < ncc; ++p) v -= w.V[p * nA + i] * w.V[p * nA + j];
+    const double si = (i < nfd) ? (double)sgn[i / s.nF] : 1.0;
+    const double sj = (j < nfd) ? (double)sgn[j / s.nF] : 1.0;
+    v *= si * sj;
+    w.A[i * nA + j] = v;
+    w.A[j * nA + i] = v;
   }
   sync();
 }

@@ -26,6 +26,14 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem_dst, const void* gmem_src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 struct WarpSync {
   __device__ void operator()() const { __syncwarp(); }
@@ -732,9 +740,12 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
 // Facet-centric block step over the facet records rec[0..n) (colour order):
 //   r_F = b_F - tb_F - sum_{T in F} (A^d_T x_T)|_F,
 // UPDATE: x_F += D_F^{-1} r_F (block Gauss-Seidel within one colour); else rr_F = r_F.
-// FB facets per block.  Two dependent rounds of loads: the 64-byte facet records, then
-// everything else at once (A^d slabs and D_F^{-1} staged in shared memory with 16-byte
-// loads, x of both elements, b, tb); then one thread per (facet, side, row) forms the product.
+// Persistent blocks walk batches of FB facets.  (1D TMA bulk copies of the 592-byte slabs
+// measured slower than 16-byte cp.async here: the slabs are too small per request.)  Everything a batch needs (A^d slabs of both
+// elements, D_F^{-1}, x of both elements, b, tb) is fetched with asynchronous copies into one
+// of two shared-memory stages while the previous batch is computed; the 64-byte facet
+// records are read one batch ahead.  Facets of one colour share no element, so the copies
+// of batch i+1 never read values that batch i updates.
 template <class R, class S, bool UPDATE>
 __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, const R* __restrict__ Ad,
                                                     const R* __restrict__ Dinv, const R* __restrict__ b,
@@ -744,97 +755,145 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char sraw[];
   const int nc = s.n_c, mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), ds = dinv_stride(s);
-  int* rc = (int*)sraw;              // [FB][16] facet records
-  R* As = (R*)(rc + FB * 16);        // [FB][2][slab]  (16-byte aligned)
-  R* Di = As + FB * 2 * slab;        // [FB][ds]
-  R* xT = Di + FB * ds;              // [FB][2][nc]
-  R* yS = xT + FB * 2 * nc;          // [FB][2][mF]
-  R* rF = yS + FB * 2 * mF;          // [FB][mF]
-  const int64_t base = (int64_t)blockIdx.x * FB;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  for (int q = tid; q < FB * 4; q += blockDim.x) {
-    const int fb = q >> 2;
-    int4 v = make_int4(-1, -1, -1, -1);
-    if (base + fb < n) v = rec[(base + fb) * 4 + (q & 3)];
-    reinterpret_cast<int4*>(rc)[q] = v;
-  }
-  __syncthreads();
-  // slabs and D_F^{-1}: asynchronous 16-byte copies, all issued before any is awaited
-  {
-    constexpr int V = 16 / (int)sizeof(R);
-    const int cs = slab / V, cd = ds / V;           // 16-byte chunks per slab / per D_F^{-1}
-    const int nsl = FB * 2 * cs;
-    const int ntot = nsl + (UPDATE ? FB * cd : 0);
-    for (int q = tid; q < ntot; q += blockDim.x) {
-      if (q < nsl) {
-        const int fs = q / cs, ch = q - fs * cs, fb = fs >> 1, side = fs & 1;
-        const int* rr_ = rc + fb * 16;
-        if (rr_[0] >= 0)
-          cp_async16(As + fs * slab + ch * V, Ad + adw_index(dp1, slab, mF, rr_[1 + side], rr_[3 + side], 0, 0) + ch * V);
-      } else {
-        const int qq = q - nsl, fb = qq / cd, ch = qq - fb * cd;
+  // stage layout (both stages identical, 16-byte aligned pieces)
+  unsigned char* sbase = sraw;
+  const int rec_b = FB * 16 * (int)sizeof(int);
+  const int as_b = FB * 2 * slab * (int)sizeof(R);
+  const int di_b = UPDATE ? FB * ds * (int)sizeof(R) : 0;
+  const int xt_b = ((FB * 2 * nc * (int)sizeof(R)) + 15) / 16 * 16;
+  const int bb_b = ((FB * mF * (int)sizeof(R)) + 15) / 16 * 16;
+  const int stage_b = rec_b + as_b + di_b + xt_b + 2 * bb_b;
+  R* yS = (R*)(sbase + 2 * stage_b);       // [FB][2][mF]
+  R* rF = yS + FB * 2 * mF;                // [FB][mF]
+  auto RC = [&](int st) { return (int*)(sbase + st * stage_b); };
+  auto AS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b); };
+  auto DI = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b); };
+  auto XT = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b + di_b); };
+  auto BS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b + di_b + xt_b); };
+  auto TS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b + di_b + xt_b + bb_b); };
+  constexpr int V = 16 / (int)sizeof(R);
+  const int cs = slab / V, cd = ds / V;
+  const int tid = threadIdx.x;
+  const int64_t nb = (n + FB - 1) / FB;
+
+  auto load_records = [&](int st, int64_t bi) {
+    int* rc = RC(st);
+    for (int q = tid; q < FB * 4; q += blockDim.x) {
+      const int fb = q >> 2;
+      int4 v = make_int4(-1, -1, -1, -1);
+      if (bi * FB + fb < n) v = rec[(bi * FB + fb) * 4 + (q & 3)];
+      reinterpret_cast<int4*>(rc)[q] = v;
+    }
+  };
+  auto issue = [&](int st) {
+    const int* rc = RC(st);
+    R* As = AS(st);
+    R* Di = DI(st);
+    R* xT = XT(st);
+    R* bS = BS(st);
+    R* tS = TS(st);
+    for (int q = tid; q < FB * 2 * cs; q += blockDim.x) {
+      const int fs = q / cs, ch = q - fs * cs, fb = fs >> 1, side = fs & 1;
+      const int* r_ = rc + fb * 16;
+      if (r_[0] >= 0)
+        cp_async16(As + fs * slab + ch * V, Ad + adw_index(dp1, slab, mF, r_[1 + side], r_[3 + side], 0, 0) + ch * V);
+    }
+    if (UPDATE)
+      for (int q = tid; q < FB * cd; q += blockDim.x) {
+        const int fb = q / cd, ch = q - fb * cd;
         const int r = rc[fb * 16];
         if (r >= 0) cp_async16(Di + fb * ds + ch * V, Dinv + (int64_t)r * ds + ch * V);
       }
-    }
-  }
-  for (int q = tid; q < FB * 2 * nc; q += blockDim.x) {
-    const int fs = q / nc, c = q - fs * nc, fb = fs >> 1, side = fs & 1;
-    const int* rr_ = rc + fb * 16;
-    R v = 0;
-    if (rr_[0] >= 0) {
+    for (int q = tid; q < FB * 2 * nc; q += blockDim.x) {
+      const int fs = q / nc, c = q - fs * nc, fb = fs >> 1, side = fs & 1;
+      const int* r_ = rc + fb * 16;
+      int32_t g = -1;
       const int f = c / mF;
-      v = coup_get<R>(s, L, x, rr_[5 + side * dp1 + f], c - f * mF);
+      if (r_[0] >= 0) g = r_[5 + side * dp1 + f];
+      if (g >= 0) cp_async_small<sizeof(R)>(xT + q, x + coup_idx<R>(s, L, g, c - f * mF));
+      else xT[q] = (R)0;
     }
-    xT[q] = v;
-  }
-  for (int q = tid; q < FB * mF; q += blockDim.x) {
-    const int fb = q / mF, t = q - fb * mF;
-    const int r = rc[fb * 16];
-    R v = 0;
-    if (r >= 0) {
-      const int64_t gi = coup_idx<R>(s, L, r, t);
-      v = b[gi] - (tb ? tb[gi] : (R)0);
+    for (int q = tid; q < FB * mF; q += blockDim.x) {
+      const int fb = q / mF, t = q - fb * mF;
+      const int r = rc[fb * 16];
+      if (r >= 0) {
+        const int64_t gi = coup_idx<R>(s, L, r, t);
+        cp_async_small<sizeof(R)>(bS + q, b + gi);
+        if (tb) cp_async_small<sizeof(R)>(tS + q, tb + gi);
+        else tS[q] = (R)0;
+      } else {
+        bS[q] = (R)0;
+        tS[q] = (R)0;
+      }
     }
-    rF[q] = v;
+  };
+
+  int64_t bi = blockIdx.x;
+  int st = 0;
+  if (bi < nb) {
+    load_records(0, bi);
+    __syncthreads();
+    issue(0);
   }
-  cp_async_wait_all();
-  __syncthreads();
-  for (int q = tid; q < FB * 2 * mF; q += blockDim.x) {
-    const int fs = q / mF, t = q - fs * mF;
-    const R* A = As + fs * slab + t;
-    const R* xv = xT + fs * nc;
-    R v0 = 0, v1 = 0;
-    int c = 0;
+  cp_async_commit();
+  while (bi < nb) {
+    const int64_t nbi = bi + gridDim.x;
+    const int ns = st ^ 1;
+    if (nbi < nb) load_records(ns, nbi);
+    __syncthreads();
+    if (nbi < nb) issue(ns);
+    cp_async_commit();
+    cp_async_wait_group<1>();
+    __syncthreads();
+    // ---- compute batch bi from stage st
+    const int* rc = RC(st);
+    const R* As = AS(st);
+    const R* Di = DI(st);
+    const R* xT = XT(st);
+    const R* bS = BS(st);
+    const R* tS = TS(st);
+    for (int q = tid; q < FB * 2 * mF; q += blockDim.x) {
+      const int fs = q / mF, t = q - fs * mF;
+      const R* A = As + fs * slab + t;
+      const R* xv = xT + fs * nc;
+      R v0 = 0, v1 = 0;
+      int c = 0;
 #pragma unroll 4
-    for (; c + 1 < nc; c += 2) {
-      v0 += A[c * mF] * xv[c];
-      v1 += A[(c + 1) * mF] * xv[c + 1];
+      for (; c + 1 < nc; c += 2) {
+        v0 += A[c * mF] * xv[c];
+        v1 += A[(c + 1) * mF] * xv[c + 1];
+      }
+      if (c < nc) v0 += A[c * mF] * xv[c];
+      yS[q] = v0 + v1;
     }
-    if (c < nc) v0 += A[c * mF] * xv[c];
-    yS[q] = v0 + v1;
-  }
-  __syncthreads();
-  for (int q = tid; q < FB * mF; q += blockDim.x) {
-    const int fb = q / mF, t = q - fb * mF;
-    const int r = rc[fb * 16];
-    const R v = rF[q] - yS[(fb * 2) * mF + t] - yS[(fb * 2 + 1) * mF + t];
-    if (UPDATE) rF[q] = v;
-    else if (r >= 0) rr[coup_idx<R>(s, L, r, t)] = v;
-  }
-  if (UPDATE) {
     __syncthreads();
     for (int q = tid; q < FB * mF; q += blockDim.x) {
       const int fb = q / mF, t = q - fb * mF;
       const int r = rc[fb * 16];
-      if (r < 0) continue;
-      const R* Dr = Di + fb * ds + t * mF;
-      const R* rv = rF + fb * mF;
-      R v = 0;
-      for (int j = 0; j < mF; ++j) v += Dr[j] * rv[j];
-      x[coup_idx<R>(s, L, r, t)] += v;
+      const R v = bS[q] - tS[q] - yS[(fb * 2) * mF + t] - yS[(fb * 2 + 1) * mF + t];
+      if (UPDATE) rF[q] = v;
+      else if (r >= 0) rr[coup_idx<R>(s, L, r, t)] = v;
     }
+    if (UPDATE) {
+      __syncthreads();
+      for (int q = tid; q < FB * mF; q += blockDim.x) {
+        const int fb = q / mF, t = q - fb * mF;
+        const int r = rc[fb * 16];
+        if (r < 0) continue;
+        const R* Dr = Di + fb * ds + t * mF;
+        const R* rv = rF + fb * mF;
+        R v = 0;
+        for (int j = 0; j < mF; ++j) v += Dr[j] * rv[j];
+        // x_F before the update is the facet's own entry in the gathered x of side 0
+        const int f0 = rc[fb * 16 + 3];
+        x[coup_idx<R>(s, L, r, t)] = xT[(fb * 2) * nc + f0 * mF + t] + v;
+      }
+    }
+    __syncthreads();
+    st = ns;
+    bi = nbi;
   }
+  cp_async_wait_all();
 }
 
 // xbar = E^d^T rr  (gather per P1 dof over incident facets)
@@ -939,6 +998,7 @@ static void vcycle(PrecData<R>& P, int l, const int* stop, cudaStream_t st) {
     k_coarse<R><<<g, bs, 0, st>>>(G.n, P.coarse_inv, P.pb[0], P.px[0], stop);
     return;
   }
+
   const R* va = (const R*)G.val;
   const R* di = (const R*)G.dl1inv;
   R* x = P.px[l];
@@ -960,27 +1020,41 @@ static void vcycle(PrecData<R>& P, int l, const int* stop, cudaStream_t st) {
 }
 
 template <class R>
+static size_t facet_step_smem(const ElemSizes& s, int FB, bool update) {
+  const int slab = slab_pad(s), ds = dinv_stride(s);
+  auto up16 = [](size_t v) { return (v + 15) / 16 * 16; };
+  const size_t stage = (size_t)FB * 16 * sizeof(int) + (size_t)FB * 2 * slab * sizeof(R) +
+                       (update ? (size_t)FB * ds * sizeof(R) : 0) + up16((size_t)FB * 2 * s.n_c * sizeof(R)) +
+                       2 * up16((size_t)FB * s.mF * sizeof(R));
+  return 2 * stage + (size_t)FB * 3 * s.mF * sizeof(R) + 16;
+}
+
+template <class R>
 static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* b,
                               const R* tb, R* x, R* rr, int64_t first, int64_t n, bool update,
                               const int* stop, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const int slab = slab_pad(s), ds = dinv_stride(s);
   int FB = 256 / (2 * s.mF);
-  const int budget = 48 * 1024;
-  while (FB > 1 && (size_t)FB * (2 * slab + ds) * sizeof(R) > (size_t)budget) --FB;
   if (FB < 1) FB = 1;
+  while (FB > 1 && facet_step_smem<R>(s, FB, update) > 96 * 1024) --FB;
   const int threads = 256;
-  size_t sm = (size_t)FB * (2 * slab + ds + 2 * s.n_c + 2 * s.mF + s.mF) * sizeof(R) + (size_t)FB * 16 * sizeof(int) + 32;
-  int64_t blocks = (n + FB - 1) / FB;
+  const size_t sm = facet_step_smem<R>(s, FB, update);
+  const int64_t nb = (n + FB - 1) / FB;
   const int4* rec = m.frec + first * 4;
   dispatch_sizes(s, [&](auto sz) {
     using SZ = decltype(sz);
-    static bool set = false;
-    if (!set) {
+    static int per_sm[2] = {0, 0};
+    const int ui = update ? 1 : 0;
+    if (!per_sm[ui]) {
       cudaFuncSetAttribute(k_facet_step<R, SZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(k_facet_step<R, SZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      set = true;
+      int occ = 0;
+      if (update) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step<R, SZ, true>, threads, sm);
+      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step<R, SZ, false>, threads, sm);
+      per_sm[ui] = occ > 0 ? occ : 1;
     }
+    int64_t blocks = (int64_t)sm_count() * per_sm[ui];
+    if (blocks > nb) blocks = nb;
     const int cls = update ? PROF_FACET_GS : PROF_FACET_RES;
     prof_begin(cls, st);
     if (update)

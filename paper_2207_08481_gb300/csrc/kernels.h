@@ -171,6 +171,7 @@ struct PrecData {
   const double* coarse_inv;    // [n0][n0] FP64
   // work vectors (R), all length ndof unless noted
   R *b, *x, *t, *rr, *zz;
+  int* err;  // device flag: set when a bounded wait on an asynchronous copy gave up
   R *pb[12], *px[12], *pr[12], *ptmp[12];  // GMG vectors per level
   double* coarse_tmp;  // [n0]
 };
