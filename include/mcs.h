@@ -68,8 +68,11 @@ typedef struct {
   int gmg_smooth;     /* l1-Jacobi sweeps before and after each coarse-grid correction (2) */
   double rtol;        /* stop when ||r||_{Khat^{-1}} <= rtol * ||F - K x0||_{Khat^{-1}} (1e-8) */
   int maxit;          /* total MinRes iterations (1000) */
-  int max_refine;     /* MCS_MIXED: outer FP64 refinement cycles (8) */
+  int max_refine;     /* outer refinement cycles after the first (8); MCS_FP64 uses at most 2 of them */
   double inner_rtol;  /* MCS_MIXED: relative reduction per refinement cycle (1e-5) */
+  int residual_dd;    /* residual of each refinement cycle in double-double: 1 always, 0 never (plain
+                         FP64 K x, whose rounding floors the attainable residual near 1e-12 relative
+                         for k = 4), -1 auto: when rtol < 1e-10 (-1) */
 } mcs_options;
 
 typedef struct {
@@ -85,7 +88,7 @@ typedef struct {
 
 typedef struct {
   int iterations;            /* MinRes iterations (all refinement cycles) */
-  int refinements;           /* outer cycles (1 for MCS_FP64) */
+  int refinements;           /* outer cycles (each restarts MinRes from the recomputed residual) */
   int status;                /* MCS_OK, MCS_ERR_NOT_CONVERGED or MCS_ERR_BREAKDOWN */
   double rel_res_precond;    /* ||F - K x||_{Khat^{-1}} / ||F - K x0||_{Khat^{-1}} */
   double rel_res_true;       /* ||F - K x||_2 / ||F||_2 (FP64) */
@@ -101,7 +104,7 @@ int mcs_default_options(mcs_options* o);
 /* Set-up on the Kuhn triangulation of [0,1]^dim with N cells per direction
  * (Sec. 7 uses unstructured meshes; the synthetic workloads use this nested
  * family so that the conforming space has a geometric multigrid hierarchy).
- * dim in {2, 3}, k >= 2 (Sec. 3; k = 1 is the variant of Sec. 6, not supported),
+ * dim in {2, 3}, k = 2..4 (Sec. 3; k = 1 is the variant of Sec. 6, not supported),
  * nu > 0 as printed in eq. (stokes).  stream: a cudaStream_t (NULL = default).
  * Builds mesh, facets, dof maps, colouring and the multigrid hierarchy on the
  * host and uploads them; allocates the resident operators.  Synchronous.
@@ -155,13 +158,21 @@ int mcs_mass_velocity(mcs_handle* h, const double* c, double* F);
 
 /* y = K x (eq. femSPmat), FP64, device vectors [ndof]. */
 int mcs_apply(mcs_handle* h, const double* x, double* y);
+/* r = F - K x, device vectors [ndof], with every element product and the sum of a facet dof's
+ * two element contributions carried in double-double and rounded once, so r is accurate to a
+ * few units in its own last place even where F and K x cancel.  MCS_MIXED: K uses the stored
+ * float pairs hi + lo of A_T, taken as exact.  r may alias F, not x.  Uses a workspace of the
+ * handle (calls on one handle are serialised by its stream). */
+int mcs_residual(mcs_handle* h, const double* F, const double* x, double* r);
 /* z = Khat^{-1} r (eq. mhatinvfactor applied with two Ahat^{-1}), device vectors [ndof];
  * the pressure part of z is not mean-corrected. */
 int mcs_precond(mcs_handle* h, const double* r, double* z);
-/* Solves K x = F by preconditioned MinRes (FP64 recurrence; MCS_MIXED adds FP64
- * iterative refinement around FP32-preconditioned cycles).  x: in = initial guess,
- * out = solution with mean-zero pressure.  Device vectors.  Synchronises with the
- * stream to read the convergence state.  info may be NULL.  Returns MCS_OK, or
+/* Solves K x = F by preconditioned MinRes (FP64 recurrence) inside outer refinement cycles:
+ * each cycle recomputes r = F - K x (in double-double as mcs_residual when residual_dd selects
+ * it, so the attainable accuracy is not limited by the rounding of K x); MCS_MIXED runs
+ * FP32-preconditioned cycles, each asked for at least inner_rtol reduction.
+ * x: in = initial guess, out = solution with mean-zero pressure.  Device vectors.  Synchronises
+ * with the stream to read the convergence state.  info may be NULL.  Returns MCS_OK, or
  * MCS_ERR_NOT_CONVERGED / MCS_ERR_BREAKDOWN (x then holds the last iterate). */
 int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info);
 /* Same as mcs_solve with HOST vectors F, x [ndof]: copies F and x in, solves, copies x out. */
@@ -181,6 +192,13 @@ typedef struct {
 } mcs_kernel_stat;
 int mcs_profile(mcs_handle* h, int enable);
 int mcs_profile_read(mcs_handle* h, mcs_kernel_stat* out, int max_n);
+
+/* Kernel-launch accounting (diagnostics): *count receives the number of kernels this library
+ * has launched in this process, over all handles and threads, since it was loaded.  A kernel
+ * that runs as a node of one of the library's CUDA graphs counts once per graph launch;
+ * launches recorded while a graph is being captured do not count.  Copies and memsets are not
+ * kernels and do not count.  Host-only; never fails except for a NULL count (INVALID_ARG). */
+int mcs_launch_count(uint64_t* count);
 
 /* Condensed element matrices without any device allocation, for callers that cannot let the
  * library allocate at call time (work enqueued during CUDA-graph stream capture, where

@@ -62,6 +62,7 @@ void validate_options(const mcs_options& o) {
   if (o.smooth_steps < 0 || o.smooth_steps > 16) throw McsError(MCS_ERR_INVALID_ARG, "smooth_steps");
   if (o.gmg_smooth < 1 || o.gmg_smooth > 16) throw McsError(MCS_ERR_INVALID_ARG, "gmg_smooth");
   if (!(o.rtol > 0) || o.maxit < 1) throw McsError(MCS_ERR_INVALID_ARG, "rtol/maxit");
+  if (o.residual_dd < -1 || o.residual_dd > 1) throw McsError(MCS_ERR_INVALID_ARG, "residual_dd");
 }
 
 template <class R>
@@ -335,6 +336,7 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
     h->K.AT = h->dalloc<double>(m.ne * (int64_t)s.n_A * s.n_A);
   }
   for (int i = 0; i < 11; ++i) h->kv[i] = h->dalloc<double>(L.ndof);
+  h->ydd = h->dalloc<double>(4 * L.ndof);
   cuda_check(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   h->scratch = h->dalloc<double>(4096);
   cuda_check(cudaMemset(h->scratch, 0, sizeof(double) * 4096), "memset");
@@ -347,12 +349,18 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (h->cond_scratch_doubles / ((int64_t)nsm * 8) * 8 > maxsm)
     h->cond_scratch = h->dalloc<double>(h->cond_scratch_doubles);
-  cuda_check(cudaDeviceSynchronize(), "setup");
+  // wait for this set-up's own work only (legacy-stream memsets, the handle's stream): work of
+  // other handles on other streams keeps running
+  cuda_check(cudaStreamSynchronize(0), "setup");
+  cuda_check(cudaStreamSynchronize(h->stream), "setup");
 }
 
 mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* stream) {
   if (dim < 2 || dim > 3) throw McsError(MCS_ERR_UNSUPPORTED, "dim must be 2 or 3");
-  if (k < 2 || k > 6) throw McsError(MCS_ERR_UNSUPPORTED, "k must be in 2..6");
+  // k >= 5: the dual BDM basis of the dof contract (monomial interior moments) makes A_T so badly
+  // scaled (2D k = 6: entries near 1e11 around a facet Schur complement near 1e2) that the
+  // condensed blocks lose about 10 digits; 3D k >= 5 also exceeds the per-thread bubble block
+  if (k < 2 || k > 4) throw McsError(MCS_ERR_UNSUPPORTED, "k must be in 2..4");
   if (!(nu > 0)) throw McsError(MCS_ERR_INVALID_ARG, "nu must be positive");
   auto h = std::make_unique<mcs_handle>();
   h->d = dim;
@@ -388,6 +396,7 @@ int mcs_default_options(mcs_options* o) {
   o->maxit = 1000;
   o->max_refine = 8;
   o->inner_rtol = 1e-5;
+  o->residual_dd = -1;
   return MCS_OK;
 }
 
@@ -669,6 +678,16 @@ int mcs_apply(mcs_handle* h, const double* x, double* y) {
   });
 }
 
+int mcs_residual(mcs_handle* h, const double* F, const double* x, double* r) {
+  return guarded([&]() -> int {
+    if (!h || !F || !x || !r) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
+    if (!h->condensed) throw McsError(MCS_ERR_INVALID_ARG, "mcs_condense has not been called");
+    if (r == x) throw McsError(MCS_ERR_INVALID_ARG, "r must not alias x");
+    cuda_check(launch_residual_dd(h->es, h->dt, h->dm, h->L, h->K, F, x, h->ydd, r, h->stream), "residual");
+    return MCS_OK;
+  });
+}
+
 static void precond_any(mcs_handle* h, const double* r, double* z, const int* stop, cudaStream_t st = nullptr) {
   if (!st) st = h->stream;
   cudaError_t e = (h->opt.precision == MCS_MIXED)
@@ -718,15 +737,32 @@ void capture_iterations(mcs_handle* h, double* x_acc) {
   cudaStream_t cs = h->cap_stream;
   cuda_check(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   cudaGraph_t g = nullptr;
+  g_capturing = true;
   try {
     minres_iteration(h, cs, v_old, v, z, zn, w_old, w, Kz, x_acc);
     minres_iteration(h, cs, v_old, v, z, zn, w_old, w, Kz, x_acc);
   } catch (...) {
+    g_capturing = false;
     cudaStreamEndCapture(cs, &g);
     if (g) cudaGraphDestroy(g);
     throw;
   }
+  g_capturing = false;
   cuda_check(cudaStreamEndCapture(cs, &g), "cudaStreamEndCapture");
+  size_t nn = 0;
+  cudaError_t ce = cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (ce == cudaSuccess && nn) ce = cudaGraphGetNodes(g, nodes.data(), &nn);
+  uint64_t nk = 0;
+  for (size_t i = 0; ce == cudaSuccess && i < nn; ++i) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+  }
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cuda_check(ce, "cudaGraphGetNodes");
+  }
+  h->graph_kernels = nk;
   cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
   cudaGraphDestroy(g);
   cuda_check(e, "cudaGraphInstantiate");
@@ -763,7 +799,10 @@ void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double floor_
     cuda_check(cudaStreamSynchronize(st), "sync");
     if (h->S_host->stop) break;
     if (graphs) {
-      for (int q = 0; q < check_every / 2; ++q) cuda_check(cudaGraphLaunch(h->gexec, st), "cudaGraphLaunch");
+      for (int q = 0; q < check_every / 2; ++q) {
+        cuda_check(cudaGraphLaunch(h->gexec, st), "cudaGraphLaunch");
+        note_launches(h->graph_kernels);
+      }
     } else {
       for (int q = 0; q < check_every; ++q) minres_iteration(h, st, v_old, v, z, zn, w_old, w, Kz, x_acc);
     }
@@ -783,15 +822,23 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
     double* xi = h->kv[10];  // the iterate (fixed address for the captured iterations)
     cuda_check(cudaMemcpyAsync(xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy x");
     const bool mixed = h->opt.precision == MCS_MIXED;
-    // FP64 form: one cycle to rtol plus a check of the true residual.  Mixed form: FP64
-    // iterative refinement, each cycle asked for at least inner_rtol reduction.
-    const int max_cycles = mixed ? std::max(2, h->opt.max_refine + 1) : 2;
+    // FP64 form: cycles to rtol, restarted from the recomputed residual (at most 3).  Mixed
+    // form: iterative refinement, each cycle asked for at least inner_rtol reduction.
+    const int max_cycles = mixed ? std::max(2, h->opt.max_refine + 1) : std::min(3, std::max(2, h->opt.max_refine + 1));
     const double floor_rtol = mixed ? h->opt.inner_rtol : 0.0;
+    const bool dd = h->opt.residual_dd == 1 || (h->opt.residual_dd == -1 && h->opt.rtol < 1e-10);
+    auto residual = [&](const double* xv) {  // r = F - K xv
+      if (dd) {
+        cuda_check(launch_residual_dd(h->es, h->dt, h->dm, h->L, h->K, F, xv, h->ydd, r, st), "residual");
+      } else {
+        cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->K, xv, r, nullptr, st), "apply");
+        cuda_check(launch_axpby(n, 1.0, F, -1.0, r, st), "axpby");
+      }
+    };
     int total_it = 0, cycles = 0, status = MCS_ERR_NOT_CONVERGED;
     double g_first = -1.0, g_now = 0.0;
     while (cycles < max_cycles) {
-      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->K, xi, r, nullptr, st), "apply");
-      cuda_check(launch_axpby(n, 1.0, F, -1.0, r, st), "axpby");
+      residual(xi);
       minres_cycle(h, r, xi, floor_rtol, std::max(1, h->opt.maxit - total_it), g_first);
       const MinresScalars& Sh = *h->S_host;
       g_first = Sh.g_first;
@@ -811,8 +858,7 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
     cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, xi, h->scratch, h->total_adet, nullptr, st), "mean");
     cuda_check(cudaMemcpyAsync(x, xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy x");
     if (info) {
-      cuda_check(launch_apply_K(h->es, h->dt, h->dm, h->L, h->K, x, r, nullptr, st), "apply");
-      cuda_check(launch_axpby(n, 1.0, F, -1.0, r, st), "axpby");
+      residual(x);
       double* res = h->scratch + 3000;
       cuda_check(launch_dot(r, r, n, h->scratch, res, nullptr, st), "dot");
       cuda_check(launch_dot(F, F, n, h->scratch, res + 1, nullptr, st), "dot");
@@ -869,6 +915,14 @@ int mcs_profile(mcs_handle* h, int enable) {
     } else {
       h->prof.reset();
     }
+    return MCS_OK;
+  });
+}
+
+int mcs_launch_count(uint64_t* count) {
+  return guarded([&]() -> int {
+    if (!count) throw McsError(MCS_ERR_INVALID_ARG, "count is NULL");
+    *count = launch_count();
     return MCS_OK;
   });
 }

@@ -68,8 +68,10 @@ struct mcs_handle {
   double *kv[11] = {nullptr};  // Krylov vectors; kv[10] is the iterate the captured graph updates
   cudaStream_t cap_stream = nullptr;   // non-default stream for graph capture
   cudaGraphExec_t gexec = nullptr;     // two MinRes iterations
+  uint64_t graph_kernels = 0;          // kernel nodes of gexec
   bool use_graphs = true;
   double* scratch = nullptr;
+  double* ydd = nullptr;            // [4][ndof] double-double row sums of the refinement residual
   MinresScalars* S = nullptr;
   MinresScalars* S_host = nullptr;  // pinned
   double* cond_scratch = nullptr;

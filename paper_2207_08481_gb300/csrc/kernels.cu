@@ -1,4 +1,5 @@
 // Device kernels of libmcs (sm_103a).  See kernels.h for the roles.
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -120,18 +121,21 @@ cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMes
   prof_begin(PROF_CONDENSE, st);
   if (bytes <= maxsm) {
     size_t sm = (size_t)bytes;
-    cudaFuncSetAttribute(k_condense<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // the opt-in maximum, never lowered: other threads may launch this kernel with other sizes
+    cudaFuncSetAttribute(k_condense<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense<R, true>, threads, sm);
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)nsm * per_sm;
     if (blocks > m.ne) blocks = m.ne;
     k_condense<R, true><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, nu, K, Ad, G, Aoi, nullptr, slot);
+    note_launch();
   } else {
     int64_t blocks = scratch_doubles / slot;
     if (blocks < 1) return cudaErrorMemoryAllocation;
     if (blocks > m.ne) blocks = m.ne;
     k_condense<R, false><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, nu, K, Ad, G, Aoi, scratch, slot);
+    note_launch();
   }
   {
     // FP64 flops of the element condensation (products and factorisations, see element.cuh)
@@ -208,11 +212,12 @@ cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, const R* A
   if (m.nint == 0) return cudaSuccess;
   int wpb = 4;
   size_t sm = (size_t)wpb * 2 * s.mF * s.mF * sizeof(double);
-  cudaFuncSetAttribute(k_facet_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_facet_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int64_t blocks = (m.nint + wpb - 1) / wpb;
   if (blocks > 65535 * 8) blocks = 65535 * 8;
   prof_begin(PROF_FACET_BLOCKS, st);
   k_facet_blocks<R><<<(unsigned)blocks, wpb * 32, sm, st>>>(s, m, Ad, Dinv);
+  note_launch();
   prof_end(PROF_FACET_BLOCKS, (double)m.nint * (2.0 * s.mF * s.mF + s.mF * s.mF) * sizeof(R), 0.0, st);
   return cudaGetLastError();
 }
@@ -234,8 +239,10 @@ __device__ __forceinline__ int64_t local_to_global(const S& s, const Layout& L, 
 }
 
 // y = K x element by element: the blocks A_T of EB elements are staged in shared memory with
-// coalesced loads (full symmetric storage), then one thread per row forms the product.
-template <class S>
+// coalesced loads (full symmetric storage), then one thread per row forms the product.  When
+// one block does not fit in shared memory (3D, k = 4) STAGED is false and the rows are read
+// from global memory directly (thread i reads column entries i of consecutive rows: coalesced).
+template <class S, bool STAGED>
 __global__ void __launch_bounds__(256) k_apply_K(S s, DevTables t, DevMesh m, Layout L,
                                                  const double* __restrict__ AT, const double* __restrict__ x,
                                                  double* y, int EB, const int* stop) {
@@ -243,8 +250,9 @@ __global__ void __launch_bounds__(256) k_apply_K(S s, DevTables t, DevMesh m, La
   extern __shared__ double sk[];
   const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d, nfd = (s.d + 1) * s.nF;
   const int per = nA + np_, nA2 = nA * nA;
-  double* As = sk;                   // [EB][nA*nA]
-  double* xs = As + EB * nA2;        // [EB][nA + np]
+  const int64_t Tb = (int64_t)blockIdx.x * EB;
+  const double* As = STAGED ? sk : AT + Tb * nA2;   // [EB][nA*nA]
+  double* xs = STAGED ? sk + EB * nA2 : sk;           // [EB][nA + np]
   int* er = (int*)(xs + EB * per);   // [EB][4]
   float* sg = (float*)(er + EB * 4); // [EB][4]
   const int tid = threadIdx.x;
@@ -257,14 +265,14 @@ __global__ void __launch_bounds__(256) k_apply_K(S s, DevTables t, DevMesh m, La
     er[tid] = ok ? m.elem_rank[T * (d + 1) + f] : -1;
     sg[tid] = ok ? (float)m.signs[T * (d + 1) + f] : 0.f;
   }
-  {
+  if (STAGED) {
     const double2* src = reinterpret_cast<const double2*>(AT + T0 * nA2);
-    double2* dst = reinterpret_cast<double2*>(As);
+    double2* dst = reinterpret_cast<double2*>(sk);
     const int cnt = nvalid * nA2;
     if ((nA2 & 1) == 0) {
       for (int q = tid; q < cnt / 2; q += blockDim.x) dst[q] = src[q];
     } else {
-      for (int q = tid; q < cnt; q += blockDim.x) As[q] = AT[T0 * nA2 + q];
+      for (int q = tid; q < cnt; q += blockDim.x) sk[q] = AT[T0 * nA2 + q];
     }
   }
   __syncthreads();
@@ -424,18 +432,19 @@ __global__ void k_zero_facet(const Layout L, double* y, const int* stop) {
 }
 
 static int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   return n;
 }
 
 cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
                            KOp K, const double* x, double* y, const int* stop, cudaStream_t st) {
   k_zero_facet<<<sm_count() * 4, 256, 0, st>>>(L, y, stop);
+  note_launch();
   const int per = s.n_A + s.n_p;
   // algorithmic: packed symmetric A_T, x read once, y written once; flops: full row products
   const double alg_bytes = (double)m.ne * s.n_A * (s.n_A + 1) / 2 * 8.0 + 16.0 * L.ndof;
@@ -449,36 +458,190 @@ cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh
     const size_t sm = (size_t)EB * per_bytes + 64;
     const int64_t blocks = (m.ne + EB - 1) / EB;
     dispatch_sizes(s, [&](auto sz) {
-      static bool set = false;
-      if (!set) {
+      static std::atomic<bool> set{false};
+      if (!set.load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(k_apply_K_df<decltype(sz)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        set = true;
+        set.store(true, std::memory_order_release);
       }
       prof_begin(PROF_APPLY, st);
       k_apply_K_df<decltype(sz)><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.Ahi, K.Alo, x, y, EB, stop);
+      note_launch();
       prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
     });
     return cudaGetLastError();
   }
-  const size_t per_bytes = ((size_t)s.n_A * s.n_A + per) * sizeof(double) + 4 * (sizeof(int) + sizeof(float));
-  int EB = (int)((40 * 1024) / per_bytes);
+  const size_t small_bytes = (size_t)per * sizeof(double) + 4 * (sizeof(int) + sizeof(float));
+  const size_t per_bytes = (size_t)s.n_A * s.n_A * sizeof(double) + small_bytes;
+  const bool staged = per_bytes + 64 <= 200 * 1024;
+  int EB = staged ? (int)((40 * 1024) / per_bytes) : 1;
   if (EB < 1) EB = 1;
   if (EB > 16) EB = 16;
   const int threads = EB * per <= 128 ? 128 : 256;
-  size_t sm = (size_t)EB * per_bytes + 64;
+  size_t sm = (size_t)EB * (staged ? per_bytes : small_bytes) + 64;
   int64_t blocks = (m.ne + EB - 1) / EB;
   dispatch_sizes(s, [&](auto sz) {
-    static bool set = false;
-    if (!set) {
-      cudaFuncSetAttribute(k_apply_K<decltype(sz)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      set = true;
+    static std::atomic<bool> set{false};
+    if (!set.load(std::memory_order_acquire)) {
+      cudaFuncSetAttribute(k_apply_K<decltype(sz), true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set.store(true, std::memory_order_release);
     }
     prof_begin(PROF_APPLY, st);
-    k_apply_K<decltype(sz)><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.AT, x, y, EB, stop);
+    if (staged)
+      k_apply_K<decltype(sz), true><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.AT, x, y, EB, stop);
+    else
+      k_apply_K<decltype(sz), false><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.AT, x, y, EB, stop);
+    note_launch();
     prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
   });
   return cudaGetLastError();
 }
+
+// ============================================================================ refinement residual
+// Double-double arithmetic (error-free transformations: TwoProd with one fma, Knuth's TwoSum).
+// Every operation is an explicitly rounded intrinsic so the compiler cannot contract or reorder.
+struct DDv {
+  double hi, lo;
+};
+__device__ __forceinline__ void dd_mac(DDv& a, double u, double v) {
+  const double p = __dmul_rn(u, v);
+  const double e = __fma_rn(u, v, -p);
+  const double sum = __dadd_rn(a.hi, p);
+  const double bb = __dsub_rn(sum, a.hi);
+  const double err = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(sum, bb)), __dsub_rn(p, bb));
+  a.hi = sum;
+  a.lo = __dadd_rn(a.lo, __dadd_rn(err, e));
+}
+__device__ __forceinline__ DDv dd_add(DDv a, DDv b) {
+  const double sum = __dadd_rn(a.hi, b.hi);
+  const double bb = __dsub_rn(sum, a.hi);
+  const double err = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(sum, bb)), __dsub_rn(b.hi, bb));
+  return DDv{sum, __dadd_rn(err, __dadd_rn(a.lo, b.lo))};
+}
+
+// The rows of K_T x_T in double-double.  A block takes EB elements: their A_T (lower triangle,
+// as doubles: FP64 storage, or the exact sums hi + lo of the float pairs of the mixed form) and
+// their x_T are staged in shared memory, then one thread per (element, local row) accumulates
+// with one TwoProd and one TwoSum per entry.  Contributions to a facet dof go to the slot of
+// the element's side (s_{T,f} = +1: slot 0, -1: slot 1), so no sum is rounded before
+// k_residual_combine.
+template <class S, bool PACKED>
+__global__ void __launch_bounds__(256) k_residual_rows(S s, DevTables t, DevMesh m, Layout L,
+                                                       const double* __restrict__ AT, const float* __restrict__ Ahi,
+                                                       const float* __restrict__ Alo, const double* __restrict__ x,
+                                                       double* __restrict__ Y, int EB) {
+  extern __shared__ double srd[];
+  const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d, nfd = (s.d + 1) * s.nF;
+  const int per = nA + np_, pl = nA * (nA + 1) / 2, pp = packed_pad(s);
+  double* Ap = srd;               // [EB][pl] lower triangle, row-major
+  double* xs = Ap + EB * pl;      // [EB][per]
+  const int64_t nd = L.ndof;
+  const int tid = threadIdx.x;
+  for (int64_t T0 = (int64_t)blockIdx.x * EB; T0 < m.ne; T0 += (int64_t)gridDim.x * EB) {
+    const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
+    for (int q = tid; q < nvalid * pl; q += blockDim.x) {
+      const int e = q / pl, l = q - e * pl;
+      const int64_t T = T0 + e;
+      if (PACKED) {
+        Ap[q] = (double)Ahi[T * pp + l] + (double)Alo[T * pp + l];
+      } else {
+        const int r = (int)((sqrtf(8.f * l + 1.f) - 1.f) * 0.5f);
+        int rr = r;
+        if (rr * (rr + 1) / 2 > l) --rr;
+        else if ((rr + 1) * (rr + 2) / 2 <= l) ++rr;
+        Ap[q] = AT[T * (int64_t)nA * nA + (int64_t)rr * nA + (l - rr * (rr + 1) / 2)];
+      }
+    }
+    for (int q = tid; q < nvalid * per; q += blockDim.x) {
+      const int e = q / per, j = q - e * per;
+      const int64_t T = T0 + e;
+      double v;
+      if (j < nA) {
+        const int64_t g = local_to_global(s, L, m.elem_rank + T * (d + 1), T, j);
+        v = g < 0 ? 0.0 : x[g];
+      } else {
+        v = x[L.off_p + T * np_ + (j - nA)];
+      }
+      xs[q] = v;
+    }
+    __syncthreads();
+    for (int q = tid; q < nvalid * per; q += blockDim.x) {
+      const int e = q / per, i = q - e * per;
+      const int64_t T = T0 + e;
+      const int8_t* sg = m.signs + T * (d + 1);
+      const double* xe = xs + e * per;
+      const double* A = Ap + e * pl;
+      DDv acc{0.0, 0.0};
+      int64_t g;
+      int slot = 0;
+      if (i < nA) {
+        const int row = i * (i + 1) / 2;
+        for (int j = 0; j <= i; ++j) dd_mac(acc, A[row + j], xe[j]);
+        for (int j = i + 1; j < nA; ++j) dd_mac(acc, A[j * (j + 1) / 2 + i], xe[j]);
+        if (i < nu_) {  // (B^T x_p)_i = -s_i sum_p Bhat[p][i] x_p[p]
+          const double sgn = i < nfd ? (double)sg[i / s.nF] : 1.0;
+          for (int p = 0; p < np_; ++p) dd_mac(acc, -sgn * t.Bp[p * nu_ + i], xe[nA + p]);
+        }
+        g = local_to_global(s, L, m.elem_rank + T * (d + 1), T, i);
+        if (g < 0) continue;
+        if (i < nfd) slot = sg[i / s.nF] > 0 ? 0 : 1;
+        else if (i >= nu_) slot = sg[(i - nu_) / s.nhF] > 0 ? 0 : 1;
+      } else {
+        const int jp = i - nA;
+        for (int c = 0; c < nu_; ++c) {
+          const double sgn = c < nfd ? (double)sg[c / s.nF] : 1.0;
+          dd_mac(acc, -sgn * t.Bp[jp * nu_ + c], xe[c]);
+        }
+        g = L.off_p + T * np_ + jp;
+      }
+      Y[(2 * slot) * nd + g] = acc.hi;
+      Y[(2 * slot + 1) * nd + g] = acc.lo;
+    }
+    __syncthreads();
+  }
+}
+
+// r_g = F_g - (slot 0 + slot 1 for facet dofs, slot 0 otherwise), in double-double, rounded once.
+__global__ void k_residual_combine(Layout L, const double* F, const double* __restrict__ Y, double* r) {
+  const int64_t nd = L.ndof;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nd; g += (int64_t)gridDim.x * blockDim.x) {
+    DDv y{Y[g], Y[nd + g]};
+    const bool facet = g < L.off_o || (g >= L.off_h && g < L.off_p);
+    if (facet) y = dd_add(y, DDv{Y[2 * nd + g], Y[3 * nd + g]});
+    const DDv v = dd_add(DDv{F[g], 0.0}, DDv{-y.hi, -y.lo});
+    r[g] = __dadd_rn(v.hi, v.lo);
+  }
+}
+
+cudaError_t launch_residual_dd(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, KOp K,
+                               const double* F, const double* x, double* Y, double* r, cudaStream_t st) {
+  const int bs = 256;
+  const int per = s.n_A + s.n_p;
+  const size_t per_bytes = ((size_t)s.n_A * (s.n_A + 1) / 2 + per) * sizeof(double);
+  int EB = bs / per;
+  while (EB > 1 && (size_t)EB * per_bytes > 48 * 1024) --EB;
+  if (EB < 1) EB = 1;
+  const size_t sm = (size_t)EB * per_bytes;
+  int64_t g = (m.ne + EB - 1) / EB;
+  if (g > (int64_t)sm_count() * 32) g = (int64_t)sm_count() * 32;
+  dispatch_sizes(s, [&](auto sz) {
+    using SZ = decltype(sz);
+    static std::atomic<bool> set{false};
+    if (!set.load(std::memory_order_acquire)) {
+      cudaFuncSetAttribute(k_residual_rows<SZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(k_residual_rows<SZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set.store(true, std::memory_order_release);
+    }
+    if (K.Ahi)
+      k_residual_rows<SZ, true><<<(unsigned)g, bs, sm, st>>>(sz, t, m, L, nullptr, K.Ahi, K.Alo, x, Y, EB);
+    else
+      k_residual_rows<SZ, false><<<(unsigned)g, bs, sm, st>>>(sz, t, m, L, K.AT, nullptr, nullptr, x, Y, EB);
+    note_launch();
+  });
+  k_residual_combine<<<sm_count() * 8, bs, 0, st>>>(L, F, Y, r);
+  note_launch();
+  return cudaGetLastError();
+}
+
 
 // ---------------------------------------------------------------- mass and load
 __global__ void k_mass_u(ElemSizes s, DevTables t, DevMesh m, Layout L, const double* c, double* F) {
@@ -522,6 +685,7 @@ cudaError_t launch_mass_u(const ElemSizes& s, const DevTables& t, const DevMesh&
                           const double* c, double* F, cudaStream_t st) {
   cudaMemsetAsync(F, 0, sizeof(double) * L.ndof, st);
   k_mass_u<<<sm_count() * 8, 128, 0, st>>>(s, t, m, L, c, F);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -544,6 +708,7 @@ __global__ void k_load_points(ElemSizes s, DevTables t, DevMesh m, double* xq) {
 cudaError_t launch_load_points(const ElemSizes& s, const DevTables& t, const DevMesh& m, double* xq,
                                cudaStream_t st) {
   k_load_points<<<sm_count() * 8, 256, 0, st>>>(s, t, m, xq);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -581,6 +746,7 @@ cudaError_t launch_load(const ElemSizes& s, const DevTables& t, const DevMesh& m
                         const double* fq, double* F, cudaStream_t st) {
   cudaMemsetAsync(F, 0, sizeof(double) * L.ndof, st);
   k_load<<<sm_count() * 8, 128, 0, st>>>(s, t, m, L, fq, F);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -996,6 +1162,7 @@ static void vcycle(PrecData<R>& P, int l, const int* stop, cudaStream_t st) {
     unsigned g = (unsigned)((G.n * 32 + bs - 1) / bs);
     if (g > 4096) g = 4096;
     k_coarse<R><<<g, bs, 0, st>>>(G.n, P.coarse_inv, P.pb[0], P.px[0], stop);
+    note_launch();
     return;
   }
 
@@ -1005,15 +1172,20 @@ static void vcycle(PrecData<R>& P, int l, const int* stop, cudaStream_t st) {
   R* xt = P.ptmp[l];
   for (int sw = 0; sw < P.gmg_smooth; ++sw) {
     k_jacobi<R><<<grid(G.n), bs, 0, st>>>(G.n, G.rowptr, G.col, va, di, P.pb[l], x, xt, sw == 0, stop);
+    note_launch();
     R* tmp = x; x = xt; xt = tmp;
   }
   k_residual_csr<R><<<grid(G.n), bs, 0, st>>>(G.n, G.rowptr, G.col, va, P.pb[l], x, P.pr[l], stop);
+  note_launch();
   const GmgLevel& Gc = P.lev[l - 1];
   k_spmv_csr<R><<<grid(Gc.n), bs, 0, st>>>(Gc.n, G.rrow, G.rcol, (const R*)G.rval, P.pr[l], P.pb[l - 1], 0, stop);
+  note_launch();
   vcycle(P, l - 1, stop, st);
   k_spmv_csr<R><<<grid(G.n), bs, 0, st>>>(G.n, G.prow, G.pcol, (const R*)G.pval, P.px[l - 1], x, 1, stop);
+  note_launch();
   for (int sw = 0; sw < P.gmg_smooth; ++sw) {
     k_jacobi<R><<<grid(G.n), bs, 0, st>>>(G.n, G.rowptr, G.col, va, di, P.pb[l], x, xt, 0, stop);
+    note_launch();
     R* tmp = x; x = xt; xt = tmp;
   }
   if (x != P.px[l]) cudaMemcpyAsync(P.px[l], x, sizeof(R) * G.n, cudaMemcpyDeviceToDevice, st);
@@ -1043,20 +1215,21 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
   const int4* rec = m.frec + first * 4;
   dispatch_sizes(s, [&](auto sz) {
     using SZ = decltype(sz);
-    static int per_sm[2] = {0, 0};
+    static std::atomic<int> per_sm[2];
     const int ui = update ? 1 : 0;
-    if (!per_sm[ui]) {
+    if (!per_sm[ui].load(std::memory_order_acquire)) {
       cudaFuncSetAttribute(k_facet_step<R, SZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(k_facet_step<R, SZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       int occ = 0;
       if (update) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step<R, SZ, true>, threads, sm);
       else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step<R, SZ, false>, threads, sm);
-      per_sm[ui] = occ > 0 ? occ : 1;
+      per_sm[ui].store(occ > 0 ? occ : 1, std::memory_order_release);
     }
-    int64_t blocks = (int64_t)sm_count() * per_sm[ui];
+    int64_t blocks = (int64_t)sm_count() * per_sm[ui].load(std::memory_order_acquire);
     if (blocks > nb) blocks = nb;
     const int cls = update ? PROF_FACET_GS : PROF_FACET_RES;
     prof_begin(cls, st);
+    note_launch();
     if (update)
       k_facet_step<R, SZ, true><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, rec, n, FB,
                                                                         stop);
@@ -1088,13 +1261,14 @@ static void elem_prologue(const ElemSizes& s, const DevTables& t, const DevMesh&
   const int64_t blocks = (m.ne + EB - 1) / EB;
   dispatch_sizes(s, [&](auto sz) {
     using SZ = decltype(sz);
-    static bool set = false;
-    if (!set) {
+    static std::atomic<bool> set{false};
+    if (!set.load(std::memory_order_acquire)) {
       cudaFuncSetAttribute(k_elem_prologue<R, SZ, WITH_BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      set = true;
+      set.store(true, std::memory_order_release);
     }
     prof_begin(PROF_PROLOGUE, st);
     k_elem_prologue<R, SZ, WITH_BT><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, P.G, r, zp, rin, tb, EB, stop);
+    note_launch();
     prof_end(PROF_PROLOGUE, (double)m.ne * (s.n_bub * s.n_c + 2 * s.n_bub + s.n_c + (WITH_BT ? s.n_p : 0)) * sizeof(R),
              2.0 * (double)m.ne * s.n_bub * s.n_c, st);
   });
@@ -1109,14 +1283,15 @@ static void elem_epilogue(const ElemSizes& s, const DevTables& t, const DevMesh&
   const int64_t blocks = (m.ne + EB - 1) / EB;
   dispatch_sizes(s, [&](auto sz) {
     using SZ = decltype(sz);
-    static bool set = false;
-    if (!set) {
+    static std::atomic<bool> set{false};
+    if (!set.load(std::memory_order_acquire)) {
       cudaFuncSetAttribute(k_elem_epilogue<R, SZ, WITH_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      set = true;
+      set.store(true, std::memory_order_release);
     }
     prof_begin(PROF_EPILOGUE, st);
     k_elem_epilogue<R, SZ, WITH_P><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, nu, P.G, P.Aoi, rin, r, x, zp, EB,
                                                                        stop);
+    note_launch();
     prof_end(PROF_EPILOGUE, (double)m.ne * (s.n_bub * s.n_c + s.n_bub * s.n_bub + 2 * s.n_bub + s.n_c +
                                              (WITH_P ? 2 * s.n_p : 0)) * sizeof(R),
              2.0 * (double)m.ne * (s.n_bub * s.n_c + s.n_bub * s.n_bub), st);
@@ -1139,8 +1314,10 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   const int top = P.nlev - 1;
   prof_begin(PROF_GMG, st);
   k_embed_T<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.vf_ptr, P.vf_idx, P.nP1, P.rr, P.pb[top], stop);
+  note_launch();
   vcycle<R>(P, top, stop, st);
   k_embed<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.fvr, L.nint, P.px[top], x, stop);
+  note_launch();
   prof_end(PROF_GMG, 0.0, 0.0, st);
   for (int sw = 0; sw < P.smooth; ++sw)
     for (int c = P.ncol - 1; c >= 0; --c)
@@ -1154,6 +1331,7 @@ cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh
   const int bs = 256;
   const unsigned g = (unsigned)(sm_count() * 8);
   // b = r in precision R
+  note_launch();
   if (sizeof(R) == 4) k_to_R_f<<<g, bs, 0, st>>>(L.ndof, r, (float*)P.b);
   else k_to_R_d<<<g, bs, 0, st>>>(L.ndof, r, (double*)P.b);
   // first Ahat^{-1}: a = Ahat^{-1} r_u  (a in P.zz), then z_p = Shat_p^{-1}(r_p - B a) (P.x, p part)
@@ -1169,6 +1347,7 @@ cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh
   asp_core<R>(s, m, L, P, P.b, P.t, P.x, stop, st);
   elem_epilogue<R, false>(s, t, m, L, nu, P, P.x, P.b, P.x, nullptr, stop, st);
   k_from_R<R><<<g, bs, 0, st>>>(L.ndof, P.x, z, stop);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -1219,6 +1398,7 @@ cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* scra
   int blocks = sm_count() * 4;
   if (blocks > 1024) blocks = 1024;
   k_dot<<<blocks, 256, 0, st>>>(a, b, n, scratch, out, stop, (unsigned int*)(scratch + 1024));
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -1265,7 +1445,9 @@ cudaError_t launch_mean_zero(const DevMesh& m, const Layout& L, int n_p, double*
   int blocks = sm_count() * 2;
   k_mean_sum<<<blocks, 256, 0, st>>>(m, L, n_p, x, scratch + 1040, scratch + 2070, total_adet, stop,
                                      (unsigned int*)(scratch + 2080));
+  note_launch();
   k_mean_sub<<<blocks, 256, 0, st>>>(m, L, n_p, x, scratch + 2070, stop);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -1291,6 +1473,7 @@ __global__ void k_minres_init(MinresScalars* S) {
 }
 cudaError_t launch_minres_init(MinresScalars* S, cudaStream_t st) {
   k_minres_init<<<1, 1, 0, st>>>(S);
+  note_launch();
   return cudaGetLastError();
 }
 __global__ void k_minres_scalars(MinresScalars* S) {
@@ -1329,6 +1512,7 @@ __global__ void k_minres_scalars(MinresScalars* S) {
 }
 cudaError_t launch_minres_scalars(MinresScalars* S, cudaStream_t st) {
   k_minres_scalars<<<1, 1, 0, st>>>(S);
+  note_launch();
   return cudaGetLastError();
 }
 __global__ void k_minres_commit(MinresScalars* S) {
@@ -1360,16 +1544,20 @@ cudaError_t launch_minres_lanczos(MinresScalars* S, int64_t n, double* z, const 
                                   double* v_old, cudaStream_t st) {
   (void)z;
   k_lanczos<<<sm_count() * 8, 256, 0, st>>>(n, Kz, v, v_old, S);
+  note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_minres_update(MinresScalars* S, int64_t n, const double* z, double* w, double* w_old,
                                  double* x, cudaStream_t st) {
   k_update<<<sm_count() * 8, 256, 0, st>>>(n, z, w, w_old, x, S);
+  note_launch();
   k_minres_commit<<<1, 1, 0, st>>>(S);
+  note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_minres_scale(MinresScalars* S, int64_t n, const double* zin, double* z, cudaStream_t st) {
   k_scale<<<sm_count() * 8, 256, 0, st>>>(n, zin, z, S);
+  note_launch();
   return cudaGetLastError();
 }
 __global__ void k_axpby(int64_t n, double a, const double* x, double b, double* y) {
@@ -1378,6 +1566,7 @@ __global__ void k_axpby(int64_t n, double a, const double* x, double b, double* 
 }
 cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st) {
   k_axpby<<<sm_count() * 8, 256, 0, st>>>(n, a, x, b, y);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -1393,6 +1582,16 @@ template cudaError_t launch_precond<float>(const ElemSizes&, const DevTables&, c
                                            PrecData<float>&, const double*, double*, const int*, cudaStream_t);
 template cudaError_t launch_precond<double>(const ElemSizes&, const DevTables&, const DevMesh&, const Layout&, double,
                                             PrecData<double>&, const double*, double*, const int*, cudaStream_t);
+
+// ---------------------------------------------------------------- launch accounting
+static std::atomic<uint64_t> g_launches{0};
+thread_local bool g_capturing = false;
+
+void note_launch() {
+  if (!g_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- profiler
 thread_local Profiler* g_prof = nullptr;

@@ -18,6 +18,14 @@ extern thread_local Profiler* g_prof;
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, double bytes, double flops, cudaStream_t st);
 
+// Launch accounting.  Every kernel launch of the library adds one to a process-wide counter;
+// while a thread captures a CUDA graph its launches only record nodes and add nothing, and each
+// launch of a captured graph adds the number of kernel nodes it runs.
+extern thread_local bool g_capturing;
+void note_launch();
+void note_launches(uint64_t n);
+uint64_t launch_count();
+
 // Dof layout of the condensed system [u_d | u_o | uhat | p] (dof contract).
 struct Layout {
   int64_t ne, nint;
@@ -122,6 +130,10 @@ cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, const R* A
 // y = K x
 cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
                            KOp K, const double* x, double* y, const int* stop, cudaStream_t st);
+// r = F - K x with the element products and the sum of a facet dof's two contributions carried in
+// double-double and rounded once (the residual of a refinement cycle).  Y: workspace of 4 ndof doubles.
+cudaError_t launch_residual_dd(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, KOp K,
+                               const double* F, const double* x, double* Y, double* r, cudaStream_t st);
 // F = M_u c (velocity mass) on the u part; zero elsewhere
 cudaError_t launch_mass_u(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
                           const double* c, double* F, cudaStream_t st);

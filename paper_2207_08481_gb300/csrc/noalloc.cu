@@ -92,6 +92,7 @@ extern "C" int mcs_condense_noalloc(mcs_handle* h, int64_t T0, int64_t count, do
     const int threads = h->d == 2 ? 128 : 256;
     k_condense_noalloc<<<(unsigned)blocks, threads, 0, h->stream>>>(h->es, h->dt, h->dm, h->nu, T0, count, AT_out,
                                                                    scratch, slot);
+    note_launch();
     cuda_check(cudaGetLastError(), "k_condense_noalloc");
     return MCS_OK;
   } catch (const McsError& e) {

@@ -28,14 +28,15 @@ MCS_MIXED = 1
 EXPORTED = ["mcs_version", "mcs_last_error", "mcs_default_options", "mcs_setup_structured", "mcs_setup_mesh",
             "mcs_sizes", "mcs_export_mesh", "mcs_export_dofmap", "mcs_export_pattern", "mcs_condense",
             "mcs_copy_element_matrices", "mcs_copy_schur", "mcs_load_points", "mcs_load_vector",
-            "mcs_mass_velocity", "mcs_apply", "mcs_precond", "mcs_solve", "mcs_solve_host", "mcs_profile",
-            "mcs_profile_read", "mcs_condense_noalloc", "mcs_destroy"]
+            "mcs_mass_velocity", "mcs_apply", "mcs_residual", "mcs_precond", "mcs_solve", "mcs_solve_host", "mcs_profile",
+            "mcs_profile_read", "mcs_launch_count", "mcs_condense_noalloc", "mcs_destroy"]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("smooth_steps", ctypes.c_int), ("gmg_levels", ctypes.c_int),
                 ("gmg_smooth", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
+                ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("residual_dd", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -88,6 +89,7 @@ def lib() -> ctypes.CDLL:
         L.mcs_load_vector.argtypes = [vp, vp, vp]
         L.mcs_mass_velocity.argtypes = [vp, vp, vp]
         L.mcs_apply.argtypes = [vp, vp, vp]
+        L.mcs_residual.argtypes = [vp, vp, vp, vp]
         L.mcs_precond.argtypes = [vp, vp, vp]
         L.mcs_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveInfo)]
         L.mcs_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(SolveInfo)]
@@ -95,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.mcs_profile.argtypes = [vp, ctypes.c_int]
         L.mcs_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.c_int]
         L.mcs_condense_noalloc.argtypes = [vp, i64, i64, vp]
+        L.mcs_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         L.mcs_default_options.argtypes = [ctypes.POINTER(Options)]
         del i32p
         _lib = L
@@ -105,6 +108,13 @@ def _check(rc):
     if rc != MCS_OK:
         raise McsError(rc, lib().mcs_last_error().decode())
     return rc
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process (graph nodes counted per graph launch)."""
+    n = ctypes.c_uint64(0)
+    _check(lib().mcs_launch_count(ctypes.byref(n)))
+    return int(n.value)
 
 
 def default_options(**kw) -> Options:
@@ -221,6 +231,9 @@ class Handle:
 
     def apply(self, x, y):
         _check(lib().mcs_apply(self._h, _dptr(x), _dptr(y)))
+
+    def residual(self, F, x, r):
+        _check(lib().mcs_residual(self._h, _dptr(F), _dptr(x), _dptr(r)))
 
     def precond(self, r, z):
         _check(lib().mcs_precond(self._h, _dptr(r), _dptr(z)))

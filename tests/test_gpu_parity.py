@@ -31,7 +31,7 @@ def _oracle(d, N, k, nu):
     return D, system.condense(D)
 
 
-CASES = [(2, 4, 2, 0.7), (2, 3, 3, 1.3), (3, 2, 2, 0.7), (3, 1, 3, 1.0)]
+CASES = [(2, 4, 2, 0.7), (2, 3, 3, 1.3), (2, 2, 4, 0.3), (3, 2, 2, 0.7), (3, 1, 3, 1.0), (3, 1, 4, 0.5)]
 
 
 @pytest.mark.parametrize("d,N,k,nu", CASES)
@@ -98,7 +98,8 @@ def test_apply_matches_oracle(mcs, d, N, k, nu):
     h.close()
 
 
-@pytest.mark.parametrize("d,N,k,nu", [(2, 4, 2, 0.7), (2, 3, 3, 1.3), (3, 2, 2, 0.7)])
+@pytest.mark.parametrize("d,N,k,nu", [(2, 4, 2, 0.7), (2, 3, 3, 1.3), (2, 2, 4, 0.3), (3, 2, 2, 0.7), (3, 1, 3, 1.0),
+                                     (3, 1, 4, 0.5)])
 def test_apply_mixed_double_float(mcs, d, N, k, nu):
     """Mixed form: A_T as float pairs with double-float arithmetic, within 1e-12 of the FP64 K x."""
     h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_MIXED, gmg_levels=1)
@@ -116,8 +117,9 @@ def test_apply_mixed_double_float(mcs, d, N, k, nu):
     h.close()
 
 
-@pytest.mark.parametrize("d,N,k,nu,lev", [(2, 8, 2, 0.7, 2), (2, 4, 3, 1.0, 1), (2, 8, 2, 1.0, 3), (3, 2, 2, 1.0, 1),
-                                          (3, 4, 2, 0.5, 2)])
+@pytest.mark.parametrize("d,N,k,nu,lev", [(2, 8, 2, 0.7, 2), (2, 4, 3, 1.0, 1), (2, 8, 2, 1.0, 3), (2, 2, 4, 0.3, 1),
+                                          (2, 4, 4, 1.0, 2), (3, 2, 2, 1.0, 1), (3, 4, 2, 0.5, 2), (3, 1, 3, 1.0, 1),
+                                          (3, 2, 3, 1.0, 1), (3, 1, 4, 0.5, 1)])
 def test_precond_fp64_matches_oracle(mcs, d, N, k, nu, lev):
     """Khat^{-1} (eq. mhatinvfactor with the multiplicative ASP of Sec. 6.1) step for step."""
     h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=lev)
@@ -196,4 +198,79 @@ def test_solve_c1_matches_oracle(mcs, prec, tol):
     ep = np.linalg.norm(xg[n:] - xo[n:]) / np.linalg.norm(xo[n:])
     assert eu < tol and ep < tol, (eu, ep, info.iterations)
     assert info.status == 0 and info.iterations < 300
+    h.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+@pytest.mark.parametrize("d,N,k,nu", [(2, 2, 4, 0.3), (2, 4, 4, 1.0), (3, 1, 4, 0.5), (3, 2, 3, 1.0), (3, 1, 2, 1.0)])
+def test_solve_small_meshes_all_degrees(mcs, d, N, k, nu, prec, tol):
+    """Solve against the oracle's direct solve for k = 3, 4 and the smallest meshes (one cube;
+    2x2 squares), with the default multigrid hierarchy.  Both sides take the same right-hand side
+    (the library's load vector, whose own parity is tested above): on a mesh of one cube the load
+    quadratures of the two sides (degree k+7 and k+8) differ by about 1e-8 relative.  For k = 4 the
+    error is about 100 times the preconditioned residual, so the tolerances of the solves are set
+    below the plain-FP64 residual floor; the double-double refinement residual reaches them."""
+    p = mcs.MCS_FP64 if prec == "fp64" else mcs.MCS_MIXED
+    h = _handle(mcs, d, N, k, nu, precision=p, rtol=1e-13 if prec == "fp64" else 1e-12)
+    F = _manufactured_rhs(h, d, nu)
+    x = torch.zeros_like(F)
+    info = h.solve(F, x, check=False)
+    D = system.discretize(mesh.structured(d, N), k, nu)
+    xo, _, _ = system.solve_full(D, F.cpu().numpy())
+    xo = system.mean_zero_pressure(D, xo)
+    xg = x.cpu().numpy()
+    n = D.off_p
+    eu = np.linalg.norm(xg[:n] - xo[:n]) / np.linalg.norm(xo[:n])
+    ep = np.linalg.norm(xg[n:] - xo[n:]) / np.linalg.norm(xo[n:])
+    assert info.status == 0, (info.status, info.iterations, info.refinements, info.rel_res_precond, eu, ep)
+    assert eu < tol and ep < tol, (eu, ep, info.iterations)
+    h.close()
+
+
+def test_residual_double_double_is_exact_to_rounding(mcs):
+    """mcs_residual: F - K x to within a few ulp of the exact value even where F and K x cancel.
+    F is K x itself rounded to double, so the exact residual is only the rounding error of F; a
+    residual formed in FP64 would be wrong in every digit.  The velocity rows are checked in
+    exact rational arithmetic against the library's own stored A_T (x_p = 0)."""
+    from fractions import Fraction
+    d, N, k = 2, 2, 3
+    h = _handle(mcs, d, N, k, 1.0, precision=mcs.MCS_FP64, gmg_levels=1)
+    D = system.discretize(mesh.structured(d, N), k, 1.0)
+    ne, nA = D.mesh.elems.shape[0], D.sz["n_A"]
+    P = h.element_matrices(0, ne)
+    AT = np.zeros((ne, nA, nA))
+    il = np.tril_indices(nA)
+    AT[:, il[0], il[1]] = P
+    AT[:, il[1], il[0]] = P
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(D.ndof)
+    x[D.off_p:] = 0.0
+    xf = [Fraction(v) for v in x]
+    Kx = [Fraction(0)] * D.ndof
+    scale = [Fraction(0)] * D.ndof
+    for T in range(ne):
+        g = D.a_map[T]
+        for i in range(nA):
+            if g[i] < 0:
+                continue
+            acc, sc = Fraction(0), Fraction(0)
+            for j in range(nA):
+                if g[j] >= 0:
+                    acc += Fraction(AT[T, i, j]) * xf[g[j]]
+                    sc += abs(Fraction(AT[T, i, j]) * xf[g[j]])
+            Kx[g[i]] += acc
+            scale[g[i]] += sc
+    F = np.array([float(v) for v in Kx])
+    r = torch.zeros(D.ndof, dtype=torch.float64, device="cuda")
+    h.residual(torch.tensor(F, device="cuda"), torch.tensor(x, device="cuda"), r)
+    rg = r.cpu().numpy()
+    nu_ = D.off_p
+    for g in range(nu_):
+        exact = Fraction(F[g]) - Kx[g]
+        err = abs(Fraction(rg[g]) - exact)
+        assert err <= 2 * abs(exact) * Fraction(2) ** -52 + Fraction(2) ** -100 * scale[g], (g, float(exact), rg[g])
+    # pressure rows against the oracle's B (FP64 tables on both sides: rounding-level agreement)
+    K = system.condensed_system(D)
+    rp = (F - K @ x)[nu_:]
+    assert np.abs(rg[nu_:] - rp).max() <= 1e-14 * np.abs(x).max() * np.abs(K[nu_:]).max() * 50
     h.close()

@@ -41,6 +41,8 @@ def test_host_entry_points(lib):
     assert o.precision == lib.MCS_MIXED and o.smooth_steps == 2 and o.rtol == 1e-8
     assert L.mcs_default_options(None) == lib.MCS_ERR_INVALID_ARG
     assert isinstance(L.mcs_last_error(), bytes)
+    assert lib.launch_count() >= 0
+    assert L.mcs_launch_count(None) == lib.MCS_ERR_INVALID_ARG
 
 
 def test_invalid_arguments_are_reported_not_raised(lib):
@@ -53,5 +55,10 @@ def test_invalid_arguments_are_reported_not_raised(lib):
     assert L.mcs_setup_structured(2, 8, 2, -1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(o), None, None) == lib.MCS_ERR_INVALID_ARG
     assert b"NULL" in L.mcs_last_error()
+    assert L.mcs_setup_structured(3, 4, 5, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
+    assert L.mcs_setup_structured(2, 4, 6, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
+    bad = lib.default_options(residual_dd=3)
+    assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
+    assert b"residual_dd" in L.mcs_last_error()
     assert L.mcs_apply(None, None, None) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_destroy(None) == lib.MCS_OK
