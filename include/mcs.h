@@ -31,10 +31,23 @@
  *     u_o: BDM bubbles (element T, m) at off_o + T*n_bub + m;
  *     uhat: tangential facet dofs (r, tangent m, mode j) at off_h + r*nhF + m*dimP^{k-1}(F) + j;
  *     p: pressure (T, mode j) at off_p + T*n_p + j.
- *     Basis functions, facet orientation and numbering follow the dof contract
- *     documented in the design doc (Dubiner bases, Kuhn meshes, lexicographic
- *     facets).  All boundary facets are Dirichlet (u = 0) and carry no dofs;
- *     the pressure is fixed by a zero mean.
+ *   - Dof contract (the paper leaves bases and orientations open):
+ *     * facets are the distinct sorted vertex tuples in lexicographic order; interior
+ *       facets keep that order (rank r); local facet f of an element is opposite its
+ *       local vertex f; the unit normal n_F satisfies det[e_1..e_{d-1}, n_F] > 0 for
+ *       the edge vectors e_m = x_{w_m} - x_{w_0} of the sorted facet vertices w, and
+ *       s_{T,f} = +1 where n_F points out of T;
+ *     * orthonormal Dubiner polynomials (homogeneous Jacobi products, total degree
+ *       ascending) on the reference simplex and on the facet parameter simplex;
+ *     * V_h = BDM^k as the dual basis of the facet moments int_F u.n_F q_j and of
+ *       interior moments of the Piola pull-back against psi_a e_c (deg <= k-2) and
+ *       the Nedelec-type functions (-y, x) x^a y^b (2D) or x cross (x^alpha e_c) (3D),
+ *       |alpha| = k-2;
+ *     * uhat: q_j(s) e_m on each interior facet, deg q_j <= k-1; p: Dubiner, deg <= k-1;
+ *     * structured meshes: the Kuhn split of N^dim cells, vertex (i,j[,l]) has id
+ *       i + (N+1)(j + (N+1) l); element cell*dim! + (permutation index).
+ *     All boundary facets are Dirichlet (u = 0) and carry no dofs; the pressure is
+ *     fixed by a zero mean.
  */
 #ifndef MCS_H
 #define MCS_H
