@@ -166,7 +166,7 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
     P.ptmp[l] = h->dalloc<R>(G.n);
   }
   P.coarse_inv = h->upload(coarse_inv);
-  const int64_t n = h->L.ndof;
+  const int64_t n = precond_layout(h->L, h->es, (int)sizeof(R)).ndof;  // facet-interleaved layout
   P.b = h->dalloc<R>(n);
   P.x = h->dalloc<R>(n);
   P.t = h->dalloc<R>(n);

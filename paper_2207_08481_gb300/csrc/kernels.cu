@@ -26,6 +26,18 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
 }
+// L2 policy for data read once per pass (element slabs, facet blocks): evict first, so the
+// vectors the pass gathers stay resident in L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async16_hint(void* smem_dst, const void* gmem_src, uint64_t pol) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem_src), "l"(pol)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 template <int BYTES>
 __device__ __forceinline__ void cp_async_small(void* smem_dst, const void* gmem_src) {
@@ -752,29 +764,57 @@ cudaError_t launch_load(const ElemSizes& s, const DevTables& t, const DevMesh& m
 
 // ============================================================================ preconditioner (precision R)
 // gather the coupling vector x_T (facet-major) of element T from an external-layout vector
+// index of coupling dof t (facet-major: u_d modes, then uhat modes) of interior facet rk
+template <class R, class S>
+__device__ __forceinline__ int64_t coup_idx(const S& s, const Layout& L, int32_t rk, int t) {
+  if (L.fstride) return (int64_t)rk * L.fstride + t;
+  return (t < s.nF) ? (int64_t)rk * s.nF + t : L.off_h + (int64_t)rk * s.nhF + (t - s.nF);
+}
 template <class R, class S>
 __device__ __forceinline__ R coup_get(const S& s, const Layout& L, const R* x, int32_t rk, int t) {
   if (rk < 0) return (R)0;
-  return (t < s.nF) ? x[(int64_t)rk * s.nF + t] : x[L.off_h + (int64_t)rk * s.nhF + (t - s.nF)];
-}
-template <class R, class S>
-__device__ __forceinline__ int64_t coup_idx(const S& s, const Layout& L, int32_t rk, int t) {
-  return (t < s.nF) ? (int64_t)rk * s.nF + t : L.off_h + (int64_t)rk * s.nhF + (t - s.nF);
+  return x[coup_idx<R>(s, L, rk, t)];
 }
 
-__global__ void k_to_R_f(int64_t n, const double* a, float* b) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
-}
-__global__ void k_to_R_d(int64_t n, const double* a, double* b) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = a[i];
-}
+// b (preconditioner layout PL, precision R) = a (external layout L); padding entries are zero
 template <class R>
-__global__ void k_from_R(int64_t n, const R* a, double* b, const int* stop) {
+__global__ void k_to_prec(ElemSizes s, Layout L, Layout PL, const double* __restrict__ a, R* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < PL.ndof;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v;
+    if (i < PL.n_dd) {
+      const int64_t rk = i / PL.fstride;
+      const int t = (int)(i - rk * PL.fstride);
+      v = t < s.nF ? a[rk * s.nF + t] : (t < s.mF ? a[L.off_h + rk * s.nhF + (t - s.nF)] : 0.0);
+    } else if (i < PL.off_p) {
+      v = a[L.off_o + (i - PL.off_o)];
+    } else {
+      v = a[L.off_p + (i - PL.off_p)];
+    }
+    b[i] = (R)v;
+  }
+}
+// b (external layout L, FP64) = a (preconditioner layout PL)
+template <class R>
+__global__ void k_from_prec(ElemSizes s, Layout L, Layout PL, const R* __restrict__ a, double* __restrict__ b,
+                            const int* stop) {
   if (stop && *stop) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L.ndof;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i;
+    if (j < L.n_dd) {
+      const int64_t rk = j / s.nF;
+      i = rk * PL.fstride + (j - rk * s.nF);
+    } else if (j < L.off_h) {
+      i = PL.off_o + (j - L.off_o);
+    } else if (j < L.off_p) {
+      const int64_t q = j - L.off_h, rk = q / s.nhF;
+      i = rk * PL.fstride + s.nF + (q - rk * s.nhF);
+    } else {
+      i = PL.off_p + (j - L.off_p);
+    }
+    b[j] = (double)a[i];
+  }
 }
 
 // ---------------------------------------------------------------- element-level preconditioner kernels
@@ -906,12 +946,14 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
 // Facet-centric block step over the facet records rec[0..n) (colour order):
 //   r_F = b_F - tb_F - sum_{T in F} (A^d_T x_T)|_F,
 // UPDATE: x_F += D_F^{-1} r_F (block Gauss-Seidel within one colour); else rr_F = r_F.
-// Persistent blocks walk batches of FB facets.  (1D TMA bulk copies of the 592-byte slabs
-// measured slower than 16-byte cp.async here: the slabs are too small per request.)  Everything a batch needs (A^d slabs of both
-// elements, D_F^{-1}, x of both elements, b, tb) is fetched with asynchronous copies into one
-// of two shared-memory stages while the previous batch is computed; the 64-byte facet
-// records are read one batch ahead.  Facets of one colour share no element, so the copies
-// of batch i+1 never read values that batch i updates.
+// Vectors are in the preconditioner layout (L.fstride > 0): the m_F coupling values of a facet
+// are one 32-byte-aligned segment, fetched with 16-byte copies.  Persistent blocks walk batches
+// of FB facets.  Everything a batch needs (A^d slabs of both elements, D_F^{-1}, the segments of
+// all facets of both elements, b, tb) is fetched with asynchronous copies into one of two
+// shared-memory stages while the previous batch is computed; the 64-byte facet records are read
+// one batch ahead.  Slabs and D_F^{-1} are read once per pass and carry an L2 evict-first hint.
+// Facets of one colour share no element, so the copies of batch i+1 never read values that
+// batch i updates.
 template <class R, class S, bool UPDATE>
 __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, const R* __restrict__ Ad,
                                                     const R* __restrict__ Dinv, const R* __restrict__ b,
@@ -920,14 +962,16 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
                                                     const int* stop) {
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char sraw[];
-  const int nc = s.n_c, mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), ds = dinv_stride(s);
+  const int mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), ds = dinv_stride(s);
+  const int fs = facet_stride(s, (int)sizeof(R));   // equals L.fstride
+  const int xe = dp1 * fs;                          // gathered values per (facet, side)
   // stage layout (both stages identical, 16-byte aligned pieces)
   unsigned char* sbase = sraw;
   const int rec_b = FB * 16 * (int)sizeof(int);
   const int as_b = FB * 2 * slab * (int)sizeof(R);
   const int di_b = UPDATE ? FB * ds * (int)sizeof(R) : 0;
-  const int xt_b = ((FB * 2 * nc * (int)sizeof(R)) + 15) / 16 * 16;
-  const int bb_b = ((FB * mF * (int)sizeof(R)) + 15) / 16 * 16;
+  const int xt_b = FB * 2 * xe * (int)sizeof(R);
+  const int bb_b = FB * fs * (int)sizeof(R);
   const int stage_b = rec_b + as_b + di_b + xt_b + 2 * bb_b;
   R* yS = (R*)(sbase + 2 * stage_b);       // [FB][2][mF]
   R* rF = yS + FB * 2 * mF;                // [FB][mF]
@@ -938,9 +982,10 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
   auto BS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b + di_b + xt_b); };
   auto TS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b + di_b + xt_b + bb_b); };
   constexpr int V = 16 / (int)sizeof(R);
-  const int cs = slab / V, cd = ds / V;
+  const int cs = slab / V, cd = ds / V, cx = fs / V;
   const int tid = threadIdx.x;
   const int64_t nb = (n + FB - 1) / FB;
+  const uint64_t pol = l2_evict_first_policy();
 
   auto load_records = [&](int st, int64_t bi) {
     int* rc = RC(st);
@@ -959,37 +1004,39 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
     R* bS = BS(st);
     R* tS = TS(st);
     for (int q = tid; q < FB * 2 * cs; q += blockDim.x) {
-      const int fs = q / cs, ch = q - fs * cs, fb = fs >> 1, side = fs & 1;
+      const int fsd = q / cs, ch = q - fsd * cs, fb = fsd >> 1, side = fsd & 1;
       const int* r_ = rc + fb * 16;
       if (r_[0] >= 0)
-        cp_async16(As + fs * slab + ch * V, Ad + adw_index(dp1, slab, mF, r_[1 + side], r_[3 + side], 0, 0) + ch * V);
+        cp_async16_hint(As + fsd * slab + ch * V,
+                        Ad + adw_index(dp1, slab, mF, r_[1 + side], r_[3 + side], 0, 0) + ch * V, pol);
     }
     if (UPDATE)
       for (int q = tid; q < FB * cd; q += blockDim.x) {
         const int fb = q / cd, ch = q - fb * cd;
         const int r = rc[fb * 16];
-        if (r >= 0) cp_async16(Di + fb * ds + ch * V, Dinv + (int64_t)r * ds + ch * V);
+        if (r >= 0) cp_async16_hint(Di + fb * ds + ch * V, Dinv + (int64_t)r * ds + ch * V, pol);
       }
-    for (int q = tid; q < FB * 2 * nc; q += blockDim.x) {
-      const int fs = q / nc, c = q - fs * nc, fb = fs >> 1, side = fs & 1;
+    for (int q = tid; q < FB * 2 * dp1 * cx; q += blockDim.x) {
+      const int seg = q / cx, ch = q - seg * cx;          // seg = (fb*2 + side)*dp1 + f
+      const int fsd = seg / dp1, f = seg - fsd * dp1, fb = fsd >> 1, side = fsd & 1;
       const int* r_ = rc + fb * 16;
-      int32_t g = -1;
-      const int f = c / mF;
-      if (r_[0] >= 0) g = r_[5 + side * dp1 + f];
-      if (g >= 0) cp_async_small<sizeof(R)>(xT + q, x + coup_idx<R>(s, L, g, c - f * mF));
-      else xT[q] = (R)0;
+      const int32_t g = r_[0] >= 0 ? r_[5 + side * dp1 + f] : -1;
+      R* dst = xT + seg * fs + ch * V;
+      if (g >= 0) cp_async16(dst, x + (int64_t)g * fs + ch * V);
+      else *reinterpret_cast<int4*>(dst) = make_int4(0, 0, 0, 0);
     }
-    for (int q = tid; q < FB * mF; q += blockDim.x) {
-      const int fb = q / mF, t = q - fb * mF;
+    for (int q = tid; q < FB * cx; q += blockDim.x) {
+      const int fb = q / cx, ch = q - fb * cx;
       const int r = rc[fb * 16];
+      R* db = bS + fb * fs + ch * V;
+      R* dt = tS + fb * fs + ch * V;
       if (r >= 0) {
-        const int64_t gi = coup_idx<R>(s, L, r, t);
-        cp_async_small<sizeof(R)>(bS + q, b + gi);
-        if (tb) cp_async_small<sizeof(R)>(tS + q, tb + gi);
-        else tS[q] = (R)0;
+        cp_async16(db, b + (int64_t)r * fs + ch * V);
+        if (tb) cp_async16(dt, tb + (int64_t)r * fs + ch * V);
+        else *reinterpret_cast<int4*>(dt) = make_int4(0, 0, 0, 0);
       } else {
-        bS[q] = (R)0;
-        tS[q] = (R)0;
+        *reinterpret_cast<int4*>(db) = make_int4(0, 0, 0, 0);
+        *reinterpret_cast<int4*>(dt) = make_int4(0, 0, 0, 0);
       }
     }
   };
@@ -1019,26 +1066,31 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
     const R* bS = BS(st);
     const R* tS = TS(st);
     for (int q = tid; q < FB * 2 * mF; q += blockDim.x) {
-      const int fs = q / mF, t = q - fs * mF;
-      const R* A = As + fs * slab + t;
-      const R* xv = xT + fs * nc;
+      const int fsd = q / mF, t = q - fsd * mF;
+      const R* A = As + fsd * slab + t;
+      const R* xv = xT + fsd * xe;
       R v0 = 0, v1 = 0;
-      int c = 0;
-#pragma unroll 4
-      for (; c + 1 < nc; c += 2) {
-        v0 += A[c * mF] * xv[c];
-        v1 += A[(c + 1) * mF] * xv[c + 1];
+#pragma unroll
+      for (int f = 0; f < dp1; ++f) {
+        const R* Af = A + f * mF * mF;
+        const R* xf = xv + f * fs;
+        int tt = 0;
+#pragma unroll
+        for (; tt + 1 < mF; tt += 2) {
+          v0 += Af[tt * mF] * xf[tt];
+          v1 += Af[(tt + 1) * mF] * xf[tt + 1];
+        }
+        if (tt < mF) v0 += Af[tt * mF] * xf[tt];
       }
-      if (c < nc) v0 += A[c * mF] * xv[c];
       yS[q] = v0 + v1;
     }
     __syncthreads();
     for (int q = tid; q < FB * mF; q += blockDim.x) {
       const int fb = q / mF, t = q - fb * mF;
       const int r = rc[fb * 16];
-      const R v = bS[q] - tS[q] - yS[(fb * 2) * mF + t] - yS[(fb * 2 + 1) * mF + t];
+      const R v = bS[fb * fs + t] - tS[fb * fs + t] - yS[(fb * 2) * mF + t] - yS[(fb * 2 + 1) * mF + t];
       if (UPDATE) rF[q] = v;
-      else if (r >= 0) rr[coup_idx<R>(s, L, r, t)] = v;
+      else if (r >= 0) rr[(int64_t)r * fs + t] = v;
     }
     if (UPDATE) {
       __syncthreads();
@@ -1050,9 +1102,9 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
         const R* rv = rF + fb * mF;
         R v = 0;
         for (int j = 0; j < mF; ++j) v += Dr[j] * rv[j];
-        // x_F before the update is the facet's own entry in the gathered x of side 0
+        // x_F before the update is the facet's own segment in the gathered values of side 0
         const int f0 = rc[fb * 16 + 3];
-        x[coup_idx<R>(s, L, r, t)] = xT[(fb * 2) * nc + f0 * mF + t] + v;
+        x[(int64_t)r * fs + t] = xT[(fb * 2) * xe + f0 * fs + t] + v;
       }
     }
     __syncthreads();
@@ -1193,11 +1245,10 @@ static void vcycle(PrecData<R>& P, int l, const int* stop, cudaStream_t st) {
 
 template <class R>
 static size_t facet_step_smem(const ElemSizes& s, int FB, bool update) {
-  const int slab = slab_pad(s), ds = dinv_stride(s);
-  auto up16 = [](size_t v) { return (v + 15) / 16 * 16; };
+  const int slab = slab_pad(s), ds = dinv_stride(s), fs = facet_stride(s, (int)sizeof(R));
   const size_t stage = (size_t)FB * 16 * sizeof(int) + (size_t)FB * 2 * slab * sizeof(R) +
-                       (update ? (size_t)FB * ds * sizeof(R) : 0) + up16((size_t)FB * 2 * s.n_c * sizeof(R)) +
-                       2 * up16((size_t)FB * s.mF * sizeof(R));
+                       (update ? (size_t)FB * ds * sizeof(R) : 0) + (size_t)FB * 2 * (s.d + 1) * fs * sizeof(R) +
+                       2 * (size_t)FB * fs * sizeof(R);
   return 2 * stage + (size_t)FB * 3 * s.mF * sizeof(R) + 16;
 }
 
@@ -1206,6 +1257,7 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
                               const R* tb, R* x, R* rr, int64_t first, int64_t n, bool update,
                               const int* stop, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  if (L.fstride != facet_stride(s, (int)sizeof(R))) return cudaErrorInvalidValue;  // preconditioner layout only
   int FB = 256 / (2 * s.mF);
   if (FB < 1) FB = 1;
   while (FB > 1 && facet_step_smem<R>(s, FB, update) > 96 * 1024) --FB;
@@ -1305,7 +1357,7 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   const int bs = 256;
   const unsigned g = (unsigned)(sm_count() * 8);
   cudaMemsetAsync(x, 0, sizeof(R) * L.n_dd, st);
-  cudaMemsetAsync(x + L.off_h, 0, sizeof(R) * L.n_hat, st);
+  if (L.n_hat) cudaMemsetAsync(x + L.off_h, 0, sizeof(R) * L.n_hat, st);
   const int64_t* co = P.colour_off;
   for (int sw = 0; sw < P.smooth; ++sw)
     for (int c = 0; c < P.ncol; ++c)
@@ -1330,23 +1382,22 @@ cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh
                            PrecData<R>& P, const double* r, double* z, const int* stop, cudaStream_t st) {
   const int bs = 256;
   const unsigned g = (unsigned)(sm_count() * 8);
-  // b = r in precision R
+  const Layout& LE = L;                                 // external layout of r and z
+  const Layout PL = precond_layout(LE, s, sizeof(R));   // facet-interleaved internal layout
+  // b = r in precision R, preconditioner layout
+  k_to_prec<R><<<g, bs, 0, st>>>(s, LE, PL, r, P.b);
   note_launch();
-  if (sizeof(R) == 4) k_to_R_f<<<g, bs, 0, st>>>(L.ndof, r, (float*)P.b);
-  else k_to_R_d<<<g, bs, 0, st>>>(L.ndof, r, (double*)P.b);
   // first Ahat^{-1}: a = Ahat^{-1} r_u  (a in P.zz), then z_p = Shat_p^{-1}(r_p - B a) (P.x, p part)
-  cudaMemsetAsync(P.t, 0, sizeof(R) * L.n_dd, st);
-  cudaMemsetAsync(P.t + L.off_h, 0, sizeof(R) * L.n_hat, st);
-  elem_prologue<R, false>(s, t, m, L, P, P.b, nullptr, P.zz, P.t, stop, st);
-  asp_core<R>(s, m, L, P, P.b, P.t, P.zz, stop, st);
-  elem_epilogue<R, true>(s, t, m, L, nu, P, P.zz, P.b, P.zz, P.x, stop, st);
+  cudaMemsetAsync(P.t, 0, sizeof(R) * PL.n_dd, st);
+  elem_prologue<R, false>(s, t, m, PL, P, P.b, nullptr, P.zz, P.t, stop, st);
+  asp_core<R>(s, m, PL, P, P.b, P.t, P.zz, stop, st);
+  elem_epilogue<R, true>(s, t, m, PL, nu, P, P.zz, P.b, P.zz, P.x, stop, st);
   // second Ahat^{-1}: z_u = Ahat^{-1}(r_u - B^T z_p)  (P.x velocity part)
-  cudaMemsetAsync(P.t, 0, sizeof(R) * L.n_dd, st);
-  cudaMemsetAsync(P.t + L.off_h, 0, sizeof(R) * L.n_hat, st);
-  elem_prologue<R, true>(s, t, m, L, P, P.b, P.x, P.x, P.t, stop, st);
-  asp_core<R>(s, m, L, P, P.b, P.t, P.x, stop, st);
-  elem_epilogue<R, false>(s, t, m, L, nu, P, P.x, P.b, P.x, nullptr, stop, st);
-  k_from_R<R><<<g, bs, 0, st>>>(L.ndof, P.x, z, stop);
+  cudaMemsetAsync(P.t, 0, sizeof(R) * PL.n_dd, st);
+  elem_prologue<R, true>(s, t, m, PL, P, P.b, P.x, P.x, P.t, stop, st);
+  asp_core<R>(s, m, PL, P, P.b, P.t, P.x, stop, st);
+  elem_epilogue<R, false>(s, t, m, PL, nu, P, P.x, P.b, P.x, nullptr, stop, st);
+  k_from_prec<R><<<g, bs, 0, st>>>(s, LE, PL, P.x, z, stop);
   note_launch();
   return cudaGetLastError();
 }

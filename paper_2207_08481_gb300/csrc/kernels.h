@@ -31,6 +31,11 @@ struct Layout {
   int64_t ne, nint;
   int64_t n_dd, n_oo, n_hat, n_pres, ndof;
   int64_t off_o, off_h, off_p;
+  // 0: the external layout [u_d | u_o | uhat | p].  > 0: the preconditioner's internal layout, in
+  // which the m_F coupling dofs of interior facet r (its u_d modes, then its uhat modes) sit
+  // together at r*fstride .. r*fstride + m_F - 1 (fstride = m_F rounded up to 32 bytes), followed
+  // by the bubbles and the pressure; one facet's values are one 32-byte-aligned segment.
+  int64_t fstride = 0;
 };
 
 // Static mesh / table data resident on the device.
@@ -83,6 +88,23 @@ template <class S> __host__ __device__ inline int slab_pad(const S& s) { return 
 template <class S> __host__ __device__ inline int g_stride(const S& s) { return pad4(s.n_bub * s.n_c); }
 template <class S> __host__ __device__ inline int a_stride(const S& s) { return pad4(s.n_bub * s.n_bub); }
 template <class S> __host__ __device__ inline int dinv_stride(const S& s) { return pad4(s.mF * s.mF); }
+// facet stride of the preconditioner layout: m_F rounded up to a multiple of 32 bytes
+template <class S> __host__ __device__ inline int facet_stride(const S& s, int elem_bytes) {
+  const int v = 32 / elem_bytes;
+  return (s.mF + v - 1) / v * v;
+}
+template <class S>
+inline Layout precond_layout(const Layout& L, const S& s, int elem_bytes) {
+  Layout P = L;
+  P.fstride = facet_stride(s, elem_bytes);
+  P.n_dd = L.nint * P.fstride;
+  P.n_hat = 0;
+  P.off_o = P.n_dd;
+  P.off_h = P.off_o + L.n_oo;
+  P.off_p = P.off_h;
+  P.ndof = P.off_p + L.n_pres;
+  return P;
+}
 
 // A^d_T storage: per element, facet slab f (rows f*mF .. f*mF+mF-1) stored column-major,
 // Ad[(T*(d+1) + f)*slab_pad + c*mF + t] = A^d_T[f*mF + t][c], so the rows of one facet are one
