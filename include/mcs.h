@@ -157,7 +157,9 @@ int mcs_condense(mcs_handle* h);
  * elements T0 .. T0+count-1 to a host buffer.  Synchronous. */
 int mcs_copy_element_matrices(const mcs_handle* h, int64_t T0, int64_t count, double* AT_host);
 /* Copies A^d_T ([count][n_c][n_c]) and G_T ([count][n_bub][n_c]) as FP64 to host buffers;
- * coupling dofs in facet-major order (facet f: nF facet moments then nhF tangential dofs). */
+ * coupling dofs in facet-major order (facet f: nF facet moments then nhF tangential dofs).
+ * The rows of A^d_T that belong to boundary facets are not kept on the device (those dofs are
+ * eliminated by the Dirichlet condition) and come back as NaN.  Synchronous. */
 int mcs_copy_schur(const mcs_handle* h, int64_t T0, int64_t count, double* Ad_host, double* G_host);
 
 /* Physical load quadrature points, device buffer xq [ne*nq_load][dim]. */

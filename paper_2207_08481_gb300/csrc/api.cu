@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <exception>
@@ -122,11 +123,10 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
                      const std::vector<int32_t>& clist) {
   const Sizes& s = h->sz;
   const int64_t ne = h->mesh.ne, nint = h->mesh.nint;
-  P.Ad = h->dalloc<R>(ne * (int64_t)(s.d + 1) * slab_pad(s));
+  P.Fs = h->dalloc<R>(nint * (int64_t)fs_stride(s));
+  cuda_check(cudaMemset((void*)P.Fs, 0, sizeof(R) * nint * (int64_t)fs_stride(s)), "memset");  // padding
   P.G = h->dalloc<R>(ne * (int64_t)g_stride(s));
   P.Aoi = h->dalloc<R>(ne * (int64_t)a_stride(s));
-  P.Dinv = h->dalloc<R>(nint * (int64_t)dinv_stride(s));
-  cuda_check(cudaMemset((void*)P.Dinv, 0, sizeof(R) * nint * (int64_t)dinv_stride(s)), "memset");
   P.Eb = h->upload(cast_vec<R>(Eb));
   P.fvr = h->upload(fvr);
   P.vf_ptr = h->upload(vf_ptr);
@@ -175,6 +175,13 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   P.coarse_tmp = nullptr;
   P.err = h->dalloc<int>(1);
   cuda_check(cudaMemset(P.err, 0, sizeof(int)), "memset");
+  const char* dbg = std::getenv("MCS_DEBUG_CHECKS");
+  if (dbg && dbg[0] == '1') {
+    P.debug = true;
+    h->use_graphs = false;  // the diagnostics synchronise after launches
+    P.dbg = h->dalloc<int>(8);
+    cuda_check(cudaMemset(P.dbg, 0, 8 * sizeof(int)), "memset");
+  }
 }
 
 void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
@@ -271,6 +278,9 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
       if (h->colour[r] == c) clist.push_back((int32_t)r);
   }
   h->colour_off[h->ncol] = (int64_t)clist.size();
+  h->fpos.assign(m.nint, -1);
+  for (size_t li = 0; li < clist.size(); ++li) h->fpos[clist[li]] = (int32_t)li;
+  dm.fpos = h->upload(h->fpos);
   {
     // facet records in colour order
     std::vector<int32_t> rec(clist.size() * 16, -1);
@@ -563,16 +573,15 @@ int mcs_condense(mcs_handle* h) {
     if (!h) throw McsError(MCS_ERR_INVALID_ARG, "NULL handle");
     ProfScope ps(h->prof.get());
     if (h->opt.precision == MCS_MIXED) {
-      cuda_check(launch_condense<float>(h->es, h->dt, h->dm, h->nu, h->K, (float*)h->pf.Ad, (float*)h->pf.G,
+      cuda_check(launch_condense<float>(h->es, h->dt, h->dm, h->nu, h->K, h->pf.Fs, (float*)h->pf.G,
                                         (float*)h->pf.Aoi, h->cond_scratch, h->cond_scratch_doubles, h->stream),
                  "condense");
-      cuda_check(launch_facet_blocks<float>(h->es, h->dm, h->pf.Ad, (float*)h->pf.Dinv, h->stream), "facet blocks");
+      cuda_check(launch_facet_blocks<float>(h->es, h->dm, h->pf.Fs, h->stream), "facet blocks");
     } else {
-      cuda_check(launch_condense<double>(h->es, h->dt, h->dm, h->nu, h->K, (double*)h->pd.Ad, (double*)h->pd.G,
+      cuda_check(launch_condense<double>(h->es, h->dt, h->dm, h->nu, h->K, h->pd.Fs, (double*)h->pd.G,
                                          (double*)h->pd.Aoi, h->cond_scratch, h->cond_scratch_doubles, h->stream),
                  "condense");
-      cuda_check(launch_facet_blocks<double>(h->es, h->dm, h->pd.Ad, (double*)h->pd.Dinv, h->stream),
-                 "facet blocks");
+      cuda_check(launch_facet_blocks<double>(h->es, h->dm, h->pd.Fs, h->stream), "facet blocks");
     }
     h->condensed = true;
     return MCS_OK;
@@ -621,17 +630,35 @@ int mcs_copy_schur(const mcs_handle* h, int64_t T0, int64_t count, double* Ad_ho
                               cudaMemcpyDeviceToHost), "copy");
       }
     };
-    const void* Ad = h->opt.precision == MCS_MIXED ? (const void*)h->pf.Ad : (const void*)h->pd.Ad;
+    const void* Fs = h->opt.precision == MCS_MIXED ? (const void*)h->pf.Fs : (const void*)h->pd.Fs;
     const void* G = h->opt.precision == MCS_MIXED ? (const void*)h->pf.G : (const void*)h->pd.G;
     if (Ad_host) {
-      const int64_t per = (int64_t)(s.d + 1) * slab_pad(s), nc2 = (int64_t)s.n_c * s.n_c;
-      std::vector<double> tmp(per * count);
-      fetch(Ad, per, tmp.data());
-      for (int64_t T = 0; T < count; ++T)
-        for (int i = 0; i < s.n_c; ++i)
-          for (int c = 0; c < s.n_c; ++c)
-            Ad_host[T * nc2 + (int64_t)i * s.n_c + c] =
-                tmp[adw_index(s.d + 1, slab_pad(s), s.mF, T, i / s.mF, c, i % s.mF)];
+      // rows of interior facets from the facet stream; rows of boundary facets are not stored (NaN)
+      const int64_t fss = fs_stride(s), nc2 = (int64_t)s.n_c * s.n_c, nint = h->mesh.nint;
+      std::vector<double> stream(fss * nint);
+      if (h->opt.precision == MCS_MIXED) {
+        std::vector<float> tmp(fss * nint);
+        cuda_check(cudaMemcpy(tmp.data(), Fs, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost), "copy");
+        for (size_t i = 0; i < tmp.size(); ++i) stream[i] = tmp[i];
+      } else {
+        cuda_check(cudaMemcpy(stream.data(), Fs, sizeof(double) * stream.size(), cudaMemcpyDeviceToHost), "copy");
+      }
+      const int mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s);
+      for (int64_t e = 0; e < count; ++e) {
+        const int64_t T = T0 + e;
+        for (int f = 0; f < dp1; ++f) {
+          const int32_t rk = h->mesh.elem_rank[T * dp1 + f];
+          const double* blk = nullptr;
+          if (rk >= 0) {
+            const int32_t F = h->mesh.int_facets[rk];
+            const int side = h->mesh.facet_elems[(int64_t)F * 2] == (int32_t)T ? 0 : 1;
+            blk = stream.data() + (int64_t)h->fpos[rk] * fss + side * slab;
+          }
+          for (int t = 0; t < mF; ++t)
+            for (int c = 0; c < s.n_c; ++c)
+              Ad_host[e * nc2 + (int64_t)(f * mF + t) * s.n_c + c] = blk ? blk[c * mF + t] : std::nan("");
+        }
+      }
     }
     if (G_host) {
       const int64_t per = g_stride(s), ng = (int64_t)s.n_bub * s.n_c;

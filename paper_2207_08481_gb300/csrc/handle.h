@@ -52,6 +52,7 @@ struct mcs_handle {
   int ncol = 0;
   std::vector<int32_t> colour;          // per interior rank
   std::vector<int64_t> colour_off;      // host offsets into colour_list
+  std::vector<int32_t> fpos;            // interior rank -> position in colour order
   int nlev = 0;
   std::vector<int> level_N;
   int64_t np1 = 0;

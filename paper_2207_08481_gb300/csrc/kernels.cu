@@ -60,7 +60,7 @@ struct BlockSync {
 // One thread block per element (grid-stride).  Workspace in dynamic shared memory when
 // it fits, else in a global scratch slot per resident block.
 template <class R, bool SMEM>
-__global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, KOp K, R* Ad,
+__global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, KOp K, R* Fs,
                                                   R* G, R* Aoi, double* gscratch, int64_t slot_doubles) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x, nl = blockDim.x;
@@ -101,10 +101,15 @@ __global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevM
     }
     __syncthreads();
     bubble_condense(s, w.A, bw, Adt, Gt, Ait, lane, nl, BlockSync());
-    const int nc = s.n_c, no = s.n_bub;
-    for (int q = lane; q < nc * nc; q += nl) {
-      int i = q / nc, c = q % nc;   // row i = f*mF + t
-      Ad[adw_index(d + 1, slab_pad(s), s.mF, T, i / s.mF, c, i % s.mF)] = (R)Adt[q];
+    const int nc = s.n_c, no = s.n_bub, mF = s.mF, fss = fs_stride(s), slab = slab_pad(s);
+    // slabs of the interior facets into the facet stream (boundary facets carry no dofs)
+    for (int q = lane; q < nc * nc; q += nl) {   // q = (f*nc + c)*mF + tt: contiguous slab writes
+      const int f = q / (nc * mF), rem = q - f * nc * mF, c = rem / mF, tt = rem - c * mF;
+      const int i = f * mF + tt;                 // row of A^d_T
+      const int32_t rk = m.elem_rank[T * (d + 1) + f];
+      if (rk < 0) continue;
+      const int side = m.fel[2 * (int64_t)rk] == (int32_t)T ? 0 : 1;
+      Fs[(int64_t)m.fpos[rk] * fss + side * slab + c * mF + tt] = (R)Adt[i * nc + c];
     }
     for (int q = lane; q < no * nc; q += nl) G[T * g_stride(s) + q] = (R)Gt[q];
     for (int q = lane; q < no * no; q += nl) Aoi[T * a_stride(s) + q] = (R)Ait[q];
@@ -121,7 +126,7 @@ static int64_t condense_slot_doubles(const ElemSizes& s) {
 static int condense_threads(const ElemSizes& s) { return s.d == 2 ? 128 : 256; }
 
 template <class R>
-cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K, R* Ad,
+cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K, R* Fs,
                             R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st) {
   const int64_t slot = condense_slot_doubles(s);
   int dev = 0, nsm = 0, maxsm = 0;
@@ -140,13 +145,13 @@ cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMes
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)nsm * per_sm;
     if (blocks > m.ne) blocks = m.ne;
-    k_condense<R, true><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, nu, K, Ad, G, Aoi, nullptr, slot);
+    k_condense<R, true><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, nu, K, Fs, G, Aoi, nullptr, slot);
     note_launch();
   } else {
     int64_t blocks = scratch_doubles / slot;
     if (blocks < 1) return cudaErrorMemoryAllocation;
     if (blocks > m.ne) blocks = m.ne;
-    k_condense<R, false><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, nu, K, Ad, G, Aoi, scratch, slot);
+    k_condense<R, false><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, nu, K, Fs, G, Aoi, scratch, slot);
     note_launch();
   }
   {
@@ -157,7 +162,8 @@ cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMes
                             ncp * ncp * no + no * no * no) +
                      2.0 * nA * nr * s.n_s0;
     const double out = (double)m.ne * ((K.AT ? nA * nA * 8 : 0.0) + (K.Ahi ? 8.0 * packed_pad(s) : 0.0) +
-                                       (double)((s.d + 1) * slab_pad(s) + g_stride(s) + a_stride(s)) * sizeof(R));
+                                       (double)(g_stride(s) + a_stride(s)) * sizeof(R)) +
+                       (double)m.nint * 2.0 * slab_pad(s) * sizeof(R);
     prof_end(PROF_CONDENSE, out, f * (double)m.ne, st);
   }
   return cudaGetLastError();
@@ -169,7 +175,7 @@ int64_t condense_scratch_doubles(const ElemSizes& s, int nsm) {
 
 // ---------------------------------------------------------------- facet blocks
 template <class R>
-__global__ void k_facet_blocks(ElemSizes s, DevMesh m, const R* Ad, R* Dinv) {
+__global__ void k_facet_blocks(ElemSizes s, DevMesh m, R* Fs) {
   extern __shared__ double sm2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int mF = s.mF, nc = s.n_c;
@@ -179,10 +185,10 @@ __global__ void k_facet_blocks(ElemSizes s, DevMesh m, const R* Ad, R* Dinv) {
     for (int q = lane; q < mF * mF; q += 32) {
       int i = q / mF, j = q % mF;
       double v = 0;
+      const R* blk = Fs + (int64_t)m.fpos[r] * fs_stride(s);
       for (int side = 0; side < 2; ++side) {
-        int64_t T = m.fel[r * 2 + side];
-        int f = m.floc[r * 2 + side];
-        v += (double)Ad[adw_index(s.d + 1, slab_pad(s), mF, T, f, f * mF + j, i)];
+        const int f = m.floc[r * 2 + side];
+        v += (double)blk[side * slab_pad(s) + (f * mF + j) * mF + i];
       }
       A[q] = v;
       I[q] = (i == j) ? 1.0 : 0.0;
@@ -214,13 +220,14 @@ __global__ void k_facet_blocks(ElemSizes s, DevMesh m, const R* Ad, R* Dinv) {
         if (rr != c) A[rr * mF + c] = 0.0;
       __syncwarp();
     }
-    for (int q = lane; q < mF * mF; q += 32) Dinv[r * dinv_stride(s) + q] = (R)(0.5 * (I[q] + I[(q % mF) * mF + q / mF]));
+    R* Dinv = Fs + (int64_t)m.fpos[r] * fs_stride(s) + 2 * slab_pad(s);
+    for (int q = lane; q < mF * mF; q += 32) Dinv[q] = (R)(0.5 * (I[q] + I[(q % mF) * mF + q / mF]));
     __syncwarp();
   }
 }
 
 template <class R>
-cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, const R* Ad, R* Dinv, cudaStream_t st) {
+cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, R* Fs, cudaStream_t st) {
   if (m.nint == 0) return cudaSuccess;
   int wpb = 4;
   size_t sm = (size_t)wpb * 2 * s.mF * s.mF * sizeof(double);
@@ -228,7 +235,7 @@ cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, const R* A
   int64_t blocks = (m.nint + wpb - 1) / wpb;
   if (blocks > 65535 * 8) blocks = 65535 * 8;
   prof_begin(PROF_FACET_BLOCKS, st);
-  k_facet_blocks<R><<<(unsigned)blocks, wpb * 32, sm, st>>>(s, m, Ad, Dinv);
+  k_facet_blocks<R><<<(unsigned)blocks, wpb * 32, sm, st>>>(s, m, Fs);
   note_launch();
   prof_end(PROF_FACET_BLOCKS, (double)m.nint * (2.0 * s.mF * s.mF + s.mF * s.mF) * sizeof(R), 0.0, st);
   return cudaGetLastError();
@@ -955,34 +962,45 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
 // Facets of one colour share no element, so the copies of batch i+1 never read values that
 // batch i updates.
 template <class R, class S, bool UPDATE>
-__global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, const R* __restrict__ Ad,
-                                                    const R* __restrict__ Dinv, const R* __restrict__ b,
+__global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, const R* __restrict__ Fs,
+                                                    const R* __restrict__ b,
                                                     const R* __restrict__ tb, R* x, R* rr,
                                                     const int4* __restrict__ rec, int64_t n, int FB,
-                                                    const int* stop) {
+                                                    const int* stop, int* dbg, int64_t fs_avail,
+                                                    int smem_bytes) {
   if (stop && *stop) return;
+  // diagnostics: returns false (and records the first failure) for an access outside its buffer
+  // or a 16-byte copy off its alignment
+  auto ok = [&](int code, int64_t off, int64_t len, int64_t size, const void* addr, bool a16) -> bool {
+    if (!dbg) return true;
+    const bool good = off >= 0 && off + len <= size && (!a16 || (reinterpret_cast<uintptr_t>(addr) & 15) == 0);
+    if (!good && atomicCAS(dbg, 0, code) == 0) {
+      dbg[1] = (int)blockIdx.x;
+      dbg[2] = (int)(off & 0x7fffffff);
+      dbg[3] = (int)(size & 0x7fffffff);
+    }
+    return good;
+  };
   extern __shared__ __align__(16) unsigned char sraw[];
-  const int mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), ds = dinv_stride(s);
+  const int mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), fss = fs_stride(s);
   const int fs = facet_stride(s, (int)sizeof(R));   // equals L.fstride
   const int xe = dp1 * fs;                          // gathered values per (facet, side)
   // stage layout (both stages identical, 16-byte aligned pieces)
   unsigned char* sbase = sraw;
   const int rec_b = FB * 16 * (int)sizeof(int);
-  const int as_b = FB * 2 * slab * (int)sizeof(R);
-  const int di_b = UPDATE ? FB * ds * (int)sizeof(R) : 0;
+  const int fsb = FB * fss * (int)sizeof(R);        // the batch's facet-stream blocks
   const int xt_b = FB * 2 * xe * (int)sizeof(R);
   const int bb_b = FB * fs * (int)sizeof(R);
-  const int stage_b = rec_b + as_b + di_b + xt_b + 2 * bb_b;
+  const int stage_b = rec_b + fsb + xt_b + 2 * bb_b;
   R* yS = (R*)(sbase + 2 * stage_b);       // [FB][2][mF]
   R* rF = yS + FB * 2 * mF;                // [FB][mF]
   auto RC = [&](int st) { return (int*)(sbase + st * stage_b); };
-  auto AS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b); };
-  auto DI = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b); };
-  auto XT = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b + di_b); };
-  auto BS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b + di_b + xt_b); };
-  auto TS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + as_b + di_b + xt_b + bb_b); };
+  auto FSB = [&](int st) { return (R*)(sbase + st * stage_b + rec_b); };
+  auto XT = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + fsb); };
+  auto BS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + fsb + xt_b); };
+  auto TS = [&](int st) { return (R*)(sbase + st * stage_b + rec_b + fsb + xt_b + bb_b); };
   constexpr int V = 16 / (int)sizeof(R);
-  const int cs = slab / V, cd = ds / V, cx = fs / V;
+  const int cf = fss / V, cslab = 2 * slab / V, cx = fs / V;
   const int tid = threadIdx.x;
   const int64_t nb = (n + FB - 1) / FB;
   const uint64_t pol = l2_evict_first_policy();
@@ -996,41 +1014,45 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
       reinterpret_cast<int4*>(rc)[q] = v;
     }
   };
-  auto issue = [&](int st) {
+  auto issue = [&](int st, int64_t bi) {
     const int* rc = RC(st);
-    R* As = AS(st);
-    R* Di = DI(st);
+    R* Fb = FSB(st);
     R* xT = XT(st);
     R* bS = BS(st);
     R* tS = TS(st);
-    for (int q = tid; q < FB * 2 * cs; q += blockDim.x) {
-      const int fsd = q / cs, ch = q - fsd * cs, fb = fsd >> 1, side = fsd & 1;
-      const int* r_ = rc + fb * 16;
-      if (r_[0] >= 0)
-        cp_async16_hint(As + fsd * slab + ch * V,
-                        Ad + adw_index(dp1, slab, mF, r_[1 + side], r_[3 + side], 0, 0) + ch * V, pol);
+    // the batch's stream blocks are one contiguous range (without D_F^{-1} for the residual pass)
+    const int nvalid = (int)((n - bi * FB) < FB ? (n - bi * FB) : FB);
+    const R* src = Fs + bi * FB * (int64_t)fss;
+    for (int q = tid; q < nvalid * cf; q += blockDim.x) {
+      if (!UPDATE && q % cf >= cslab) continue;
+      R* dst = Fb + q * V;
+      const R* sp = src + (int64_t)q * V;
+      if (!ok(1, (const unsigned char*)dst - sraw, 16, smem_bytes, dst, true)) continue;
+      if (!ok(2, bi * FB * (int64_t)fss + (int64_t)q * V, V, fs_avail, sp, true)) continue;
+      cp_async16_hint(dst, sp, pol);
     }
-    if (UPDATE)
-      for (int q = tid; q < FB * cd; q += blockDim.x) {
-        const int fb = q / cd, ch = q - fb * cd;
-        const int r = rc[fb * 16];
-        if (r >= 0) cp_async16_hint(Di + fb * ds + ch * V, Dinv + (int64_t)r * ds + ch * V, pol);
-      }
     for (int q = tid; q < FB * 2 * dp1 * cx; q += blockDim.x) {
       const int seg = q / cx, ch = q - seg * cx;          // seg = (fb*2 + side)*dp1 + f
       const int fsd = seg / dp1, f = seg - fsd * dp1, fb = fsd >> 1, side = fsd & 1;
       const int* r_ = rc + fb * 16;
       const int32_t g = r_[0] >= 0 ? r_[5 + side * dp1 + f] : -1;
       R* dst = xT + seg * fs + ch * V;
-      if (g >= 0) cp_async16(dst, x + (int64_t)g * fs + ch * V);
-      else *reinterpret_cast<int4*>(dst) = make_int4(0, 0, 0, 0);
+      if (!ok(3, (const unsigned char*)dst - sraw, 16, smem_bytes, dst, true)) continue;
+      if (g >= 0) {
+        if (!ok(4, (int64_t)g * fs + ch * V, V, L.ndof, x + (int64_t)g * fs + ch * V, true)) continue;
+        cp_async16(dst, x + (int64_t)g * fs + ch * V);
+      } else {
+        *reinterpret_cast<int4*>(dst) = make_int4(0, 0, 0, 0);
+      }
     }
     for (int q = tid; q < FB * cx; q += blockDim.x) {
       const int fb = q / cx, ch = q - fb * cx;
       const int r = rc[fb * 16];
       R* db = bS + fb * fs + ch * V;
       R* dt = tS + fb * fs + ch * V;
+      if (!ok(5, (const unsigned char*)dt - sraw, 16, smem_bytes, dt, true)) continue;
       if (r >= 0) {
+        if (!ok(6, (int64_t)r * fs + ch * V, V, L.ndof, b + (int64_t)r * fs + ch * V, true)) continue;
         cp_async16(db, b + (int64_t)r * fs + ch * V);
         if (tb) cp_async16(dt, tb + (int64_t)r * fs + ch * V);
         else *reinterpret_cast<int4*>(dt) = make_int4(0, 0, 0, 0);
@@ -1046,7 +1068,7 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
   if (bi < nb) {
     load_records(0, bi);
     __syncthreads();
-    issue(0);
+    issue(0, bi);
   }
   cp_async_commit();
   while (bi < nb) {
@@ -1054,20 +1076,19 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
     const int ns = st ^ 1;
     if (nbi < nb) load_records(ns, nbi);
     __syncthreads();
-    if (nbi < nb) issue(ns);
+    if (nbi < nb) issue(ns, nbi);
     cp_async_commit();
     cp_async_wait_group<1>();
     __syncthreads();
     // ---- compute batch bi from stage st
     const int* rc = RC(st);
-    const R* As = AS(st);
-    const R* Di = DI(st);
+    const R* Fb = FSB(st);
     const R* xT = XT(st);
     const R* bS = BS(st);
     const R* tS = TS(st);
     for (int q = tid; q < FB * 2 * mF; q += blockDim.x) {
       const int fsd = q / mF, t = q - fsd * mF;
-      const R* A = As + fsd * slab + t;
+      const R* A = Fb + (fsd >> 1) * fss + (fsd & 1) * slab + t;
       const R* xv = xT + fsd * xe;
       R v0 = 0, v1 = 0;
 #pragma unroll
@@ -1090,7 +1111,7 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
       const int r = rc[fb * 16];
       const R v = bS[fb * fs + t] - tS[fb * fs + t] - yS[(fb * 2) * mF + t] - yS[(fb * 2 + 1) * mF + t];
       if (UPDATE) rF[q] = v;
-      else if (r >= 0) rr[(int64_t)r * fs + t] = v;
+      else if (r >= 0 && ok(7, (int64_t)r * fs + t, 1, L.ndof, rr, false)) rr[(int64_t)r * fs + t] = v;
     }
     if (UPDATE) {
       __syncthreads();
@@ -1098,12 +1119,13 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
         const int fb = q / mF, t = q - fb * mF;
         const int r = rc[fb * 16];
         if (r < 0) continue;
-        const R* Dr = Di + fb * ds + t * mF;
+        const R* Dr = Fb + fb * fss + 2 * slab + t * mF;
         const R* rv = rF + fb * mF;
         R v = 0;
         for (int j = 0; j < mF; ++j) v += Dr[j] * rv[j];
         // x_F before the update is the facet's own segment in the gathered values of side 0
         const int f0 = rc[fb * 16 + 3];
+        if (!ok(8, (int64_t)r * fs + t, 1, L.ndof, x, false) || !ok(9, f0, 1, dp1, x, false)) continue;
         x[(int64_t)r * fs + t] = xT[(fb * 2) * xe + f0 * fs + t] + v;
       }
     }
@@ -1243,12 +1265,32 @@ static void vcycle(PrecData<R>& P, int l, const int* stop, cudaStream_t st) {
   if (x != P.px[l]) cudaMemcpyAsync(P.px[l], x, sizeof(R) * G.n, cudaMemcpyDeviceToDevice, st);
 }
 
+// Diagnostics mode: synchronise after a preconditioner launch and report a failure by name.
+template <class R>
+static void dbg_sync(const PrecData<R>& P, cudaStream_t st, const char* what) {
+  if (!P.debug) return;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "mcs diagnostics: %s failed: %s\n", what, cudaGetErrorString(e));
+    std::fflush(stderr);
+    return;
+  }
+  int hv[4] = {0, 0, 0, 0};
+  cudaMemcpy(hv, P.dbg, sizeof(hv), cudaMemcpyDeviceToHost);
+  if (hv[0]) {
+    std::fprintf(stderr, "mcs diagnostics: %s: check %d failed (block %d, offset %d, size %d)\n", what, hv[0], hv[1],
+                 hv[2], hv[3]);
+    std::fflush(stderr);
+  }
+}
+
 template <class R>
 static size_t facet_step_smem(const ElemSizes& s, int FB, bool update) {
-  const int slab = slab_pad(s), ds = dinv_stride(s), fs = facet_stride(s, (int)sizeof(R));
-  const size_t stage = (size_t)FB * 16 * sizeof(int) + (size_t)FB * 2 * slab * sizeof(R) +
-                       (update ? (size_t)FB * ds * sizeof(R) : 0) + (size_t)FB * 2 * (s.d + 1) * fs * sizeof(R) +
-                       2 * (size_t)FB * fs * sizeof(R);
+  (void)update;
+  const int fs = facet_stride(s, (int)sizeof(R));
+  const size_t stage = (size_t)FB * 16 * sizeof(int) + (size_t)FB * fs_stride(s) * sizeof(R) +
+                       (size_t)FB * 2 * (s.d + 1) * fs * sizeof(R) + 2 * (size_t)FB * fs * sizeof(R);
   return 2 * stage + (size_t)FB * 3 * s.mF * sizeof(R) + 16;
 }
 
@@ -1265,6 +1307,8 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
   const size_t sm = facet_step_smem<R>(s, FB, update);
   const int64_t nb = (n + FB - 1) / FB;
   const int4* rec = m.frec + first * 4;
+  const R* fsrc = P.Fs + first * (int64_t)fs_stride(s);
+  const int64_t fs_avail = (L.nint - first) * (int64_t)fs_stride(s);
   dispatch_sizes(s, [&](auto sz) {
     using SZ = decltype(sz);
     static std::atomic<int> per_sm[2];
@@ -1283,17 +1327,18 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
     prof_begin(cls, st);
     note_launch();
     if (update)
-      k_facet_step<R, SZ, true><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, rec, n, FB,
-                                                                        stop);
+      k_facet_step<R, SZ, true><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, fsrc, b, tb, x, rr, rec, n, FB, stop,
+                                                                        P.dbg, fs_avail, (int)sm);
     else
-      k_facet_step<R, SZ, false><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, P.Ad, P.Dinv, b, tb, x, rr, rec, n,
-                                                                         FB, stop);
+      k_facet_step<R, SZ, false><<<(unsigned)blocks, threads, sm, st>>>(sz, m, L, fsrc, b, tb, x, rr, rec, n, FB, stop,
+                                                                         P.dbg, fs_avail, (int)sm);
     // algorithmic bytes per facet: the facet's rows of A^d from both elements, D_F^{-1}, b, tb,
     // x_F read and written (update) or rr_F written (residual)
     const double per = update ? (2.0 * s.mF * s.n_c + (double)s.mF * s.mF + 4.0 * s.mF)
                               : (2.0 * s.mF * s.n_c + 3.0 * s.mF);
     prof_end(cls, (double)n * per * sizeof(R), 2.0 * (double)n * (2.0 * s.mF * s.n_c + (update ? s.mF * s.mF : 0)), st);
   });
+  dbg_sync(P, st, update ? "k_facet_step (update)" : "k_facet_step (residual)");
   return cudaGetLastError();
 }
 
@@ -1367,9 +1412,12 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   prof_begin(PROF_GMG, st);
   k_embed_T<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.vf_ptr, P.vf_idx, P.nP1, P.rr, P.pb[top], stop);
   note_launch();
+  dbg_sync(P, st, "k_embed_T");
   vcycle<R>(P, top, stop, st);
+  dbg_sync(P, st, "V-cycle");
   k_embed<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.fvr, L.nint, P.px[top], x, stop);
   note_launch();
+  dbg_sync(P, st, "k_embed");
   prof_end(PROF_GMG, 0.0, 0.0, st);
   for (int sw = 0; sw < P.smooth; ++sw)
     for (int c = P.ncol - 1; c >= 0; --c)
@@ -1387,11 +1435,14 @@ cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh
   // b = r in precision R, preconditioner layout
   k_to_prec<R><<<g, bs, 0, st>>>(s, LE, PL, r, P.b);
   note_launch();
+  dbg_sync(P, st, "k_to_prec");
   // first Ahat^{-1}: a = Ahat^{-1} r_u  (a in P.zz), then z_p = Shat_p^{-1}(r_p - B a) (P.x, p part)
   cudaMemsetAsync(P.t, 0, sizeof(R) * PL.n_dd, st);
   elem_prologue<R, false>(s, t, m, PL, P, P.b, nullptr, P.zz, P.t, stop, st);
+  dbg_sync(P, st, "k_elem_prologue");
   asp_core<R>(s, m, PL, P, P.b, P.t, P.zz, stop, st);
   elem_epilogue<R, true>(s, t, m, PL, nu, P, P.zz, P.b, P.zz, P.x, stop, st);
+  dbg_sync(P, st, "k_elem_epilogue");
   // second Ahat^{-1}: z_u = Ahat^{-1}(r_u - B^T z_p)  (P.x velocity part)
   cudaMemsetAsync(P.t, 0, sizeof(R) * PL.n_dd, st);
   elem_prologue<R, true>(s, t, m, PL, P, P.b, P.x, P.x, P.t, stop, st);
@@ -1399,6 +1450,7 @@ cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh
   elem_epilogue<R, false>(s, t, m, PL, nu, P, P.x, P.b, P.x, nullptr, stop, st);
   k_from_prec<R><<<g, bs, 0, st>>>(s, LE, PL, P.x, z, stop);
   note_launch();
+  dbg_sync(P, st, "k_from_prec");
   return cudaGetLastError();
 }
 
@@ -1626,9 +1678,8 @@ template cudaError_t launch_condense<float>(const ElemSizes&, const DevTables&, 
                                             float*, float*, float*, double*, int64_t, cudaStream_t);
 template cudaError_t launch_condense<double>(const ElemSizes&, const DevTables&, const DevMesh&, double, KOp,
                                              double*, double*, double*, double*, int64_t, cudaStream_t);
-template cudaError_t launch_facet_blocks<float>(const ElemSizes&, const DevMesh&, const float*, float*, cudaStream_t);
-template cudaError_t launch_facet_blocks<double>(const ElemSizes&, const DevMesh&, const double*, double*,
-                                                 cudaStream_t);
+template cudaError_t launch_facet_blocks<float>(const ElemSizes&, const DevMesh&, float*, cudaStream_t);
+template cudaError_t launch_facet_blocks<double>(const ElemSizes&, const DevMesh&, double*, cudaStream_t);
 template cudaError_t launch_precond<float>(const ElemSizes&, const DevTables&, const DevMesh&, const Layout&, double,
                                            PrecData<float>&, const double*, double*, const int*, cudaStream_t);
 template cudaError_t launch_precond<double>(const ElemSizes&, const DevTables&, const DevMesh&, const Layout&, double,

@@ -54,6 +54,7 @@ struct DevMesh {
   // [3..4] local facet indices, [5..] interior ranks of the facets of element 0 (d+1), then of
   // element 1 (d+1); unused entries -1
   const int4* frec;
+  const int32_t* fpos;       // [nint] position of interior facet r in colour order (its record index)
 };
 
 
@@ -106,12 +107,15 @@ inline Layout precond_layout(const Layout& L, const S& s, int elem_bytes) {
   return P;
 }
 
-// A^d_T storage: per element, facet slab f (rows f*mF .. f*mF+mF-1) stored column-major,
-// Ad[(T*(d+1) + f)*slab_pad + c*mF + t] = A^d_T[f*mF + t][c], so the rows of one facet are one
-// contiguous, aligned block.
-__host__ __device__ inline int64_t adw_index(int dp1, int slabp, int mF, int64_t T, int f, int c, int t) {
-  return (T * dp1 + f) * (int64_t)slabp + (int64_t)c * mF + t;
-}
+// Facet stream: everything the facet-block smoother reads per interior facet, stored in colour
+// order (record index i = fpos[r]) as one contiguous, 16-byte-aligned block of fs_stride entries:
+//   [slab of side 0 | slab of side 1 | D_F^{-1}]
+// where the slab of side s holds the m_F rows of A^d_T of that side's element T (the element
+// fel[2r + s]) belonging to the facet, column-major over T's n_c coupling dofs:
+//   slab[c*mF + t] = A^d_T[f*mF + t][c]   (f = the facet's local index in T),
+// and D_F^{-1} is row-major [m_F][m_F] (stride dinv_stride).  A colour sweep therefore reads one
+// contiguous range of the stream.
+template <class S> __host__ __device__ inline int fs_stride(const S& s) { return 2 * slab_pad(s) + dinv_stride(s); }
 
 struct DevTables {
   const double* B0;
@@ -143,10 +147,10 @@ template <class S> __host__ __device__ inline int packed_pad(const S& s) { retur
 
 template <class R>
 cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K,
-                            R* Ad, R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st);
-// Facet blocks D_F of A^d (sum of the two elements), inverted.
+                            R* Fs, R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st);
+// Facet blocks D_F of A^d (sum of the two elements' slabs), inverted into the facet stream.
 template <class R>
-cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, const R* Ad, R* Dinv, cudaStream_t st);
+cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, R* Fs, cudaStream_t st);
 
 // ---------------------------------------------------------------- operators (FP64)
 // y = K x
@@ -185,10 +189,9 @@ struct GmgLevel {
 
 template <class R>
 struct PrecData {
-  const R* Ad;
+  R* Fs;                    // facet stream [nint][fs_stride] in colour order (slabs of A^d, D_F^{-1})
   const R* G;
   const R* Aoi;
-  const R* Dinv;
   const R* Eb;              // [nint][mF][d*d]
   const int32_t* fvr;       // [nint][d] P1 rank of each facet vertex (-1 on the boundary)
   const int32_t* vf_ptr;    // P1 vertex -> (facet rank, facet-vertex index) list, CSR over P1 vertices
@@ -206,6 +209,11 @@ struct PrecData {
   // work vectors (R), all length ndof unless noted
   R *b, *x, *t, *rr, *zz;
   int* err;  // device flag: set when a bounded wait on an asynchronous copy gave up
+  // diagnostics (environment MCS_DEBUG_CHECKS=1 at set-up): the facet step checks every address
+  // against its buffer and records the first bad one in dbg[0..3] instead of accessing it, and
+  // the host synchronises after every preconditioner launch and names a kernel that failed
+  int* dbg = nullptr;
+  bool debug = false;
   R *pb[12], *px[12], *pr[12], *ptmp[12];  // GMG vectors per level
   double* coarse_tmp;  // [n0]
 };
