@@ -175,6 +175,9 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   P.coarse_tmp = nullptr;
   P.err = h->dalloc<int>(1);
   cuda_check(cudaMemset(P.err, 0, sizeof(int)), "memset");
+  P.gbar = h->dalloc<unsigned>(2);
+  cuda_check(cudaMemset(P.gbar, 0, 2 * sizeof(unsigned)), "memset");
+  P.fused_blocks = gmg_fused_blocks<R>();
   const char* dbg = std::getenv("MCS_DEBUG_CHECKS");
   if (dbg && dbg[0] == '1') {
     P.debug = true;
@@ -906,6 +909,8 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       cuda_check(cudaStreamSynchronize(st), "sync");
       if (herr) {
         cuda_check(cudaMemsetAsync(errp, 0, sizeof(int), st), "memset");
+        unsigned* gbar = h->opt.precision == MCS_MIXED ? h->pf.gbar : h->pd.gbar;  // barrier left mid-way
+        cuda_check(cudaMemsetAsync(gbar, 0, 2 * sizeof(unsigned), st), "memset");
         status = MCS_ERR_TIMEOUT;
         if (info) info->status = status;
       }

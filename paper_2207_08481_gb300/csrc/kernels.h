@@ -214,9 +214,17 @@ struct PrecData {
   // the host synchronises after every preconditioner launch and names a kernel that failed
   int* dbg = nullptr;
   bool debug = false;
+  // fused V-cycle: one cooperative launch for E^T, the whole V-cycle and E (grid barrier state:
+  // [0] arrivals of this launch, [1] blocks finished)
+  unsigned* gbar = nullptr;
+  int fused_blocks = 0;     // 0: separate launches per level
   R *pb[12], *px[12], *pr[12], *ptmp[12];  // GMG vectors per level
   double* coarse_tmp;  // [n0]
 };
+
+// blocks of the fused V-cycle launch on this device (0: not available)
+template <class R>
+int gmg_fused_blocks();
 
 template <class R>
 cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
