@@ -115,6 +115,30 @@ std::vector<int32_t> to_i32(const std::vector<int64_t>& v) {
   return o;
 }
 
+// CSR -> column-major ELL on the device (precision R)
+template <class R>
+Ell to_ell(mcs_handle* h, const Csr& M) {
+  Ell E;
+  E.n = M.nrows;
+  int64_t k = 0;
+  for (int64_t r = 0; r < M.nrows; ++r) k = std::max<int64_t>(k, M.rowptr[r + 1] - M.rowptr[r]);
+  if (M.ncols < 1) k = 0;
+  E.k = (int)k;
+  std::vector<int32_t> col(std::max<int64_t>(1, k * M.nrows));
+  std::vector<R> val(std::max<int64_t>(1, k * M.nrows), (R)0);
+  for (int64_t r = 0; r < M.nrows; ++r) {
+    int64_t q = 0;
+    for (int64_t t = M.rowptr[r]; t < M.rowptr[r + 1]; ++t, ++q) {
+      col[q * M.nrows + r] = M.col[t];
+      val[q * M.nrows + r] = (R)M.val[t];
+    }
+    for (; q < k; ++q) col[q * M.nrows + r] = 0;  // padding: value 0 at a column that exists
+  }
+  E.col = h->upload(col);
+  E.val = h->upload(val);
+  return E;
+}
+
 template <class R>
 void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, const std::vector<Csr>& Pr,
                      const std::vector<Csr>& Rt, const std::vector<double>& coarse_inv,
@@ -142,9 +166,7 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   for (int l = 0; l < h->nlev; ++l) {
     GmgLevel& G = P.lev[l];
     G.n = A[l].nrows;
-    G.rowptr = h->upload(to_i32(A[l].rowptr));
-    G.col = h->upload(A[l].col);
-    G.val = h->upload(cast_vec<R>(A[l].val));
+    G.A = to_ell<R>(h, A[l]);
     std::vector<double> dl1(A[l].nrows, 0.0);
     for (int64_t r = 0; r < A[l].nrows; ++r) {
       double sabs = 0;
@@ -153,12 +175,8 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
     }
     G.dl1inv = h->upload(cast_vec<R>(dl1));
     if (l > 0) {
-      G.prow = h->upload(to_i32(Pr[l].rowptr));
-      G.pcol = h->upload(Pr[l].col);
-      G.pval = h->upload(cast_vec<R>(Pr[l].val));
-      G.rrow = h->upload(to_i32(Rt[l].rowptr));
-      G.rcol = h->upload(Rt[l].col);
-      G.rval = h->upload(cast_vec<R>(Rt[l].val));
+      G.P = to_ell<R>(h, Pr[l]);
+      G.Rt = to_ell<R>(h, Rt[l]);
     }
     P.pb[l] = h->dalloc<R>(G.n);
     P.px[l] = h->dalloc<R>(G.n);
@@ -175,9 +193,6 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   P.coarse_tmp = nullptr;
   P.err = h->dalloc<int>(1);
   cuda_check(cudaMemset(P.err, 0, sizeof(int)), "memset");
-  P.gbar = h->dalloc<unsigned>(2);
-  cuda_check(cudaMemset(P.gbar, 0, 2 * sizeof(unsigned)), "memset");
-  P.fused_blocks = gmg_fused_blocks<R>();
   const char* dbg = std::getenv("MCS_DEBUG_CHECKS");
   if (dbg && dbg[0] == '1') {
     P.debug = true;
@@ -909,8 +924,6 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       cuda_check(cudaStreamSynchronize(st), "sync");
       if (herr) {
         cuda_check(cudaMemsetAsync(errp, 0, sizeof(int), st), "memset");
-        unsigned* gbar = h->opt.precision == MCS_MIXED ? h->pf.gbar : h->pd.gbar;  // barrier left mid-way
-        cuda_check(cudaMemsetAsync(gbar, 0, 2 * sizeof(unsigned), st), "memset");
         status = MCS_ERR_TIMEOUT;
         if (info) info->status = status;
       }

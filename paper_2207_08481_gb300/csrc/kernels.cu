@@ -930,22 +930,23 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
   }
   if (WITH_P) {
     __syncthreads();
+    // in the precision of the preconditioner: the B table as R (float: its leading part)
+    const R* Bt = sizeof(R) == 4 ? (const R*)(const void*)t.Bp_hi : (const R*)(const void*)t.Bp;
     for (int q = tid; q < nvalid * np_; q += blockDim.x) {
       const int e = q / np_, j = q - e * np_;
       const int64_t T = T0 + e;
-      double v = 0;  // sum_i Bhat[j][i] sign_i a_i over the velocity dofs
-      for (int i = 0; i < nu_; ++i) {
-        double ai;
-        if (i < nfd) {
-          const int f = i / s.nF;
-          ai = (double)m.signs[T * (d + 1) + f] * (double)xc[e * nc + f * mF + (i - f * s.nF)];
-        } else {
-          ai = (double)xo[e * no + i - nfd];
-        }
-        v += t.Bp[j * nu_ + i] * ai;
+      R v = 0;  // sum_i Bhat[j][i] sign_i a_i over the velocity dofs
+      const R* Bj = Bt + j * nu_;
+      for (int f = 0; f <= d; ++f) {
+        const R sg = (R)m.signs[T * (d + 1) + f];
+        const R* xf = xc + e * nc + f * mF;
+        R vf = 0;
+        for (int i = 0; i < s.nF; ++i) vf += Bj[f * s.nF + i] * xf[i];
+        v += sg * vf;
       }
+      for (int o = 0; o < no; ++o) v += Bj[nfd + o] * xo[e * no + o];
       const int64_t gp = L.off_p + T * np_ + j;
-      zp[gp] = (R)(nu / m.adet[T] * ((double)r[gp] + v));
+      zp[gp] = (R)(nu / m.adet[T]) * (r[gp] + v);
     }
   }
 }
@@ -1136,23 +1137,29 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
   cp_async_wait_all();
 }
 
-// xbar = E^d^T rr  (gather per P1 dof over incident facets)
+// xbar = E^d^T rr: one warp per P1 vertex; the lanes take the (incident facet, mode) pairs and the
+// d sums are combined by a fixed butterfly, so the result does not depend on scheduling.
 template <class R>
 __global__ void k_embed_T(ElemSizes s, Layout L, const R* Eb, const int32_t* vf_ptr, const int32_t* vf_idx,
                           int64_t nP1, const R* rr, R* xb, const int* stop) {
   if (stop && *stop) return;
-  const int d = s.d, mF = s.mF, dd = d * d;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nP1 * d;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    int64_t v = q / d;
-    int a = (int)(q % d);
-    R acc = 0;
-    for (int32_t e = vf_ptr[v]; e < vf_ptr[v + 1]; ++e) {
-      int32_t rk = vf_idx[2 * e], w = vf_idx[2 * e + 1];
-      const R* B = Eb + (int64_t)rk * mF * dd;
-      for (int t = 0; t < mF; ++t) acc += B[t * dd + w * d + a] * rr[coup_idx<R>(s, L, rk, t)];
+  const int d = s.d, mF = s.mF, dd = d * d, lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = w0; v < nP1; v += ws) {
+    const int32_t e0 = vf_ptr[v], ne = vf_ptr[v + 1] - e0;
+    R acc[3] = {0, 0, 0};
+    for (int q = lane; q < ne * mF; q += 32) {
+      const int ei = q / mF, t = q - ei * mF;
+      const int32_t rk = vf_idx[2 * (e0 + ei)], w = vf_idx[2 * (e0 + ei) + 1];
+      const R r = rr[coup_idx<R>(s, L, rk, t)];
+      const R* B = Eb + (int64_t)rk * mF * dd + t * dd + w * d;
+      for (int a = 0; a < d; ++a) acc[a] += B[a] * r;
     }
-    xb[q] = acc;
+    for (int a = 0; a < d; ++a) {
+      R x = acc[a];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) xb[v * d + a] = x;
+    }
   }
 }
 
@@ -1178,37 +1185,57 @@ __global__ void k_embed(ElemSizes s, Layout L, const R* Eb, const int32_t* fvr, 
 }
 
 // ---- GMG kernels ----
+// l1-Jacobi sweep xn = x + D (b - A x) (first: from x = 0, xn = D b).
 template <class R>
-__global__ void k_jacobi(int64_t n, const int32_t* rp, const int32_t* ci, const R* va, const R* dinv, const R* b,
-                         const R* x, R* xn, int first, const int* stop) {
+__global__ void k_jacobi(Ell A, const R* dinv, const R* b, const R* x, R* xn, int first, const int* stop) {
   if (stop && *stop) return;
+  const int64_t n = A.n;
+  const R* va = (const R*)A.val;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (first) {
       xn[i] = dinv[i] * b[i];
       continue;
     }
     R ax = 0;
-    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) ax += va[e] * x[ci[e]];
+    for (int k = 0; k < A.k; ++k) ax += va[k * n + i] * x[A.col[k * n + i]];
     xn[i] = x[i] + dinv[i] * (b[i] - ax);
   }
 }
+// Two l1-Jacobi sweeps from x = 0 in one pass: x1 = D b, x2 = x1 + D (b - A x1).
 template <class R>
-__global__ void k_residual_csr(int64_t n, const int32_t* rp, const int32_t* ci, const R* va, const R* b, const R* x,
-                               R* r, const int* stop) {
+__global__ void k_jacobi2_from_b(Ell A, const R* dinv, const R* b, R* xn, const int* stop) {
   if (stop && *stop) return;
+  const int64_t n = A.n;
+  const R* va = (const R*)A.val;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     R ax = 0;
-    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) ax += va[e] * x[ci[e]];
-    r[i] = b[i] - ax;
+    for (int k = 0; k < A.k; ++k) {
+      const int32_t j = A.col[k * n + i];
+      ax += va[k * n + i] * (dinv[j] * b[j]);
+    }
+    xn[i] = dinv[i] * b[i] + dinv[i] * (b[i] - ax);
   }
 }
 template <class R>
-__global__ void k_spmv_csr(int64_t n, const int32_t* rp, const int32_t* ci, const R* va, const R* x, R* y, int add,
-                           const int* stop) {
+__global__ void k_residual_ell(Ell A, const R* b, const R* x, R* r, const int* stop) {
   if (stop && *stop) return;
+  const int64_t n = A.n;
+  const R* va = (const R*)A.val;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    R ax = 0;
+    for (int k = 0; k < A.k; ++k) ax += va[k * n + i] * x[A.col[k * n + i]];
+    r[i] = b[i] - ax;
+  }
+}
+// y = M x (add: y += M x)
+template <class R>
+__global__ void k_spmv_ell(Ell M, const R* x, R* y, int add, const int* stop) {
+  if (stop && *stop) return;
+  const int64_t n = M.n;
+  const R* va = (const R*)M.val;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     R v = 0;
-    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) v += va[e] * x[ci[e]];
+    for (int k = 0; k < M.k; ++k) v += va[k * n + i] * x[M.col[k * n + i]];
     y[i] = add ? y[i] + v : v;
   }
 }
@@ -1240,25 +1267,33 @@ static void vcycle(PrecData<R>& P, int l, const int* stop, cudaStream_t st) {
     return;
   }
 
-  const R* va = (const R*)G.val;
   const R* di = (const R*)G.dl1inv;
+  const GmgLevel& Gc = P.lev[l - 1];
   R* x = P.px[l];
   R* xt = P.ptmp[l];
-  for (int sw = 0; sw < P.gmg_smooth; ++sw) {
-    k_jacobi<R><<<grid(G.n), bs, 0, st>>>(G.n, G.rowptr, G.col, va, di, P.pb[l], x, xt, sw == 0, stop);
+  // pre-smoothing from x = 0: two sweeps per pass, a last single sweep if their number is odd
+  int sw = 0;
+  if (P.gmg_smooth >= 2) {
+    k_jacobi2_from_b<R><<<grid(G.n), bs, 0, st>>>(G.A, di, P.pb[l], x, stop);
+    note_launch();
+    sw = 2;
+  }
+  for (; sw < P.gmg_smooth; ++sw) {
+    k_jacobi<R><<<grid(G.n), bs, 0, st>>>(G.A, di, P.pb[l], x, xt, sw == 0, stop);
     note_launch();
     R* tmp = x; x = xt; xt = tmp;
   }
-  k_residual_csr<R><<<grid(G.n), bs, 0, st>>>(G.n, G.rowptr, G.col, va, P.pb[l], x, P.pr[l], stop);
+  // b_{l-1} = R (b - A x)
+  k_residual_ell<R><<<grid(G.n), bs, 0, st>>>(G.A, P.pb[l], x, P.pr[l], stop);
   note_launch();
-  const GmgLevel& Gc = P.lev[l - 1];
-  k_spmv_csr<R><<<grid(Gc.n), bs, 0, st>>>(Gc.n, G.rrow, G.rcol, (const R*)G.rval, P.pr[l], P.pb[l - 1], 0, stop);
+  k_spmv_ell<R><<<grid(Gc.n), bs, 0, st>>>(G.Rt, P.pr[l], P.pb[l - 1], 0, stop);
   note_launch();
   vcycle(P, l - 1, stop, st);
-  k_spmv_csr<R><<<grid(G.n), bs, 0, st>>>(G.n, G.prow, G.pcol, (const R*)G.pval, P.px[l - 1], x, 1, stop);
+  // x += P x_{l-1}, post-smoothing
+  k_spmv_ell<R><<<grid(G.n), bs, 0, st>>>(G.P, P.px[l - 1], x, 1, stop);
   note_launch();
-  for (int sw = 0; sw < P.gmg_smooth; ++sw) {
-    k_jacobi<R><<<grid(G.n), bs, 0, st>>>(G.n, G.rowptr, G.col, va, di, P.pb[l], x, xt, 0, stop);
+  for (int s2 = 0; s2 < P.gmg_smooth; ++s2) {
+    k_jacobi<R><<<grid(G.n), bs, 0, st>>>(G.A, di, P.pb[l], x, xt, 0, stop);
     note_launch();
     R* tmp = x; x = xt; xt = tmp;
   }
@@ -1395,258 +1430,6 @@ static void elem_epilogue(const ElemSizes& s, const DevTables& t, const DevMesh&
   });
 }
 
-// ---------------------------------------------------------------- fused V-cycle
-// E^d^T, one V-cycle and E^d in one cooperative launch (all blocks co-resident); the phases are
-// separated by a software grid barrier whose wait is bounded.  Vectors written by other blocks in
-// an earlier phase are read with ld.global.cg (L2), never through a possibly stale L1 line.
-template <class R>
-struct GmgArgs {
-  int nlev, smooth, d, mF;
-  int64_t nP1, nint;
-  Layout L;
-  const R* Eb;
-  const int32_t *vf_ptr, *vf_idx, *fvr;
-  const R* rr;   // facet residual (preconditioner layout)
-  R* x;          // facet iterate, += E xbar
-  const double* coarse_inv;
-  int64_t n[12];
-  const int32_t *rowptr[12], *col[12], *prow[12], *pcol[12], *rrow[12], *rcol[12];
-  const R *val[12], *dl1[12], *pval[12], *rval[12];
-  R *pb[12], *px[12], *pr[12], *pt[12];
-};
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-template <class R>
-__device__ __forceinline__ R ldcg(const R* p) { return __ldcg(p); }
-
-// Barrier k of this launch: returns false if the wait gave up (the error flag is then set).
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned k, int* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();
-    atomicAdd(bar, 1u);
-    const unsigned target = (k + 1) * gridDim.x;
-    const long long t0 = clock64();
-    while (ld_acquire_u32(bar) < target) {
-      if (clock64() - t0 > (1ll << 32)) {  // about 2 s at 2 GHz
-        atomicExch(err, 3);
-        ok = 0;
-        break;
-      }
-      __nanosleep(32);
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-template <class R>
-__device__ __forceinline__ void csr_jacobi(const GmgArgs<R>& a, int l, const R* x, R* xn, bool first, int64_t t0,
-                                           int64_t ts) {
-  const int64_t n = a.n[l];
-  const int32_t *rp = a.rowptr[l], *ci = a.col[l];
-  const R *va = a.val[l], *di = a.dl1[l], *b = a.pb[l];
-  for (int64_t i = t0; i < n; i += ts) {
-    if (first) {
-      xn[i] = di[i] * ldcg(b + i);
-      continue;
-    }
-    R ax = 0;
-    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) ax += va[e] * ldcg(x + ci[e]);
-    xn[i] = ldcg(x + i) + di[i] * (ldcg(b + i) - ax);
-  }
-}
-
-template <class R>
-__global__ void __launch_bounds__(512) k_gmg_fused(GmgArgs<R> a, unsigned* bar, int* err, const int* stop) {
-  if (stop && *stop) return;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, ts = (int64_t)gridDim.x * blockDim.x;
-  const int d = a.d, mF = a.mF, dd = d * d, top = a.nlev - 1;
-  unsigned k = 0;
-  bool ok = true;
-  // xbar = E^T rr (per P1 dof, over incident facets)
-  for (int64_t q = t0; q < a.nP1 * d; q += ts) {
-    const int64_t v = q / d;
-    const int c = (int)(q - v * d);
-    R acc = 0;
-    for (int32_t e = a.vf_ptr[v]; e < a.vf_ptr[v + 1]; ++e) {
-      const int32_t rk = a.vf_idx[2 * e], w = a.vf_idx[2 * e + 1];
-      const R* B = a.Eb + (int64_t)rk * mF * dd;
-      for (int t = 0; t < mF; ++t) acc += B[t * dd + w * d + c] * a.rr[(int64_t)rk * a.L.fstride + t];
-    }
-    a.pb[top][q] = acc;
-  }
-  ok = grid_barrier(bar, k++, err);
-  // down: pre-smoothing, residual, restriction
-  for (int l = top; l >= 1 && ok; --l) {
-    R* x = a.px[l];
-    R* xt = a.pt[l];
-    for (int sw = 0; sw < a.smooth && ok; ++sw) {
-      csr_jacobi(a, l, x, xt, sw == 0, t0, ts);
-      R* tmp = x; x = xt; xt = tmp;
-      ok = grid_barrier(bar, k++, err);
-    }
-    if (!ok) break;
-    {
-      const int64_t n = a.n[l];
-      const int32_t *rp = a.rowptr[l], *ci = a.col[l];
-      const R* va = a.val[l];
-      for (int64_t i = t0; i < n; i += ts) {
-        R ax = 0;
-        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) ax += va[e] * ldcg(x + ci[e]);
-        a.pr[l][i] = ldcg(a.pb[l] + i) - ax;
-      }
-    }
-    ok = grid_barrier(bar, k++, err);
-    if (!ok) break;
-    {
-      const int64_t nc = a.n[l - 1];
-      const int32_t *rp = a.rrow[l], *ci = a.rcol[l];
-      const R* va = a.rval[l];
-      for (int64_t i = t0; i < nc; i += ts) {
-        R v = 0;
-        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) v += va[e] * ldcg(a.pr[l] + ci[e]);
-        a.pb[l - 1][i] = v;
-      }
-    }
-    ok = grid_barrier(bar, k++, err);
-  }
-  // coarsest: dense FP64 inverse, one warp per row
-  if (ok) {
-    const int64_t n = a.n[0];
-    const int lane = threadIdx.x & 31;
-    for (int64_t i = t0 >> 5; i < n; i += ts >> 5) {
-      double v = 0;
-      for (int64_t j = lane; j < n; j += 32) v += a.coarse_inv[i * n + j] * (double)ldcg(a.pb[0] + j);
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) a.px[0][i] = (R)v;
-    }
-    ok = grid_barrier(bar, k++, err);
-  }
-  // up: prolongation, post-smoothing (the pre-smoothed iterate is in px after an even number of
-  // sweeps, in pt after an odd one)
-  for (int l = 1; l <= top && ok; ++l) {
-    R* x = (a.smooth & 1) ? a.pt[l] : a.px[l];
-    R* xt = (a.smooth & 1) ? a.px[l] : a.pt[l];
-    {
-      const int64_t n = a.n[l];
-      const int32_t *rp = a.prow[l], *ci = a.pcol[l];
-      const R* va = a.pval[l];
-      for (int64_t i = t0; i < n; i += ts) {
-        R v = 0;
-        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) v += va[e] * ldcg(a.px[l - 1] + ci[e]);
-        x[i] = ldcg(x + i) + v;
-      }
-    }
-    ok = grid_barrier(bar, k++, err);
-    for (int sw = 0; sw < a.smooth && ok; ++sw) {
-      csr_jacobi(a, l, x, xt, false, t0, ts);
-      R* tmp = x; x = xt; xt = tmp;
-      ok = grid_barrier(bar, k++, err);
-    }
-    if (ok && x != a.px[l])  // odd number of sweeps: the result sits in the scratch vector
-      for (int64_t i = t0; i < a.n[l]; i += ts) a.px[l][i] = ldcg(x + i);
-    if (ok && x != a.px[l]) ok = grid_barrier(bar, k++, err);
-  }
-  // x_F += E xbar
-  if (ok) {
-    for (int64_t q = t0; q < a.nint * mF; q += ts) {
-      const int64_t rk = q / mF;
-      const int t = (int)(q - rk * mF);
-      const R* B = a.Eb + rk * mF * dd + t * dd;
-      R v = 0;
-      for (int w = 0; w < d; ++w) {
-        const int32_t vr = a.fvr[rk * d + w];
-        if (vr < 0) continue;
-        for (int c = 0; c < d; ++c) v += B[w * d + c] * ldcg(a.px[top] + (int64_t)vr * d + c);
-      }
-      a.x[rk * a.L.fstride + t] += v;
-    }
-  }
-  // the last block to finish resets the barrier for the next launch (no block waits any more)
-  __syncthreads();
-  if (threadIdx.x == 0 && ok) {
-    __threadfence();
-    if (atomicAdd(bar + 1, 1u) == gridDim.x - 1) {
-      bar[0] = 0;
-      bar[1] = 0;
-      __threadfence();
-    }
-  }
-}
-
-template <class R>
-static cudaError_t launch_gmg_fused(const ElemSizes& s, const Layout& L, PrecData<R>& P, R* x, const int* stop,
-                                    cudaStream_t st) {
-  GmgArgs<R> a{};
-  a.nlev = P.nlev;
-  a.smooth = P.gmg_smooth;
-  a.d = s.d;
-  a.mF = s.mF;
-  a.nP1 = P.nP1;
-  a.nint = L.nint;
-  a.L = L;
-  a.Eb = P.Eb;
-  a.vf_ptr = P.vf_ptr;
-  a.vf_idx = P.vf_idx;
-  a.fvr = P.fvr;
-  a.rr = P.rr;
-  a.x = x;
-  a.coarse_inv = P.coarse_inv;
-  for (int l = 0; l < P.nlev; ++l) {
-    const GmgLevel& G = P.lev[l];
-    a.n[l] = G.n;
-    a.rowptr[l] = G.rowptr;
-    a.col[l] = G.col;
-    a.val[l] = (const R*)G.val;
-    a.dl1[l] = (const R*)G.dl1inv;
-    a.prow[l] = G.prow;
-    a.pcol[l] = G.pcol;
-    a.pval[l] = (const R*)G.pval;
-    a.rrow[l] = G.rrow;
-    a.rcol[l] = G.rcol;
-    a.rval[l] = (const R*)G.rval;
-    a.pb[l] = P.pb[l];
-    a.px[l] = P.px[l];
-    a.pr[l] = P.pr[l];
-    a.pt[l] = P.ptmp[l];
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)P.fused_blocks);
-  cfg.blockDim = dim3(512);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_gmg_fused<R>, a, P.gbar, P.err, stop);
-  note_launch();
-  return e;
-}
-
-// Blocks of the fused V-cycle: one per SM when a 512-thread block fits (cooperative launch), else 0.
-template <class R>
-int gmg_fused_blocks() {
-  int dev = 0, occ = 0, coop = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmg_fused<R>, 512, 0) != cudaSuccess || occ < 1) return 0;
-  return sm_count();
-}
-template int gmg_fused_blocks<float>();
-template int gmg_fused_blocks<double>();
-
 // Multiplicative ASP on A^d (Sec. 5.2 / 6.1): x_c from the right-hand side b_c - tb_c.
 template <class R>
 static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* b, const R* tb,
@@ -1662,19 +1445,19 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   facet_step<R>(s, m, L, P, b, tb, x, P.rr, 0, L.nint, false, stop, st);
   const int top = P.nlev - 1;
   prof_begin(PROF_GMG, st);
-  if (P.fused_blocks > 0 && P.lev[0].n > 0) {
-    launch_gmg_fused<R>(s, L, P, x, stop, st);
-    dbg_sync(P, st, "k_gmg_fused");
-  } else {
-    k_embed_T<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.vf_ptr, P.vf_idx, P.nP1, P.rr, P.pb[top], stop);
-    note_launch();
-    dbg_sync(P, st, "k_embed_T");
-    vcycle<R>(P, top, stop, st);
-    dbg_sync(P, st, "V-cycle");
-    k_embed<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.fvr, L.nint, P.px[top], x, stop);
-    note_launch();
-    dbg_sync(P, st, "k_embed");
+  {
+    int64_t ge = (P.nP1 * 32 + bs - 1) / bs;  // a warp per P1 vertex
+    if (ge > (int64_t)sm_count() * 32) ge = (int64_t)sm_count() * 32;
+    if (ge < 1) ge = 1;
+    k_embed_T<R><<<(unsigned)ge, bs, 0, st>>>(s, L, P.Eb, P.vf_ptr, P.vf_idx, P.nP1, P.rr, P.pb[top], stop);
   }
+  note_launch();
+  dbg_sync(P, st, "k_embed_T");
+  vcycle<R>(P, top, stop, st);
+  dbg_sync(P, st, "V-cycle");
+  k_embed<R><<<g, bs, 0, st>>>(s, L, P.Eb, P.fvr, L.nint, P.px[top], x, stop);
+  note_launch();
+  dbg_sync(P, st, "k_embed");
   prof_end(PROF_GMG, 0.0, 0.0, st);
   for (int sw = 0; sw < P.smooth; ++sw)
     for (int c = P.ncol - 1; c >= 0; --c)

@@ -171,20 +171,20 @@ cudaError_t launch_load_points(const ElemSizes& s, const DevTables& t, const Dev
                                cudaStream_t st);
 
 // ---------------------------------------------------------------- preconditioner pieces (precision R)
+// Sparse matrices of the multigrid in ELL form, column-major: entry k of row i at k*n + i, so the
+// threads of consecutive rows read consecutive addresses; padding entries have value 0 and column 0.
+struct Ell {
+  int64_t n = 0;
+  int k = 0;
+  const int32_t* col = nullptr;  // [k][n]
+  const void* val = nullptr;     // R [k][n]
+};
 struct GmgLevel {
   int64_t n;                 // dofs
-  const int32_t* rowptr;     // CSR of Abar
-  const int32_t* col;
-  const void* val;           // R
+  Ell A;                     // Abar on this level
   const void* dl1inv;        // R, 1 / sum_j |A_ij|
-  // prolongation to this level from the coarser one (fine rows, <= 2 entries each)
-  const int32_t* prow;       // [n+1]
-  const int32_t* pcol;
-  const void* pval;
-  // restriction (transpose)
-  const int32_t* rrow;       // [n_coarse+1]
-  const int32_t* rcol;
-  const void* rval;
+  Ell P;                     // prolongation to this level from the coarser one (fine rows)
+  Ell Rt;                    // restriction (coarse rows)
 };
 
 template <class R>
@@ -214,17 +214,9 @@ struct PrecData {
   // the host synchronises after every preconditioner launch and names a kernel that failed
   int* dbg = nullptr;
   bool debug = false;
-  // fused V-cycle: one cooperative launch for E^T, the whole V-cycle and E (grid barrier state:
-  // [0] arrivals of this launch, [1] blocks finished)
-  unsigned* gbar = nullptr;
-  int fused_blocks = 0;     // 0: separate launches per level
   R *pb[12], *px[12], *pr[12], *ptmp[12];  // GMG vectors per level
   double* coarse_tmp;  // [n0]
 };
-
-// blocks of the fused V-cycle launch on this device (0: not available)
-template <class R>
-int gmg_fused_blocks();
 
 template <class R>
 cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
