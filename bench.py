@@ -231,6 +231,9 @@ def run_gpu(args):
     value_fp64 = fp64_steps * world / (ms_fp64 / 1e3)
     hd.close()
 
+    # ---------------- several degrees in one condensation launch (3D, 16^3 x 6 tets, k = 2, 3, 4)
+    multi = _multi_degree(args, torch, mcs) if (rank == 0 and not args.no_multi) else None
+
     # ---------------- serving: Poisson trace of mixed requests through the continuous-batching loop
     serving = None
     if args.serve_requests > 0:
@@ -280,10 +283,59 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "serving": serving,
+        "multi_degree": multi,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _multi_degree(args, torch, mcs):
+    """Mixed-degree batch: one persistent condensation launch for three problems against one launch per
+    problem, then the three solves (random F = M_u c, seeded)."""
+    ks = (2, 3, 4)
+    hs = [mcs.Handle.structured(3, 16, k, 1.0, precision=mcs.MCS_MIXED) for k in ks]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_batch = timed(lambda: mcs.condense_batch(hs))
+    t_sep = timed(lambda: [h.condense() for h in hs])
+    mcs.condense_batch(hs)
+    solves = {}
+    for k, h in zip(ks, hs):
+        s = h.sizes
+        g = torch.Generator(device="cuda")
+        g.manual_seed(100 + k)
+        c = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
+        c[:s.off_h] = torch.randn(s.off_h, dtype=torch.float64, device="cuda", generator=g)
+        F = torch.zeros_like(c)
+        h.mass_velocity(c, F)
+        x = torch.zeros_like(F)
+        h.solve(F, x)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        x.zero_()
+        e0.record()
+        info = h.solve(F, x)
+        e1.record()
+        torch.cuda.synchronize()
+        solves[f"k={k}"] = {"ndof": int(s.ndof), "ms": round(e0.elapsed_time(e1), 2), "iterations": info.iterations,
+                            "rel_res": info.rel_res_precond}
+    for h in hs:
+        h.close()
+    return {"config": "3D unit cube, 16^3 cells x 6 = 24,576 tetrahedra each, k = 2, 3, 4, nu = 1, mixed form, "
+                      "random F = M_u c (c ~ N(0,1)); k = 1, 5, 6 of the six-problem batch are not supported",
+            "condense_batched_ms": round(t_batch, 2), "condense_separate_ms": round(t_sep, 2), "solves": solves}
 
 
 def _serving(args, rank, world, torch, dist):
@@ -379,6 +431,7 @@ def main():
                     help="requests of the serving trace (2000 = the full trace; 0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--no-multi", action="store_true", help="skip the mixed-degree batch")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -151,6 +151,14 @@ int mcs_export_pattern(const mcs_handle* h, int64_t* rowptr, int32_t* col);
  * A_oo^{-1} and the inverted facet blocks of the smoother in the preconditioner's
  * precision.  Asynchronous; idempotent. */
 int mcs_condense(mcs_handle* h);
+/* Static condensation of several problems in one persistent launch (elements of different meshes
+ * and degrees k interleaved over the blocks); the same arithmetic as mcs_condense per handle, so the
+ * results are identical.  handles: host array of count handles on the current device, all of the same
+ * precision.  Runs on the stream of handles[0]; it waits for the work already enqueued on the other
+ * handles' streams and their streams wait for it (events, no host synchronisation).  Takes a
+ * temporary workspace from the stream-ordered allocator (largest element workspace x 4 blocks per
+ * SM).  Errors: INVALID_ARG (NULL, count < 1, mixed precisions or devices), OOM, CUDA. */
+int mcs_condense_batch(mcs_handle* const* handles, int count);
 
 /* Copies the packed lower triangle of A_T (FP64, [count][n_A(n_A+1)/2], row-major
  * packing i(i+1)/2 + j, local order u_d | u_o | uhat, orientation signs applied) of

@@ -406,6 +406,70 @@ mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* 
 
 void mcs::set_last_error(const char* msg) { g_err = msg ? msg : "unknown error"; }
 
+namespace {
+template <class R>
+void condense_batch(mcs_handle* const* hs, int count) {
+  mcs_handle* h0 = hs[0];
+  cudaStream_t st = h0->stream;
+  std::vector<CondenseItem<R>> items(count);
+  int64_t total = 0, slot_bytes = 0;
+  for (int i = 0; i < count; ++i) {
+    mcs_handle* h = hs[i];
+    PrecData<R>& P = *reinterpret_cast<PrecData<R>*>(sizeof(R) == 4 ? (void*)&h->pf : (void*)&h->pd);
+    CondenseItem<R>& it = items[i];
+    it.s = h->es;
+    it.t = h->dt;
+    it.m = h->dm;
+    it.nu = h->nu;
+    it.K = h->K;
+    it.Fs = P.Fs;
+    it.G = const_cast<R*>(P.G);
+    it.Aoi = const_cast<R*>(P.Aoi);
+    it.first = total;
+    total += h->mesh.ne;
+    slot_bytes = std::max<int64_t>(slot_bytes, condense_slot_bytes(h->es));
+  }
+  // order against the other handles' streams
+  std::vector<cudaEvent_t> evs;
+  auto event_on = [&](cudaStream_t s) {
+    cudaEvent_t e;
+    cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    evs.push_back(e);
+    cuda_check(cudaEventRecord(e, s), "cudaEventRecord");
+    return e;
+  };
+  for (int i = 1; i < count; ++i)
+    if (hs[i]->stream != st) cuda_check(cudaStreamWaitEvent(st, event_on(hs[i]->stream), 0), "wait");
+  int nsm = 0;
+  cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->device), "attribute");
+  const int64_t blocks = std::min<int64_t>((int64_t)nsm * 4, std::max<int64_t>(total, 1));
+  const int64_t scratch_doubles = blocks * (slot_bytes / 8);
+  void* items_dev = nullptr;
+  double* scratch = nullptr;
+  cuda_check(cudaMallocAsync(&items_dev, sizeof(CondenseItem<R>) * count, st), "cudaMallocAsync");
+  cudaError_t e = cudaMallocAsync((void**)&scratch, sizeof(double) * scratch_doubles, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(items_dev, st);
+    throw McsError(MCS_ERR_OOM, "batched condensation workspace");
+  }
+  cuda_check(cudaMemcpyAsync(items_dev, items.data(), sizeof(CondenseItem<R>) * count, cudaMemcpyHostToDevice, st),
+             "copy items");
+  e = launch_condense_batch<R>((const CondenseItem<R>*)items_dev, items.data(), count, scratch, scratch_doubles, st);
+  cudaFreeAsync(scratch, st);
+  cudaFreeAsync(items_dev, st);
+  cuda_check(e, "condense batch");
+  // the items were copied from pageable memory before the call returned; facet blocks per problem
+  for (int i = 0; i < count; ++i) {
+    PrecData<R>& P = *reinterpret_cast<PrecData<R>*>(sizeof(R) == 4 ? (void*)&hs[i]->pf : (void*)&hs[i]->pd);
+    cuda_check(launch_facet_blocks<R>(hs[i]->es, hs[i]->dm, P.Fs, st), "facet blocks");
+    hs[i]->condensed = true;
+  }
+  for (int i = 1; i < count; ++i)
+    if (hs[i]->stream != st) cuda_check(cudaStreamWaitEvent(hs[i]->stream, event_on(st), 0), "wait");
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+}
+}  // namespace
+
 extern "C" {
 
 int mcs_version(void) { return 100; }
@@ -582,6 +646,21 @@ int mcs_export_pattern(const mcs_handle* h, int64_t* rowptr, int32_t* col) {
       rowptr[r + 1] = rowptr[r] + (int64_t)v.size();
       if (col) std::copy(v.begin(), v.end(), col + rowptr[r]);
     }
+    return MCS_OK;
+  });
+}
+
+int mcs_condense_batch(mcs_handle* const* handles, int count) {
+  return guarded([&]() -> int {
+    if (!handles || count < 1) throw McsError(MCS_ERR_INVALID_ARG, "NULL handles or count < 1");
+    for (int i = 0; i < count; ++i) {
+      if (!handles[i]) throw McsError(MCS_ERR_INVALID_ARG, "NULL handle");
+      if (handles[i]->opt.precision != handles[0]->opt.precision)
+        throw McsError(MCS_ERR_INVALID_ARG, "handles of different precisions");
+      if (handles[i]->device != handles[0]->device) throw McsError(MCS_ERR_INVALID_ARG, "handles on different devices");
+    }
+    if (handles[0]->opt.precision == MCS_MIXED) condense_batch<float>(handles, count);
+    else condense_batch<double>(handles, count);
     return MCS_OK;
   });
 }

@@ -1,4 +1,5 @@
 // Device kernels of libmcs (sm_103a).  See kernels.h for the roles.
+#include <algorithm>
 #include <atomic>
 #include <cuda_runtime.h>
 
@@ -57,14 +58,11 @@ struct BlockSync {
   __device__ void operator()() const { __syncthreads(); }
 };
 
-// One thread block per element (grid-stride).  Workspace in dynamic shared memory when
-// it fits, else in a global scratch slot per resident block.
-template <class R, bool SMEM>
-__global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, KOp K, R* Fs,
-                                                  R* G, R* Aoi, double* gscratch, int64_t slot_doubles) {
-  extern __shared__ double smem[];
+// Condensation of element T by the whole block (a1-a4 except D_F), workspace at base.
+template <class R>
+__device__ __forceinline__ void condense_one(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu,
+                                             const KOp& K, R* Fs, R* G, R* Aoi, double* base, int64_t T) {
   const int lane = threadIdx.x, nl = blockDim.x;
-  double* base = SMEM ? smem : gscratch + (int64_t)blockIdx.x * slot_doubles;
   ElemWork w = elem_work_carve(s, base);
   double* bw = base + elem_work_doubles(s);                // bubble work
   double* Xs = bw + s.n_bub * s.n_bub + s.n_bub * s.n_c;   // (d+1)*d coords
@@ -74,46 +72,70 @@ __global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevM
   double* Ait = Gt + s.n_bub * s.n_c;
   ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat};
   const int d = s.d;
-  for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) {
-    if (lane < (d + 1) * d) {
-      int v = lane / d, a = lane % d;
-      Xs[lane] = m.coords[(int64_t)m.elems[T * (d + 1) + v] * d + a];
-    }
-    if (lane <= d) sg[lane] = m.signs[T * (d + 1) + lane];
-    __syncthreads();
-    condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
-    const int nA = s.n_A;
-    if (K.AT) {  // full A_T (FP64, symmetric: row-major = column-major)
-      double* out = K.AT + T * (int64_t)nA * nA;
-      for (int q = lane; q < nA * nA; q += nl) out[q] = w.A[q];
-    }
-    if (K.Ahi) {  // packed lower triangle as float pairs, hi = fl(a), lo = fl(a - hi)
-      const int pp = packed_pad(s);
-      float* oh = K.Ahi + T * (int64_t)pp;
-      float* ol = K.Alo + T * (int64_t)pp;
-      for (int i = lane; i < nA; i += nl)
-        for (int j = 0; j <= i; ++j) {
-          const double a = w.A[i * nA + j];
-          const float hi = (float)a;
-          oh[i * (i + 1) / 2 + j] = hi;
-          ol[i * (i + 1) / 2 + j] = (float)(a - (double)hi);
-        }
-    }
-    __syncthreads();
-    bubble_condense(s, w.A, bw, Adt, Gt, Ait, lane, nl, BlockSync());
-    const int nc = s.n_c, no = s.n_bub, mF = s.mF, fss = fs_stride(s), slab = slab_pad(s);
-    // slabs of the interior facets into the facet stream (boundary facets carry no dofs)
-    for (int q = lane; q < nc * nc; q += nl) {   // q = (f*nc + c)*mF + tt: contiguous slab writes
-      const int f = q / (nc * mF), rem = q - f * nc * mF, c = rem / mF, tt = rem - c * mF;
-      const int i = f * mF + tt;                 // row of A^d_T
-      const int32_t rk = m.elem_rank[T * (d + 1) + f];
-      if (rk < 0) continue;
-      const int side = m.fel[2 * (int64_t)rk] == (int32_t)T ? 0 : 1;
-      Fs[(int64_t)m.fpos[rk] * fss + side * slab + c * mF + tt] = (R)Adt[i * nc + c];
-    }
-    for (int q = lane; q < no * nc; q += nl) G[T * g_stride(s) + q] = (R)Gt[q];
-    for (int q = lane; q < no * no; q += nl) Aoi[T * a_stride(s) + q] = (R)Ait[q];
-    __syncthreads();
+  if (lane < (d + 1) * d) {
+    int v = lane / d, a = lane % d;
+    Xs[lane] = m.coords[(int64_t)m.elems[T * (d + 1) + v] * d + a];
+  }
+  if (lane <= d) sg[lane] = m.signs[T * (d + 1) + lane];
+  __syncthreads();
+  condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
+  const int nA = s.n_A;
+  if (K.AT) {  // full A_T (FP64, symmetric: row-major = column-major)
+    double* out = K.AT + T * (int64_t)nA * nA;
+    for (int q = lane; q < nA * nA; q += nl) out[q] = w.A[q];
+  }
+  if (K.Ahi) {  // packed lower triangle as float pairs, hi = fl(a), lo = fl(a - hi)
+    const int pp = packed_pad(s);
+    float* oh = K.Ahi + T * (int64_t)pp;
+    float* ol = K.Alo + T * (int64_t)pp;
+    for (int i = lane; i < nA; i += nl)
+      for (int j = 0; j <= i; ++j) {
+        const double a = w.A[i * nA + j];
+        const float hi = (float)a;
+        oh[i * (i + 1) / 2 + j] = hi;
+        ol[i * (i + 1) / 2 + j] = (float)(a - (double)hi);
+      }
+  }
+  __syncthreads();
+  bubble_condense(s, w.A, bw, Adt, Gt, Ait, lane, nl, BlockSync());
+  const int nc = s.n_c, no = s.n_bub, mF = s.mF, fss = fs_stride(s), slab = slab_pad(s);
+  // slabs of the interior facets into the facet stream (boundary facets carry no dofs)
+  for (int q = lane; q < nc * nc; q += nl) {   // q = (f*nc + c)*mF + tt: contiguous slab writes
+    const int f = q / (nc * mF), rem = q - f * nc * mF, c = rem / mF, tt = rem - c * mF;
+    const int i = f * mF + tt;                 // row of A^d_T
+    const int32_t rk = m.elem_rank[T * (d + 1) + f];
+    if (rk < 0) continue;
+    const int side = m.fel[2 * (int64_t)rk] == (int32_t)T ? 0 : 1;
+    Fs[(int64_t)m.fpos[rk] * fss + side * slab + c * mF + tt] = (R)Adt[i * nc + c];
+  }
+  for (int q = lane; q < no * nc; q += nl) G[T * g_stride(s) + q] = (R)Gt[q];
+  for (int q = lane; q < no * no; q += nl) Aoi[T * a_stride(s) + q] = (R)Ait[q];
+  __syncthreads();
+}
+
+// One thread block per element (grid-stride).  Workspace in dynamic shared memory when
+// it fits, else in a global scratch slot per resident block.
+template <class R, bool SMEM>
+__global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, KOp K, R* Fs,
+                                                  R* G, R* Aoi, double* gscratch, int64_t slot_doubles) {
+  extern __shared__ double smem[];
+  double* base = SMEM ? smem : gscratch + (int64_t)blockIdx.x * slot_doubles;
+  for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) condense_one<R>(s, t, m, nu, K, Fs, G, Aoi, base, T);
+}
+
+// Several problems (any d, k) in one persistent launch: the blocks walk the concatenated element
+// lists (problem p owns the global indices first[p] .. first[p+1]-1) with a grid stride, so costly
+// and cheap elements interleave.  Workspace: a global scratch slot per block, sized for the
+// largest element.
+template <class R>
+__global__ void __launch_bounds__(256) k_condense_batch(const CondenseItem<R>* __restrict__ items, int nitems,
+                                                        int64_t total, double* gscratch, int64_t slot_doubles) {
+  double* base = gscratch + (int64_t)blockIdx.x * slot_doubles;
+  int p = 0;
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    while (p + 1 < nitems && items[p + 1].first <= g) ++p;   // g increases: the problem index only grows
+    const CondenseItem<R>& it = items[p];
+    condense_one<R>(it.s, it.t, it.m, it.nu, it.K, it.Fs, it.G, it.Aoi, base, g - it.first);
   }
 }
 
@@ -168,6 +190,30 @@ cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMes
   }
   return cudaGetLastError();
 }
+
+template <class R>
+cudaError_t launch_condense_batch(const CondenseItem<R>* items_dev, const CondenseItem<R>* items_host, int nitems,
+                                  double* scratch, int64_t scratch_doubles, cudaStream_t st) {
+  int64_t slot = 0, total = 0;
+  for (int i = 0; i < nitems; ++i) {
+    slot = std::max<int64_t>(slot, condense_slot_doubles(items_host[i].s));
+    total += items_host[i].m.ne;
+  }
+  if (total == 0) return cudaSuccess;
+  int64_t blocks = scratch_doubles / slot;
+  if (blocks < 1) return cudaErrorMemoryAllocation;
+  if (blocks > total) blocks = total;
+  prof_begin(PROF_CONDENSE, st);
+  k_condense_batch<R><<<(unsigned)blocks, 256, 0, st>>>(items_dev, nitems, total, scratch, slot);
+  note_launch();
+  prof_end(PROF_CONDENSE, 0.0, 0.0, st);
+  return cudaGetLastError();
+}
+template cudaError_t launch_condense_batch<float>(const CondenseItem<float>*, const CondenseItem<float>*, int,
+                                                  double*, int64_t, cudaStream_t);
+template cudaError_t launch_condense_batch<double>(const CondenseItem<double>*, const CondenseItem<double>*, int,
+                                                   double*, int64_t, cudaStream_t);
+int64_t condense_slot_bytes(const ElemSizes& s) { return condense_slot_doubles(s) * 8; }
 
 int64_t condense_scratch_doubles(const ElemSizes& s, int nsm) {
   return condense_slot_doubles(s) * (int64_t)nsm * 8;

@@ -148,6 +148,27 @@ template <class S> __host__ __device__ inline int packed_pad(const S& s) { retur
 template <class R>
 cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K,
                             R* Fs, R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st);
+// One problem of a batched condensation: its sizes, tables, mesh and outputs; its elements take the
+// global indices first .. first + m.ne - 1 of the launch.
+template <class R>
+struct CondenseItem {
+  ElemSizes s;
+  DevTables t;
+  DevMesh m;
+  double nu;
+  KOp K;
+  R* Fs;
+  R* G;
+  R* Aoi;
+  int64_t first;
+};
+// Condensation of several problems (items in device memory, a host copy for the sizes) in one
+// persistent launch; scratch: global workspace of scratch_doubles.
+template <class R>
+cudaError_t launch_condense_batch(const CondenseItem<R>* items_dev, const CondenseItem<R>* items_host, int nitems,
+                                  double* scratch, int64_t scratch_doubles, cudaStream_t st);
+int64_t condense_slot_bytes(const ElemSizes& s);
+
 // Facet blocks D_F of A^d (sum of the two elements' slabs), inverted into the facet stream.
 template <class R>
 cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, R* Fs, cudaStream_t st);

@@ -27,6 +27,7 @@ MCS_MIXED = 1
 
 EXPORTED = ["mcs_version", "mcs_last_error", "mcs_default_options", "mcs_setup_structured", "mcs_setup_mesh",
             "mcs_sizes", "mcs_export_mesh", "mcs_export_dofmap", "mcs_export_pattern", "mcs_condense",
+            "mcs_condense_batch",
             "mcs_copy_element_matrices", "mcs_copy_schur", "mcs_load_points", "mcs_load_vector",
             "mcs_mass_velocity", "mcs_apply", "mcs_residual", "mcs_precond", "mcs_solve", "mcs_solve_host", "mcs_profile",
             "mcs_profile_read", "mcs_launch_count", "mcs_condense_noalloc", "mcs_destroy"]
@@ -98,6 +99,7 @@ def lib() -> ctypes.CDLL:
         L.mcs_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.c_int]
         L.mcs_condense_noalloc.argtypes = [vp, i64, i64, vp]
         L.mcs_launch_count.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.mcs_condense_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
         L.mcs_default_options.argtypes = [ctypes.POINTER(Options)]
         del i32p
         _lib = L
@@ -108,6 +110,12 @@ def _check(rc):
     if rc != MCS_OK:
         raise McsError(rc, lib().mcs_last_error().decode())
     return rc
+
+
+def condense_batch(handles) -> None:
+    """Condenses several handles (same precision, any mesh and k) in one persistent launch."""
+    arr = (ctypes.c_void_p * len(handles))(*[h._h.value for h in handles])
+    _check(lib().mcs_condense_batch(arr, len(handles)))
 
 
 def launch_count() -> int:
