@@ -86,6 +86,9 @@ typedef struct {
   int residual_dd;    /* residual of each refinement cycle in double-double: 1 always, 0 never (plain
                          FP64 K x, whose rounding floors the attainable residual near 1e-12 relative
                          for k = 4), -1 auto: when rtol < 1e-10 (-1) */
+  int asp;            /* auxiliary-space preconditioner for the condensed velocity block (Sec. 6.1):
+                         0 multiplicative (smoother, coarse correction, adjoint smoother; default),
+                         1 additive (facet-block Jacobi plus E^d C^{-1} E^d^T) */
 } mcs_options;
 
 typedef struct {

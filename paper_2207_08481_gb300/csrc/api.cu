@@ -64,6 +64,7 @@ void validate_options(const mcs_options& o) {
   if (o.gmg_smooth < 1 || o.gmg_smooth > 16) throw McsError(MCS_ERR_INVALID_ARG, "gmg_smooth");
   if (!(o.rtol > 0) || o.maxit < 1) throw McsError(MCS_ERR_INVALID_ARG, "rtol/maxit");
   if (o.residual_dd < -1 || o.residual_dd > 1) throw McsError(MCS_ERR_INVALID_ARG, "residual_dd");
+  if (o.asp < 0 || o.asp > 1) throw McsError(MCS_ERR_INVALID_ARG, "asp");
 }
 
 template <class R>
@@ -161,7 +162,7 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   P.ncol = h->ncol;
   P.smooth = h->opt.smooth_steps;
   P.gmg_smooth = h->opt.gmg_smooth;
-  P.multiplicative = 1;
+  P.multiplicative = h->opt.asp == 0 ? 1 : 0;
   P.nlev = h->nlev;
   for (int l = 0; l < h->nlev; ++l) {
     GmgLevel& G = P.lev[l];
@@ -489,6 +490,7 @@ int mcs_default_options(mcs_options* o) {
   o->max_refine = 8;
   o->inner_rtol = 1e-5;
   o->residual_dd = -1;
+  o->asp = 0;
   return MCS_OK;
 }
 

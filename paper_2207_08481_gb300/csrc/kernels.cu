@@ -1476,6 +1476,28 @@ static void elem_epilogue(const ElemSizes& s, const DevTables& t, const DevMesh&
   });
 }
 
+// Additive ASP, facet part: rr_F = b_F - tb_F and x_F = D_F^{-1} rr_F for every interior facet
+// (block Jacobi from x = 0); one thread per (facet record, mode).
+template <class R, class S>
+__global__ void k_facet_jacobi(S s, DevMesh m, Layout L, const R* __restrict__ Fs, const R* __restrict__ b,
+                               const R* __restrict__ tb, R* x, R* rr, int64_t n, const int* stop) {
+  if (stop && *stop) return;
+  const int mF = s.mF, fss = fs_stride(s), slab = slab_pad(s);
+  const int64_t fs = L.fstride;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * mF; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / mF;
+    const int t = (int)(q - i * mF);
+    const int64_t r = m.frec[i * 4].x;
+    const R* Di = Fs + i * fss + 2 * slab + t * mF;
+    const R* bf = b + r * fs;
+    const R* tf = tb + r * fs;
+    R v = 0;
+    for (int j = 0; j < mF; ++j) v += Di[j] * (bf[j] - tf[j]);
+    x[r * fs + t] = v;
+    rr[r * fs + t] = bf[t] - tf[t];
+  }
+}
+
 // Multiplicative ASP on A^d (Sec. 5.2 / 6.1): x_c from the right-hand side b_c - tb_c.
 template <class R>
 static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* b, const R* tb,
@@ -1485,10 +1507,18 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   cudaMemsetAsync(x, 0, sizeof(R) * L.n_dd, st);
   if (L.n_hat) cudaMemsetAsync(x + L.off_h, 0, sizeof(R) * L.n_hat, st);
   const int64_t* co = P.colour_off;
-  for (int sw = 0; sw < P.smooth; ++sw)
-    for (int c = 0; c < P.ncol; ++c)
-      facet_step<R>(s, m, L, P, b, tb, x, nullptr, co[c], co[c + 1] - co[c], true, stop, st);
-  facet_step<R>(s, m, L, P, b, tb, x, P.rr, 0, L.nint, false, stop, st);
+  if (P.multiplicative) {
+    for (int sw = 0; sw < P.smooth; ++sw)
+      for (int c = 0; c < P.ncol; ++c)
+        facet_step<R>(s, m, L, P, b, tb, x, nullptr, co[c], co[c + 1] - co[c], true, stop, st);
+    facet_step<R>(s, m, L, P, b, tb, x, P.rr, 0, L.nint, false, stop, st);
+  } else if (L.nint > 0) {  // additive: block Jacobi, and the coarse correction of the same residual
+    dispatch_sizes(s, [&](auto sz) {
+      k_facet_jacobi<R, decltype(sz)><<<g, bs, 0, st>>>(sz, m, L, P.Fs, b, tb, x, P.rr, L.nint, stop);
+      note_launch();
+    });
+    dbg_sync(P, st, "k_facet_jacobi");
+  }
   const int top = P.nlev - 1;
   prof_begin(PROF_GMG, st);
   {
@@ -1505,9 +1535,10 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   note_launch();
   dbg_sync(P, st, "k_embed");
   prof_end(PROF_GMG, 0.0, 0.0, st);
-  for (int sw = 0; sw < P.smooth; ++sw)
-    for (int c = P.ncol - 1; c >= 0; --c)
-      facet_step<R>(s, m, L, P, b, tb, x, nullptr, co[c], co[c + 1] - co[c], true, stop, st);
+  if (P.multiplicative)
+    for (int sw = 0; sw < P.smooth; ++sw)
+      for (int c = P.ncol - 1; c >= 0; --c)
+        facet_step<R>(s, m, L, P, b, tb, x, nullptr, co[c], co[c + 1] - co[c], true, stop, st);
 }
 
 // z = Khat^{-1} r (eq. mhatinvfactor, two applications of Ahat^{-1}, reading R3).

@@ -1,7 +1,8 @@
 """Runs one condense, one K apply and one preconditioner application on a workload, for
 kernel profilers (ncu) to capture.
 
-  python -m paper_2207_08481_gb300.profile_case [c2|c3] [mixed|fp64]
+  python -m paper_2207_08481_gb300.profile_case [c2|c3|c3s] [mixed|fp64]
+(c3s: the c3 element type on 16^3 x 6 cells, small enough for full ncu captures)
 """
 from __future__ import annotations
 
@@ -12,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-CASES = {"c2": dict(dim=2, N=256, k=3, nu=1e-2, levels=5), "c3": dict(dim=3, N=32, k=2, nu=1.0, levels=4)}
+CASES = {"c2": dict(dim=2, N=256, k=3, nu=1e-2, levels=5), "c3": dict(dim=3, N=32, k=2, nu=1.0, levels=4),
+         "c3s": dict(dim=3, N=16, k=2, nu=1.0, levels=3)}
 
 
 def main(argv):

@@ -314,3 +314,37 @@ def test_condense_batch_equals_per_problem(mcs, prec):
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-6
     for hh in ref + bat:
         hh.close()
+
+
+@pytest.mark.parametrize("d,N,k,nu,lev", [(2, 8, 2, 0.7, 2), (3, 2, 2, 1.0, 1), (2, 4, 3, 1.0, 2)])
+def test_precond_additive_matches_oracle(mcs, d, N, k, nu, lev):
+    """Additive ASP (facet-block Jacobi plus E^d C^{-1} E^d^T, Sec. 6.1) inside eq. (mhatinvfactor)."""
+    h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=lev, asp=1)
+    D, AT = _oracle(d, N, k, nu)
+    bp = precond.BlockPreconditioner(D, precond.ASP(D, AT, precond.GMG(d, N, lev, nu), multiplicative=False))
+    r = np.random.default_rng(6).standard_normal(D.ndof)
+    z = torch.zeros(D.ndof, dtype=torch.float64, device="cuda")
+    h.precond(torch.tensor(r, device="cuda"), z)
+    zo = bp.apply(r)
+    assert np.abs(z.cpu().numpy() - zo).max() < 1e-11 * np.abs(zo).max()
+    h.close()
+
+
+def test_solve_additive_c1(mcs):
+    """c1 with the additive ASP: same solution as the oracle's direct solve, more iterations than the
+    multiplicative ASP (as in the paper's comparison of the two)."""
+    d, N, k, nu = 2, 8, 2, 1.0
+    its = {}
+    for asp in (0, 1):
+        h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, rtol=1e-12, asp=asp)
+        F = _manufactured_rhs(h, d, nu)
+        x = torch.zeros_like(F)
+        info = h.solve(F, x)
+        its[asp] = info.iterations
+        D = system.discretize(mesh.structured(d, N), k, nu)
+        xo, _, _ = system.solve_full(D, F.cpu().numpy())
+        xo = system.mean_zero_pressure(D, xo)
+        xg = x.cpu().numpy()
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-10
+        h.close()
+    assert its[1] > its[0]

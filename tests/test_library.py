@@ -60,5 +60,8 @@ def test_invalid_arguments_are_reported_not_raised(lib):
     bad = lib.default_options(residual_dd=3)
     assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
     assert b"residual_dd" in L.mcs_last_error()
+    bad = lib.default_options(asp=2)
+    assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
+    assert lib.default_options().asp == 0
     assert L.mcs_apply(None, None, None) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_destroy(None) == lib.MCS_OK
