@@ -1366,6 +1366,119 @@ static void dbg_sync(const PrecData<R>& P, cudaStream_t st, const char* what) {
   }
 }
 
+// Warp-per-facet variant of the facet step (same arithmetic): every warp walks its own facets
+// (records f, f + W, ... of the colour range, W = number of warps) through a private two-stage
+// cp.async pipeline, so no block-wide barrier is needed.  Per facet: lanes (row, part) form the
+// 2 m_F slab-row dot products in L = 32 / (2 m_F) parts joined by shuffles, lanes t < m_F form r_F
+// and D_F^{-1} r_F (r broadcast by shuffles).  Stage layout per warp (16-byte aligned): stream
+// block [fs_stride], gathered segments [2][d+1][fs], b [fs], tb [fs].
+template <class S, class R>
+__host__ __device__ inline int warp_stage_elems(const S& s) {
+  const int fs = facet_stride(s, (int)sizeof(R));
+  return fs_stride(s) + 2 * (s.d + 1) * fs + 2 * fs;
+}
+template <class R, class S, bool UPDATE>
+__global__ void __launch_bounds__(256) k_facet_step_warp(S s, Layout L, const R* __restrict__ Fs,
+                                                         const R* __restrict__ b, const R* __restrict__ tb, R* x,
+                                                         R* rr, const int* __restrict__ rec, int64_t n,
+                                                         const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(16) unsigned char swr[];
+  const int mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), fss = fs_stride(s), nc = s.n_c;
+  const int fs = facet_stride(s, (int)sizeof(R));
+  const int se = warp_stage_elems<S, R>(s);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  R* wbase = reinterpret_cast<R*>(swr) + (size_t)wib * 2 * se;
+  constexpr int V = 16 / (int)sizeof(R);
+  const int cf = fss / V, cslab = 2 * slab / V, cx = fs / V;
+  const int rows = 2 * mF;
+  const int LP = rows <= 16 ? 2 : 1;            // lanes per row
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t f0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const uint64_t pol = l2_evict_first_policy();
+
+  auto issue = [&](int st, int64_t f, int myrec) {
+    R* Sb = wbase + st * se;
+    R* Xs = Sb + fss;
+    R* Bs = Xs + 2 * dp1 * fs;
+    R* Ts = Bs + fs;
+    const R* src = Fs + f * fss;
+    // record fields to every lane first (all 32 lanes shuffle, outside the lane-dependent loops)
+    int gseg[8];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) gseg[k2] = __shfl_sync(0xffffffffu, myrec, 5 + k2);
+    const int r = __shfl_sync(0xffffffffu, myrec, 0);
+    for (int q = lane; q < cf; q += 32) {
+      if (!UPDATE && q >= cslab) break;
+      cp_async16_hint(Sb + q * V, src + q * V, pol);
+    }
+    for (int q = lane; q < 2 * dp1 * cx; q += 32) {
+      const int seg = q / cx, ch = q - seg * cx;   // seg = side*dp1 + local facet
+      const int g = gseg[seg];
+      R* dst = Xs + seg * fs + ch * V;
+      if (g >= 0) cp_async16(dst, x + (int64_t)g * fs + ch * V);
+      else *reinterpret_cast<int4*>(dst) = make_int4(0, 0, 0, 0);
+    }
+    for (int q = lane; q < 2 * cx; q += 32) {
+      const int which = q / cx, ch = q - which * cx;
+      R* dst = (which ? Ts : Bs) + ch * V;
+      const R* sp = which ? tb : b;
+      if (sp) cp_async16(dst, sp + (int64_t)r * fs + ch * V);
+      else *reinterpret_cast<int4*>(dst) = make_int4(0, 0, 0, 0);
+    }
+  };
+  // the shuffles in issue() need every lane, so all lanes run the loop the same number of times
+  int st = 0;
+  int rec_next = (f0 < n && lane < 16) ? rec[f0 * 16 + lane] : -1;
+  if (f0 < n) issue(0, f0, rec_next);
+  cp_async_commit();
+  for (int64_t f = f0; f < n; f += W) {
+    const int rec_cur = rec_next;
+    const int64_t fn = f + W;
+    if (fn < n) {
+      rec_next = lane < 16 ? rec[fn * 16 + lane] : -1;
+      issue(st ^ 1, fn, rec_next);
+    }
+    cp_async_commit();
+    cp_async_wait_group<1>();
+    __syncwarp();
+    const R* Sb = wbase + st * se;
+    const R* Xs = Sb + fss;
+    const R* Bs = Xs + 2 * dp1 * fs;
+    const R* Ts = Bs + fs;
+    // slab-row dot products: lane -> (row = side*mF + t, part)
+    R y = 0;
+    const int row = lane / LP, part = lane - row * LP;
+    if (row < rows) {
+      const int side = row >= mF ? 1 : 0, t = row - side * mF;
+      const R* A = Sb + side * slab + t;
+      const R* xv = Xs + side * dp1 * fs;
+      for (int c = part; c < nc; c += LP) {
+        const int fl = c / mF, tt = c - fl * mF;
+        y += A[c * mF] * xv[fl * fs + tt];
+      }
+    }
+    if (LP == 2) y += __shfl_xor_sync(0xffffffffu, y, 1);
+    // r_F on lanes t < mF
+    const R y0 = __shfl_sync(0xffffffffu, y, (lane < mF ? lane : 0) * LP);
+    const R y1 = __shfl_sync(0xffffffffu, y, ((lane < mF ? lane : 0) + mF) * LP);
+    const R rv = lane < mF ? Bs[lane] - Ts[lane] - y0 - y1 : (R)0;
+    const int r = __shfl_sync(0xffffffffu, rec_cur, 0);
+    if (UPDATE) {
+      const int f0l = __shfl_sync(0xffffffffu, rec_cur, 3);   // local index of the facet in side 0
+      const R* Dr = Sb + 2 * slab + (lane < mF ? lane : 0) * mF;
+      R v = 0;
+      for (int j = 0; j < mF; ++j) v += Dr[j] * __shfl_sync(0xffffffffu, rv, j);
+      if (lane < mF && r >= 0) x[(int64_t)r * fs + lane] = Xs[f0l * fs + lane] + v;
+    } else {
+      if (lane < mF && r >= 0) rr[(int64_t)r * fs + lane] = rv;
+    }
+    __syncwarp();
+    st ^= 1;
+  }
+  cp_async_wait_all();
+}
+
 template <class R>
 static size_t facet_step_smem(const ElemSizes& s, int FB, bool update) {
   (void)update;
@@ -1381,6 +1494,53 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
                               const int* stop, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   if (L.fstride != facet_stride(s, (int)sizeof(R))) return cudaErrorInvalidValue;  // preconditioner layout only
+  const int4* rec0 = m.frec + first * 4;
+  const R* fs0 = P.Fs + first * (int64_t)fs_stride(s);
+  {
+    // warp-per-facet kernel for large facet blocks (at least 4 KB of stream per facet: 3D; measured
+    // faster there, slower than the batched block kernel for the 1.4 KB blocks of 2D k = 3), when the
+    // 2 m_F rows fit a warp and 8 warps' stages fit in 100 KB
+    const size_t wsm = (size_t)8 * 2 * warp_stage_elems<ElemSizes, R>(s) * sizeof(R);
+    if ((size_t)fs_stride(s) * sizeof(R) >= 4096 && 2 * s.mF <= 32 && wsm <= 100 * 1024) {
+      bool done = false;
+      dispatch_sizes(s, [&](auto sz) {
+        using SZ = decltype(sz);
+        static std::atomic<int> per_sm_w[2];
+        const int ui = update ? 1 : 0;
+        if (!per_sm_w[ui].load(std::memory_order_acquire)) {
+          cudaFuncSetAttribute(k_facet_step_warp<R, SZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
+          cudaFuncSetAttribute(k_facet_step_warp<R, SZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
+          int occ = 0;
+          if (update) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step_warp<R, SZ, true>, 256, wsm);
+          else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step_warp<R, SZ, false>, 256, wsm);
+          per_sm_w[ui].store(occ > 0 ? occ : 1, std::memory_order_release);
+        }
+        int64_t blocks = (int64_t)sm_count() * per_sm_w[ui].load(std::memory_order_acquire);
+        const int64_t need = (n + 7) / 8;
+        if (blocks > need) blocks = need;
+        const int cls = update ? PROF_FACET_GS : PROF_FACET_RES;
+        prof_begin(cls, st);
+        note_launch();
+        const int* ri = reinterpret_cast<const int*>(rec0);
+        if (update)
+          k_facet_step_warp<R, SZ, true><<<(unsigned)blocks, 256, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n, stop);
+        else
+          k_facet_step_warp<R, SZ, false><<<(unsigned)blocks, 256, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n, stop);
+        const double per = update ? (2.0 * s.mF * s.n_c + (double)s.mF * s.mF + 4.0 * s.mF)
+                                  : (2.0 * s.mF * s.n_c + 3.0 * s.mF);
+        prof_end(cls, (double)n * per * sizeof(R),
+                 2.0 * (double)n * (2.0 * s.mF * s.n_c + (update ? s.mF * s.mF : 0)), st);
+        done = true;
+      });
+      if (done && !P.debug) return cudaGetLastError();
+      if (done) {
+        dbg_sync(P, st, update ? "k_facet_step_warp (update)" : "k_facet_step_warp (residual)");
+        return cudaGetLastError();
+      }
+    }
+  }
   int FB = 256 / (2 * s.mF);
   if (FB < 1) FB = 1;
   while (FB > 1 && facet_step_smem<R>(s, FB, update) > 96 * 1024) --FB;
