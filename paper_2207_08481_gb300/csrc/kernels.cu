@@ -1541,10 +1541,18 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
       }
     }
   }
-  int FB = 256 / (2 * s.mF);
+  // small batches (at most 40 KB of stages, at least 4 facets) in narrow blocks, so that several
+  // blocks share an SM and their barriers overlap; else up to 96 KB
+  int FB = 128 / (2 * s.mF);
   if (FB < 1) FB = 1;
-  while (FB > 1 && facet_step_smem<R>(s, FB, update) > 96 * 1024) --FB;
-  const int threads = 256;
+  while (FB > 1 && facet_step_smem<R>(s, FB, update) > 40 * 1024) --FB;
+  int threads = 128;
+  if (FB < 4) {
+    FB = 256 / (2 * s.mF);
+    if (FB < 1) FB = 1;
+    while (FB > 1 && facet_step_smem<R>(s, FB, update) > 96 * 1024) --FB;
+    threads = 256;
+  }
   const size_t sm = facet_step_smem<R>(s, FB, update);
   const int64_t nb = (n + FB - 1) / FB;
   const int4* rec = m.frec + first * 4;

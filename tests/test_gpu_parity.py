@@ -138,10 +138,12 @@ def test_precond_fp64_matches_oracle(mcs, d, N, k, nu, lev):
     h.close()
 
 
-def test_precond_mixed_close_to_oracle(mcs):
-    h = _handle(mcs, 2, 8, 2, 1.0, precision=mcs.MCS_MIXED, gmg_levels=2)
-    D, AT = _oracle(2, 8, 2, 1.0)
-    bp = precond.BlockPreconditioner(D, precond.ASP(D, AT, precond.GMG(2, 8, 2, 1.0)))
+@pytest.mark.parametrize("d,N,k,lev", [(2, 8, 2, 2), (3, 4, 2, 2), (3, 2, 3, 1)])
+def test_precond_mixed_close_to_oracle(mcs, d, N, k, lev):
+    """FP32 preconditioner (3D k = 2 runs the warp-per-facet smoother kernel) against the FP64 oracle."""
+    h = _handle(mcs, d, N, k, 1.0, precision=mcs.MCS_MIXED, gmg_levels=lev)
+    D, AT = _oracle(d, N, k, 1.0)
+    bp = precond.BlockPreconditioner(D, precond.ASP(D, AT, precond.GMG(d, N, lev, 1.0)))
     r = np.random.default_rng(5).standard_normal(D.ndof)
     z = torch.zeros(D.ndof, dtype=torch.float64, device="cuda")
     h.precond(torch.tensor(r, device="cuda"), z)
