@@ -897,12 +897,14 @@ __global__ void __launch_bounds__(256) k_elem_prologue(S s, DevTables t, DevMesh
     for (int q = tid; q < nvalid * np_; q += blockDim.x) zz[q] = zp[L.off_p + T0 * np_ + q];
   __syncthreads();
   if (WITH_BT) {
+    // the B table in the preconditioner's precision (float: its leading part)
+    const R* Bt = sizeof(R) == 4 ? (const R*)(const void*)t.Bp_hi : (const R*)(const void*)t.Bp;
     for (int q = tid; q < nvalid * nu_; q += blockDim.x) {
       const int e = q / nu_, i = q - e * nu_;
       const int64_t T = T0 + e;
       R sg = i < nfd ? (R)m.signs[T * (d + 1) + i / s.nF] : (R)1;
       R v = 0;
-      for (int j = 0; j < np_; ++j) v += (R)t.Bp[j * nu_ + i] * zz[e * np_ + j];
+      for (int j = 0; j < np_; ++j) v += Bt[j * nu_ + i] * zz[e * np_ + j];
       bt[q] = -sg * v;
     }
     __syncthreads();
