@@ -204,6 +204,17 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info);
 /* Same as mcs_solve with HOST vectors F, x [ndof]: copies F and x in, solves, copies x out. */
 int mcs_solve_host(mcs_handle* h, const double* F_host, double* x_host, mcs_solve_info* info);
 
+/* Local recovery of the stress and rotation (eq. projection): for the solution x (device [ndof],
+ * layout above), per element the element-local problem of eq. (bigfemSPmat) is solved for
+ * (sigma_T, omega_T) given the element's (u, uhat), and both fields are evaluated at nq reference
+ * points xhat_host (host [nq][dim], coordinates on the reference simplex with vertices 0, e_1..e_dim;
+ * the physical point is x_0 + J xhat with J's columns x_i - x_0).  sigma, omega: device
+ * [ne][nq][dim][dim] (physical tensors; omega may be NULL).  Recomputes the condensation workspace of
+ * every element (about the cost of mcs_condense).  Asynchronous; takes a small temporary from the
+ * stream-ordered allocator.  Errors: INVALID_ARG, OOM, CUDA. */
+int mcs_recover_stress(mcs_handle* h, const double* x, int nq, const double* xhat_host, double* sigma,
+                       double* omega);
+
 /* Kernel timing (diagnostics): when enabled, the library brackets its main kernel classes
  * with CUDA events on the handle's stream during mcs_condense / mcs_apply / mcs_precond /
  * mcs_solve.  mcs_profile(h, 1) enables and clears, 0 disables.  mcs_profile_read fills up

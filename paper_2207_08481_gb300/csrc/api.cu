@@ -1045,6 +1045,26 @@ int mcs_profile(mcs_handle* h, int enable) {
   });
 }
 
+int mcs_recover_stress(mcs_handle* h, const double* x, int nq, const double* xhat_host, double* sigma,
+                       double* omega) {
+  return guarded([&]() -> int {
+    if (!h || !x || !xhat_host || !sigma || nq < 1) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument or nq < 1");
+    const int d = h->d, nk = h->sz.nk;
+    std::vector<double> psi((size_t)nq * nk);
+    for (int q = 0; q < nq; ++q) dubiner_eval(d, h->k, xhat_host + (size_t)q * d, psi.data() + (size_t)q * nk, nullptr);
+    cudaStream_t st = h->stream;
+    double* psi_dev = nullptr;
+    cuda_check(cudaMallocAsync((void**)&psi_dev, sizeof(double) * psi.size(), st), "cudaMallocAsync");
+    cudaError_t e = cudaMemcpyAsync(psi_dev, psi.data(), sizeof(double) * psi.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = launch_recover(h->es, h->dt, h->dm, h->L, h->nu, x, nq, psi_dev, sigma, omega, h->cond_scratch,
+                         h->cond_scratch_doubles, st);
+    cudaFreeAsync(psi_dev, st);
+    cuda_check(e, "stress recovery");
+    return MCS_OK;
+  });
+}
+
 int mcs_launch_count(uint64_t* count) {
   return guarded([&]() -> int {
     if (!count) throw McsError(MCS_ERR_INVALID_ARG, "count is NULL");

@@ -266,7 +266,10 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
                                                  const int* sgn, double nu, ElemWork w, int lane, int nl,
                                                  Sync sync) {
   const int nraw = s.n_raw, ns0 = s.n_s0, nA = s.n_A, nu_ = s.n_u, ncc = s.n_cc, d = s.d, rs = raw_stride(s);
-  if (lane == 0) elem_geometry(s, X, t.nhat, w.geo);
+  if (lane == 0) {
+    elem_geometry(s, X, t.nhat, w.geo);
+    w.geo[102] = nu;
+  }
   sync();
   const double* L = w.geo;
   const double* h = w.geo + 64;
@@ -382,6 +385,107 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
     v *= si * sj;
     w.A[i * nA + j] = v;
     w.A[j * nA + i] = v;
+  }
+  sync();
+}
+
+// Local stress recovery (eq. projection): after condense_element for the same element, the
+// stress of the element-local problem for the velocity coefficients a (local basis, n_A values,
+// orientation signs removed) is sigma = (I - Ct^T (Ct Ct^T)^{-1} Ct) Bt^T a in the whitened raw
+// basis, i.e. M^{-1} B_sigma^T a on the nt- and rotation-constrained space.  It is mapped back to the
+// raw basis (sigma_raw = cB (I (x) L) sigma~) and evaluated at nq reference points with the Dubiner
+// values psi [nq][nk]:  sigma(x) = J^{-T} (sum_{i,s} sigma_raw[i,s] psi_i(x^) E_s) J^T.
+// work: n_cc + n_raw + n_raw doubles; out: [nq][d][d].  X: vertex coordinates [(d+1)][d].
+// The rotation omega is the multiplier of the weak-symmetry rows of Ct: in the raw basis
+// M sigma = B^T a - C^T y / cB, and the raw rotation rows are (1/|det J|) (Phi : K_r psi), so
+// omega = sum_{r, i<n_p} w_{r,i} psi_i K_r with w = -y_rot / (cB |det J|) (skew units K_r unmapped);
+// out_w [nq][d][d] (may be NULL).
+template <class Sync>
+__host__ __device__ inline void recover_element(const ElemSizes& s, ElemWork w, const double* X, const double* a,
+                                                int nq, const double* psi, double* work, double* out,
+                                                double* out_w, int lane, int nl, Sync sync) {
+  const int nA = s.n_A, ncc = s.n_cc, nraw = s.n_raw, ns0 = s.n_s0, d = s.d, rs = raw_stride(s);
+  double* y = work;              // [ncc]
+  double* st = y + ncc;          // [nraw] whitened
+  double* sr = st + nraw;        // [nraw] raw
+  // g = Z a (Z = Lc^{-1} Ct Bt^T is in w.V), then y = Lc^{-T} g
+  for (int c = lane; c < ncc; c += nl) {
+    double v = 0;
+    for (int i = 0; i < nA; ++i) v += w.V[c * nA + i] * a[i];
+    y[c] = v;
+  }
+  sync();
+  if (lane == 0)
+    for (int i = ncc - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int p = i + 1; p < ncc; ++p) v -= w.Sc[p * ncc + i] * y[p];
+      y[i] = v / w.Sc[i * ncc + i];
+    }
+  sync();
+  for (int j = lane; j < nraw; j += nl) {
+    double v = 0;
+    for (int i = 0; i < nA; ++i) v += w.Bt[i * rs + j] * a[i];
+    for (int c = 0; c < ncc; ++c) v -= w.Ct[c * rs + j] * y[c];
+    st[j] = v;
+  }
+  sync();
+  const double* L = w.geo;
+  const double cB = sqrt(w.geo[102] / w.geo[100]);
+  for (int j = lane; j < nraw; j += nl) {
+    const int i = j / ns0, p = j - i * ns0;
+    double v = 0;
+    for (int q = 0; q <= p; ++q) v += L[p * ns0 + q] * st[i * ns0 + q];
+    sr[j] = cB * v;
+  }
+  sync();
+  double J[9], Ji[9];
+  for (int aa = 0; aa < d; ++aa)
+    for (int i = 0; i < d; ++i) J[aa * d + i] = X[(i + 1) * d + aa] - X[aa];
+  if (d == 2) {
+    const double det = J[0] * J[3] - J[1] * J[2];
+    Ji[0] = J[3] / det; Ji[1] = -J[1] / det; Ji[2] = -J[2] / det; Ji[3] = J[0] / det;
+  } else {
+    const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                       J[2] * (J[3] * J[7] - J[4] * J[6]);
+    Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+    Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+    Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+    Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+    Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+    Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+  }
+  for (int q = lane; q < nq; q += nl) {
+    double E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // sum_{i,s} sigma_raw psi_i E_s (reference tensor)
+    for (int i = 0; i < s.nk; ++i) {
+      const double pv = psi[q * s.nk + i];
+      for (int p = 0; p < ns0; ++p) {
+        const double c = sr[i * ns0 + p] * pv;
+        for (int aa = 0; aa < d; ++aa)
+          for (int bb = 0; bb < d; ++bb) E[aa * d + bb] += c * tf_unit(d, p, aa, bb);
+      }
+    }
+    // J^{-T} E J^T: entry (i, j) = sum_{a,b} Ji[a][i] E[a][b] J[j][b]
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        double v = 0;
+        for (int aa = 0; aa < d; ++aa)
+          for (int bb = 0; bb < d; ++bb) v += Ji[aa * d + i] * E[aa * d + bb] * J[j * d + bb];
+        out[(q * d + i) * d + j] = v;
+      }
+    if (out_w) {
+      const double sc = -1.0 / (cB * w.geo[100]);
+      double Wm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int r = 0; r < s.n_wskew; ++r)
+        for (int ip = 0; ip < s.n_p; ++ip) {
+          const double c = sc * y[s.n_con + r * s.n_p + ip] * psi[q * s.nk + ip];
+          for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) Wm[i * d + j] += c * skew_unit(d, r, i, j);
+        }
+      for (int i = 0; i < d * d; ++i) out_w[q * d * d + i] = Wm[i];
+    }
   }
   sync();
 }

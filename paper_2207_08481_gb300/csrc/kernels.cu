@@ -770,6 +770,74 @@ __global__ void k_load_points(ElemSizes s, DevTables t, DevMesh m, double* xq) {
   }
 }
 
+// ---------------------------------------------------------------- stress recovery
+// Per element (one block): the condensation workspace is rebuilt (condense_element), the local
+// velocity coefficients are gathered from x with the orientation signs of the facet-BDM dofs removed,
+// and recover_element evaluates sigma_h and omega_h at the reference points (eq. projection).
+template <bool SMEM>
+__global__ void __launch_bounds__(256) k_recover(ElemSizes s, DevTables t, DevMesh m, Layout L, double nu,
+                                                 const double* __restrict__ x, int nq, const double* __restrict__ psi,
+                                                 double* sig, double* om, double* gscratch, int64_t slot) {
+  extern __shared__ double smr[];
+  const int lane = threadIdx.x, nl = blockDim.x, d = s.d, nA = s.n_A, nfd = (s.d + 1) * s.nF;
+  double* base = SMEM ? smr : gscratch + (int64_t)blockIdx.x * slot;
+  ElemWork w = elem_work_carve(s, base);
+  double* Xs = base + elem_work_doubles(s);
+  int* sg = (int*)(Xs + 16);
+  double* a = Xs + 24;
+  double* wk = a + nA;
+  ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat};
+  const int64_t per = (int64_t)nq * d * d;
+  for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) {
+    if (lane < (d + 1) * d) {
+      const int v = lane / d, c = lane % d;
+      Xs[lane] = m.coords[(int64_t)m.elems[T * (d + 1) + v] * d + c];
+    }
+    if (lane <= d) sg[lane] = m.signs[T * (d + 1) + lane];
+    __syncthreads();
+    condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
+    for (int i = lane; i < nA; i += nl) {
+      const int64_t g = local_to_global(s, L, m.elem_rank + T * (d + 1), T, i);
+      a[i] = g < 0 ? 0.0 : x[g] * (i < nfd ? (double)sg[i / s.nF] : 1.0);
+    }
+    __syncthreads();
+    recover_element(s, w, Xs, a, nq, psi, wk, sig + T * per, om ? om + T * per : nullptr, lane, nl, BlockSync());
+  }
+}
+
+int64_t recover_slot_doubles(const ElemSizes& s) {
+  return ((int64_t)elem_work_doubles(s) + 24 + s.n_A + s.n_cc + 2 * s.n_raw + 31) / 32 * 32;
+}
+
+cudaError_t launch_recover(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
+                           const double* x, int nq, const double* psi, double* sig, double* om, double* scratch,
+                           int64_t scratch_doubles, cudaStream_t st) {
+  const int64_t slot = recover_slot_doubles(s);
+  int dev = 0, nsm = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int threads = s.d == 2 ? 128 : 256;
+  if (slot * 8 <= maxsm) {
+    const size_t sm = (size_t)slot * 8;
+    cudaFuncSetAttribute(k_recover<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover<true>, threads, sm);
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)nsm * per_sm;
+    if (blocks > m.ne) blocks = m.ne;
+    k_recover<true><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, L, nu, x, nq, psi, sig, om, nullptr, slot);
+    note_launch();
+  } else {
+    int64_t blocks = scratch_doubles / slot;
+    if (blocks < 1) return cudaErrorMemoryAllocation;
+    if (blocks > m.ne) blocks = m.ne;
+    k_recover<false><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, L, nu, x, nq, psi, sig, om, scratch, slot);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_load_points(const ElemSizes& s, const DevTables& t, const DevMesh& m, double* xq,
                                cudaStream_t st) {
   k_load_points<<<sm_count() * 8, 256, 0, st>>>(s, t, m, xq);

@@ -188,6 +188,13 @@ cudaError_t launch_mass_u(const ElemSizes& s, const DevTables& t, const DevMesh&
 cudaError_t launch_load(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L,
                         const double* fq, double* F, cudaStream_t st);
 // physical load quadrature points [ne][nq][d]
+// sigma_h, omega_h of every element at nq reference points (psi: Dubiner values [nq][nk], device)
+// into sig / om [ne][nq][d][d] (om may be NULL); scratch: global workspace when one element's does not
+// fit in shared memory.
+int64_t recover_slot_doubles(const ElemSizes& s);
+cudaError_t launch_recover(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
+                           const double* x, int nq, const double* psi, double* sig, double* om, double* scratch,
+                           int64_t scratch_doubles, cudaStream_t st);
 cudaError_t launch_load_points(const ElemSizes& s, const DevTables& t, const DevMesh& m, double* xq,
                                cudaStream_t st);
 

@@ -29,7 +29,7 @@ EXPORTED = ["mcs_version", "mcs_last_error", "mcs_default_options", "mcs_setup_s
             "mcs_sizes", "mcs_export_mesh", "mcs_export_dofmap", "mcs_export_pattern", "mcs_condense",
             "mcs_condense_batch",
             "mcs_copy_element_matrices", "mcs_copy_schur", "mcs_load_points", "mcs_load_vector",
-            "mcs_mass_velocity", "mcs_apply", "mcs_residual", "mcs_precond", "mcs_solve", "mcs_solve_host", "mcs_profile",
+            "mcs_mass_velocity", "mcs_apply", "mcs_residual", "mcs_recover_stress", "mcs_precond", "mcs_solve", "mcs_solve_host", "mcs_profile",
             "mcs_profile_read", "mcs_launch_count", "mcs_condense_noalloc", "mcs_destroy"]
 
 
@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         L.mcs_mass_velocity.argtypes = [vp, vp, vp]
         L.mcs_apply.argtypes = [vp, vp, vp]
         L.mcs_residual.argtypes = [vp, vp, vp, vp]
+        L.mcs_recover_stress.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp]
         L.mcs_precond.argtypes = [vp, vp, vp]
         L.mcs_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveInfo)]
         L.mcs_solve_host.argtypes = [vp, vp, vp, ctypes.POINTER(SolveInfo)]
@@ -242,6 +243,13 @@ class Handle:
 
     def residual(self, F, x, r):
         _check(lib().mcs_residual(self._h, _dptr(F), _dptr(x), _dptr(r)))
+
+    def recover_stress(self, x, xhat, sigma, omega=None):
+        """sigma_h, omega_h of every element at the reference points xhat [nq, dim] (host) into the device
+        tensors sigma, omega [ne, nq, dim, dim] (omega optional)."""
+        xh = np.ascontiguousarray(xhat, dtype=np.float64)
+        _check(lib().mcs_recover_stress(self._h, _dptr(x), xh.shape[0], _hptr(xh), _dptr(sigma),
+                                        _dptr(omega) if omega is not None else None))
 
     def precond(self, r, z):
         _check(lib().mcs_precond(self._h, _dptr(r), _dptr(z)))

@@ -9,7 +9,7 @@ if not torch.cuda.is_available():
     pytest.skip("no GPU", allow_module_level=True)
 
 import workloads  # noqa: E402
-from oracle import manufactured, mesh, precond, system  # noqa: E402
+from oracle import fem, manufactured, mesh, precond, system  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -397,4 +397,28 @@ def test_general_mesh_perturbed(mcs, d, N, k, nu):
     xo = system.mean_zero_pressure(D, xo)
     xg = x.cpu().numpy()
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-10, (info.status, info.iterations)
+    h.close()
+
+
+@pytest.mark.parametrize("d,N,k,nu", [(2, 3, 2, 0.7), (2, 2, 4, 1.3), (3, 1, 3, 0.5), (3, 2, 2, 1.0)])
+def test_recover_stress_matches_oracle(mcs, d, N, k, nu):
+    """sigma_h and omega_h of the local problems (eq. projection) for the same coefficient vector,
+    evaluated at the oracle's quadrature points of every element."""
+    h = _handle(mcs, d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=1)
+    m = mesh.structured(d, N)
+    D = system.discretize(m, k, nu)
+    x = np.random.default_rng(8).standard_normal(D.ndof)
+    sig, om = system.recover_stress(D, x)
+    X = m.coords[m.elems]
+    E = fem.element_data(X, m.signs, k)
+    so = np.einsum("ej,eqjab->eqab", sig, E.S)
+    wo = np.einsum("ej,eqjab->eqab", om, E.W)
+    J0 = (X[0, 1:, :] - X[0, :1, :]).T
+    xhat = np.linalg.solve(J0, (E.xq[0] - X[0, 0]).T).T
+    ne, nq = X.shape[0], xhat.shape[0]
+    sg = torch.zeros((ne, nq, d, d), dtype=torch.float64, device="cuda")
+    om_g = torch.zeros_like(sg)
+    h.recover_stress(torch.tensor(x, device="cuda"), xhat, sg, om_g)
+    assert np.abs(sg.cpu().numpy() - so).max() < 1e-11 * np.abs(so).max()
+    assert np.abs(om_g.cpu().numpy() - wo).max() < 1e-10 * np.abs(wo).max()
     h.close()
