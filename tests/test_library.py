@@ -64,4 +64,7 @@ def test_invalid_arguments_are_reported_not_raised(lib):
     assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
     assert lib.default_options().asp == 0
     assert L.mcs_apply(None, None, None) == lib.MCS_ERR_INVALID_ARG
+    assert L.mcs_recover_stress(None, None, 1, None, None, None) == lib.MCS_ERR_INVALID_ARG
+    assert L.mcs_residual(None, None, None, None) == lib.MCS_ERR_INVALID_ARG
+    assert L.mcs_condense_batch(None, 0) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_destroy(None) == lib.MCS_OK
