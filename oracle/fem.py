@@ -32,6 +32,7 @@ from __future__ import annotations
 
 import functools
 import itertools
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -44,6 +45,21 @@ def n_bdm_facet(d, k):
 
 
 def local_sizes(d: int, k: int) -> dict:
+    """Local dimensions.  k = 1 is the lowest-order variant of Sec. 7 (d = 3 only): W_h is
+    the H(div) space P^0(T, R^3) + x P^0(T) with one normal-flux dof per facet, kept after
+    condensation; its dof sits behind the two tangential Vhat_h dofs of each facet, so
+    n_hatF = 3, n_tF = 2 (tangential) and n_omega = 0 (no element-local rotations)."""
+    if k == 1:
+        if d != 3:
+            raise ValueError("the lowest-order variant (k = 1) is three-dimensional")
+        sz = local_sizes_general(d, 1)
+        sz.update(lowest=True, n_tF=2, n_hatF=3, n_hat=(d + 1) * 3, n_omega=0,
+                  n_A=sz["n_full"] + (d + 1) * 3)
+        return sz
+    return local_sizes_general(d, k)
+
+
+def local_sizes_general(d: int, k: int) -> dict:
     nk = polys.n_poly(d, k)
     n_full = d * nk
     nF = n_bdm_facet(d, k)
@@ -54,7 +70,8 @@ def local_sizes(d: int, k: int) -> dict:
     n_raw_sigma = (d * d - 1) * nk
     n_con = (d + 1) * (d - 1) * (polys.n_poly(d - 1, k) - polys.n_poly(d - 1, k - 1))
     return dict(d=d, k=k, nk=nk, n_full=n_full, nF=nF, n_bub=n_bub, n_dd=(d + 1) * nF,
-                n_hatF=n_hatF, n_hat=(d + 1) * n_hatF, n_p=n_p, n_omega=n_omega,
+                n_hatF=n_hatF, n_tF=n_hatF, lowest=False, n_hat=(d + 1) * n_hatF, n_p=n_p,
+                n_omega=n_omega,
                 n_sigma=n_raw_sigma - n_con, n_raw_sigma=n_raw_sigma, n_con=n_con,
                 n_u=n_full, n_A=n_full + (d + 1) * n_hatF)
 
@@ -95,6 +112,8 @@ def interior_test_functions(d: int, k: int, xh: np.ndarray) -> np.ndarray:
                     q = np.zeros(xh.shape)
                     q[:, c] = mono
                     out.append(np.cross(xh, q))
+    if not out:                                                 # k = 1: BDM^1 has no bubbles
+        return np.zeros((xh.shape[0], 0, d))
     return np.stack(out, axis=1)
 
 
@@ -145,6 +164,7 @@ class ElementData:
     fU: np.ndarray        # [E, d+1, nqf, n_u, d]
     fS: np.ndarray        # [E, d+1, nqf, n_s, d, d]
     fH: np.ndarray        # [E, d+1, nqf, n_hat, d]  hat basis (zero off its facet)
+    divW: np.ndarray | None = None   # k = 1: [E, nq, d+1] div of the H(div) rotation functions
 
 
 @functools.lru_cache(maxsize=None)
@@ -282,11 +302,25 @@ def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None,
     divS = np.einsum("eqra,ers->eqsa", divR, Nsig)
     fS = np.stack([np.einsum("qrab,ers->eqsab", raw_vals(fpsi[f]), Nsig) for f in range(dp1)], axis=1)
 
-    # ---------------- W_h = P^{k-1}(T, skew) --------------------------------
-    K = skew_units(d)
-    nkm1 = polys.n_poly(d, k - 1)
-    W = np.einsum("qi,rab->qriab", psi[:, :nkm1], K).reshape(nq, -1, d, d)
-    W = np.broadcast_to(W[None], (E_,) + W.shape).copy()
+    divW = None
+    if sz["lowest"]:
+        # ------------ k = 1 (Sec. 7): W_h in H(div), P^0(T, R^3) + x P^0(T) -----------
+        # dof of facet f = flux through F with the global normal n_F, so the function of local
+        # facet f is s_{T,f} (x - x_f) / (d |T|), x_f the vertex opposite f (its flux out of T
+        # through F_f is 1, through the other facets 0); every occurrence of omega is kappa(omega)
+        vol = np.abs(detJ) / math.factorial(d)
+        W = np.zeros((E_, nq, dp1, d, d))
+        divW = np.zeros((E_, nq, dp1))
+        for f in range(dp1):
+            phi = signs[:, f][:, None, None] * (xq - X[:, f, None, :]) / (d * vol)[:, None, None]
+            W[:, :, f] = kappa(phi)
+            divW[:, :, f] = (signs[:, f] / vol)[:, None]
+    else:
+        # ---------------- W_h = P^{k-1}(T, skew) ----------------------------
+        K = skew_units(d)
+        nkm1 = polys.n_poly(d, k - 1)
+        W = np.einsum("qi,rab->qriab", psi[:, :nkm1], K).reshape(nq, -1, d, d)
+        W = np.broadcast_to(W[None], (E_,) + W.shape).copy()
 
     # ---------------- Vhat_h on facets ---------------------------------------
     nFm1 = polys.n_poly(d - 1, k - 1)
@@ -300,7 +334,19 @@ def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None,
                 col = f * n_hatF + m * nFm1 + j
                 fH[:, f, :, col, :] = qF[None, :, j, None] * Ef[:, None, m, :]
 
-    return ElementData(detJ, wq, xq, U, DU, divU, P, S, divS, W, fw, fx, fn, fU, fS, fH)
+    return ElementData(detJ, wq, xq, U, DU, divU, P, S, divS, W, fw, fx, fn, fU, fS, fH, divW)
+
+
+def kappa(v: np.ndarray) -> np.ndarray:
+    """kappa of Sec. 2 (notation) for d = 3: v[..., 3] -> 1/2 [[0, -v3, v2], [v3, 0, -v1], [-v2, v1, 0]]."""
+    out = np.zeros(v.shape + (3,))
+    out[..., 0, 1] = -v[..., 2]
+    out[..., 0, 2] = v[..., 1]
+    out[..., 1, 0] = v[..., 2]
+    out[..., 1, 2] = -v[..., 0]
+    out[..., 2, 0] = -v[..., 1]
+    out[..., 2, 1] = v[..., 0]
+    return 0.5 * out
 
 
 def element_matrices(X, signs, k, nu):
@@ -319,7 +365,8 @@ def element_matrices(X, signs, k, nu):
     d = X.shape[2]
     out = {}
     out["M"] = np.einsum("eq,eqiab,eqjab->eij", D.wq, D.S, D.S) / nu
-    out["Bw"] = np.einsum("eq,eqjab,eqiab->eij", D.wq, D.S, D.W)
+    if D.divW is None:
+        out["Bw"] = np.einsum("eq,eqjab,eqiab->eij", D.wq, D.S, D.W)
     vol = np.einsum("eq,eqja,eqia->eij", D.wq, D.divS, D.U)
     Snn = np.einsum("efqjab,efa,efb->efqj", D.fS, D.fn, D.fn)
     Un = np.einsum("efqia,efa->efqi", D.fU, D.fn)
@@ -328,6 +375,17 @@ def element_matrices(X, signs, k, nu):
     Sn = np.einsum("efqjab,efb->efqja", D.fS, D.fn)
     Snt = Sn - Snn[..., None] * D.fn[:, :, None, None, :]
     out["Bh"] = -np.einsum("efq,efqja,efqia->eij", D.fw, Snt, D.fH)
+    if D.divW is not None:
+        # k = 1 (Sec. 7): the rotation dofs are the third entry of each facet's hat block; they
+        # couple to sigma through (phi^sigma, kappa(phi^omega))_T and carry the stabilisation
+        # nu (div omega, div eta)_T (reading R21: coefficient nu)
+        nhF = D.fH.shape[3] // (d + 1)
+        rows = [f * nhF + nhF - 1 for f in range(d + 1)]
+        out["Bw"] = np.zeros((X.shape[0], 0, D.S.shape[2]))
+        out["Bh"][:, rows, :] = np.einsum("eq,eqjab,eqfab->efj", D.wq, D.S, D.W)
+        Sh = np.zeros((X.shape[0], len(out["Bh"][0]), len(out["Bh"][0])))
+        Sh[:, np.ix_(rows, rows)[0], np.ix_(rows, rows)[1]] = nu * np.einsum("eq,eqf,eqg->efg", D.wq, D.divW, D.divW)
+        out["Shat"] = Sh
     out["Adiv"] = nu / d * np.einsum("eq,eqi,eqj->eij", D.wq, D.divU, D.divU)
     out["Bp"] = -np.einsum("eq,eqj,eqi->eij", D.wq, D.divU, D.P)
     out["Mu"] = np.einsum("eq,eqia,eqja->eij", D.wq, D.U, D.U)

@@ -7,7 +7,9 @@
                    read as nu, reading R1).
 * ``embedding``    E ubar = (ubar, (ubar)_t) (eq. defE), written out through the
                    dof functionals: facet flux moments, interior moments, and the
-                   L2(F) projection of the tangential trace onto Vhat_h.
+                   L2(F) projection of the tangential trace onto Vhat_h; for the
+                   lowest-order variant (k = 1, Sec. 7) E ubar = (ubar,
+                   Pi^0 (ubar)_t, curl ubar), the L2 projection being Pi^0 there.
 * ``GMG``          geometric multigrid V-cycle used as C (reading R11): nested
                    Kuhn meshes, prolongation = P1 interpolation (2-point edge
                    average), 2 pre- and 2 post-sweeps of l1-Jacobi
@@ -127,7 +129,7 @@ def embedding(D: system.Discretization) -> sp.csr_matrix:
     sz = D.sz
     rank, nv = p1_map(m)
     R, C, V = [], [], []
-    nF, nhF, nb = sz["nF"], sz["n_hatF"], sz["n_bub"]
+    nF, nhF, ntF, nb = sz["nF"], sz["n_hatF"], sz["n_tF"], sz["n_bub"]
     s, ws = polys.quadrature(d - 1, k + 2)
     qF = polys.dubiner(d - 1, k, s)[0]
     nFm1 = polys.n_poly(d - 1, k - 1)
@@ -161,8 +163,20 @@ def embedding(D: system.Discretization) -> sp.csr_matrix:
                     R.append(r * nF + j); C.append(col); V.append(mom[j])
                 rhs = np.einsum("q,qa,qia->i", wf, ub, basis)
                 ch = np.linalg.solve(G, rhs)
-                for j in range(nhF):
+                for j in range(ntF):
                     R.append(D.off_h + r * nhF + j); C.append(col); V.append(ch[j])
+                if sz["lowest"]:
+                    # k = 1 (Sec. 7): third component curl(ubar), as its flux int_F curl(ubar).n_F;
+                    # curl(lambda_v e_a) = grad(lambda_v) x e_a, taken on an adjacent element
+                    T = m.facet_elems[F, 0]
+                    XT = m.coords[m.elems[T]]
+                    JT = (XT[1:] - XT[:1]).T
+                    ghat = np.vstack([-np.ones(d), np.eye(d)])
+                    gl = np.linalg.solve(JT.T, ghat[list(m.elems[T]).index(vid)])
+                    ea = np.zeros(d)
+                    ea[a] = 1.0
+                    R.append(D.off_h + r * nhF + ntF); C.append(col)
+                    V.append(meas * float(np.cross(gl, ea) @ m.normals[F]))
     # bubble rows: interior moments I_m(ubar|T) = int_T ubar . J^{-T} g_m
     X = m.coords[m.elems]
     xv, wv = polys.quadrature(d, k + 2)

@@ -16,7 +16,10 @@
 
 Global vector layout (dof contract): [u_d | u_o | uhat | p], with u_d indexed by
 (interior facet rank, mode), u_o by (element, bubble), uhat by (interior facet
-rank, tangent, mode), p by (element, mode).
+rank, tangent, mode), p by (element, mode).  For the lowest-order variant (k = 1,
+Sec. 7) u_o is empty and each facet's uhat block is (tangent 1, tangent 2, flux of
+the H(div) rotation omega); the rotation is condensed away with sigma for k >= 2
+only.
 """
 from __future__ import annotations
 
@@ -167,6 +170,8 @@ def full_system(D: Discretization):
     add(shift(um), s_map, D.mats["Bu"])
     add(shift(hm), s_map, D.mats["Bh"])
     add(shift(um), shift(um), D.mats["Adiv"], sym=False)
+    if "Shat" in D.mats:                                        # k = 1: nu (div omega, div eta)
+        add(shift(hm), shift(hm), D.mats["Shat"], sym=False)
     add(shift(pm), shift(um), D.mats["Bp"])
     Kf = sp.csr_matrix((np.concatenate(V), (np.concatenate(R), np.concatenate(C))), shape=(n, n))
     return Kf, off
@@ -215,6 +220,8 @@ def condense(D: Discretization) -> np.ndarray:
     Bs[:, nu_:, :ns] = m["Bh"]
     Aext = np.zeros((ne, nu_ + nh, nu_ + nh))
     Aext[:, :nu_, :nu_] = m["Adiv"]
+    if "Shat" in m:
+        Aext[:, nu_:, nu_:] = m["Shat"]
     return Aext - Bs @ np.linalg.solve(Mloc, np.transpose(Bs, (0, 2, 1)))
 
 
