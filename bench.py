@@ -291,10 +291,14 @@ def run_gpu(args):
 
 
 def _multi_degree(args, torch, mcs):
-    """Mixed-degree batch: one persistent condensation launch for three problems against one launch per
-    problem, then the three solves (random F = M_u c, seeded)."""
-    ks = (2, 3, 4)
-    hs = [mcs.Handle.structured(3, 16, k, 1.0, precision=mcs.MCS_MIXED) for k in ks]
+    """Mixed-degree batch: one persistent condensation launch for four problems (the lowest-order
+    variant k = 1 and k = 2, 3, 4) against one launch per problem, then the four solves (random
+    F = M_u c, seeded)."""
+    ks = (1, 2, 3, 4)
+    # k = 1: the ASP condition number grows under refinement (stabilisation weight nu), hence more
+    # MinRes iterations
+    hs = [mcs.Handle.structured(3, 16, k, 1.0, precision=mcs.MCS_MIXED, maxit=8000 if k == 1 else 1000)
+          for k in ks]
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
     def timed(fn, reps=2):
@@ -333,8 +337,9 @@ def _multi_degree(args, torch, mcs):
                             "rel_res": info.rel_res_precond}
     for h in hs:
         h.close()
-    return {"config": "3D unit cube, 16^3 cells x 6 = 24,576 tetrahedra each, k = 2, 3, 4, nu = 1, mixed form, "
-                      "random F = M_u c (c ~ N(0,1)); k = 1, 5, 6 of the six-problem batch are not supported",
+    return {"config": "3D unit cube, 16^3 cells x 6 = 24,576 tetrahedra each, k = 1 (lowest-order variant), 2, 3, 4, "
+                      "nu = 1, mixed form, random F = M_u c (c ~ N(0,1)); k = 5, 6 of the six-problem batch are "
+                      "not supported",
             "condense_batched_ms": round(t_batch, 2), "condense_separate_ms": round(t_sep, 2), "solves": solves}
 
 

@@ -31,6 +31,10 @@
  *     u_o: BDM bubbles (element T, m) at off_o + T*n_bub + m;
  *     uhat: tangential facet dofs (r, tangent m, mode j) at off_h + r*nhF + m*dimP^{k-1}(F) + j;
  *     p: pressure (T, mode j) at off_p + T*n_p + j.
+ *     Lowest-order variant (k = 1, Sec. 7, dim = 3): no bubbles; the rotation omega lies in
+ *     H(div) (P^0(T, R^3) + x P^0(T)), is kept after condensation, and its dof on facet r, the
+ *     flux int_F omega.n_F, follows the two tangential uhat dofs: nhF = 3, uhat block of r =
+ *     (t_1, t_2, omega flux).  The weak form uses kappa(omega) and adds nu (div omega, div eta).
  *   - Dof contract (the paper leaves bases and orientations open):
  *     * facets are the distinct sorted vertex tuples in lexicographic order; interior
  *       facets keep that order (rank r); local facet f of an element is opposite its
@@ -120,7 +124,7 @@ int mcs_default_options(mcs_options* o);
 /* Set-up on the Kuhn triangulation of [0,1]^dim with N cells per direction
  * (Sec. 7 uses unstructured meshes; the synthetic workloads use this nested
  * family so that the conforming space has a geometric multigrid hierarchy).
- * dim in {2, 3}, k = 2..4 (Sec. 3; k = 1 is the variant of Sec. 6, not supported),
+ * dim in {2, 3}, k = 2..4 (Sec. 3), or k = 1 with dim = 3 (the lowest-order variant of Sec. 7),
  * nu > 0 as printed in eq. (stokes).  stream: a cudaStream_t (NULL = default).
  * Builds mesh, facets, dof maps, colouring and the multigrid hierarchy on the
  * host and uploads them; allocates the resident operators.  Synchronous.
@@ -211,7 +215,9 @@ int mcs_solve_host(mcs_handle* h, const double* F_host, double* x_host, mcs_solv
  * the physical point is x_0 + J xhat with J's columns x_i - x_0).  sigma, omega: device
  * [ne][nq][dim][dim] (physical tensors; omega may be NULL).  Recomputes the condensation workspace of
  * every element (about the cost of mcs_condense).  Asynchronous; takes a small temporary from the
- * stream-ordered allocator.  Errors: INVALID_ARG, OOM, CUDA. */
+ * stream-ordered allocator.  For k = 1 the rotation is a global unknown (its flux dofs are part of
+ * x), only sigma is recovered and omega must be NULL (else UNSUPPORTED).
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
 int mcs_recover_stress(mcs_handle* h, const double* x, int nq, const double* xhat_host, double* sigma,
                        double* omega);
 

@@ -51,6 +51,7 @@ ElemSizes elem_sizes(const Sizes& s) {
   e.d = s.d; e.k = s.k; e.nk = s.nk; e.nF = s.nF; e.nFm1 = s.nFm1; e.n_u = s.n_u; e.n_A = s.n_A;
   e.n_hat = s.n_hat; e.nhF = s.nhF; e.n_p = s.n_p; e.n_s0 = s.n_s0; e.n_raw = s.n_raw; e.n_con = s.n_con;
   e.n_w = s.n_w; e.n_wskew = s.n_wskew; e.n_cc = s.n_cc; e.n_bub = s.n_bub; e.n_c = s.n_c; e.mF = s.mF;
+  e.ntF = s.ntF; e.lowest = s.lowest;
   return e;
 }
 
@@ -272,6 +273,7 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   dt.Ccon = h->upload(R.Ccon);
   dt.Adiv = h->upload(R.Adiv);
   dt.nhat = h->upload(R.nhat);
+  dt.Wmom = h->upload(R.Wmom);
   dt.Bp = h->upload(R.Bp);
   {
     std::vector<float> hi(R.Bp.size()), lo(R.Bp.size());
@@ -389,7 +391,9 @@ mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* 
   // k >= 5: the dual BDM basis of the dof contract (monomial interior moments) makes A_T so badly
   // scaled (2D k = 6: entries near 1e11 around a facet Schur complement near 1e2) that the
   // condensed blocks lose about 10 digits; 3D k >= 5 also exceeds the per-thread bubble block
-  if (k < 2 || k > 4) throw McsError(MCS_ERR_UNSUPPORTED, "k must be in 2..4");
+  // k = 1 is the lowest-order variant of Sec. 7, which the paper states for d = 3 (vector rotations)
+  if (k < 1 || k > 4) throw McsError(MCS_ERR_UNSUPPORTED, "k must be in 1..4");
+  if (k == 1 && dim != 3) throw McsError(MCS_ERR_UNSUPPORTED, "k = 1 (lowest-order variant) needs dim = 3");
   if (!(nu > 0)) throw McsError(MCS_ERR_INVALID_ARG, "nu must be positive");
   auto h = std::make_unique<mcs_handle>();
   h->d = dim;
@@ -1049,6 +1053,8 @@ int mcs_recover_stress(mcs_handle* h, const double* x, int nq, const double* xha
                        double* omega) {
   return guarded([&]() -> int {
     if (!h || !x || !xhat_host || !sigma || nq < 1) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument or nq < 1");
+    if (h->sz.lowest && omega)
+      throw McsError(MCS_ERR_UNSUPPORTED, "k = 1: the rotation is a global unknown (flux dofs in x); pass omega = NULL");
     const int d = h->d, nk = h->sz.nk;
     std::vector<double> psi((size_t)nq * nk);
     for (int q = 0; q < nq; ++q) dubiner_eval(d, h->k, xhat_host + (size_t)q * d, psi.data() + (size_t)q * nk, nullptr);

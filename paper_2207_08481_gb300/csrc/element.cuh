@@ -37,7 +37,13 @@ namespace mcs {
 struct ElemSizes {
   int d, k, nk, nF, nFm1, n_u, n_A, n_hat, nhF, n_p, n_s0, n_raw, n_con, n_w, n_wskew, n_cc;
   int n_bub, n_c, mF;
+  int ntF, lowest;   // tangential Vhat_h dofs per facet; 1 for the lowest-order variant (k = 1)
 };
+
+// Local index i of A_T is the rotation flux dof of a facet (lowest-order variant only).
+__host__ __device__ inline bool is_rot_dof(const ElemSizes& s, int i) {
+  return s.lowest && i >= s.n_u && (i - s.n_u) % s.nhF == s.ntF;
+}
 
 struct ElemTables {
   const double* B0;    // [n_u][n_raw]
@@ -46,6 +52,7 @@ struct ElemTables {
   const double* Ccon;  // [n_con][n_raw]
   const double* Adiv;  // [n_u][n_u]
   const double* nhat;  // [d+1][d]
+  const double* Wmom;  // k = 1: [d+1][d][nk]
 };
 
 // workspace layout (doubles), per element
@@ -259,12 +266,37 @@ __host__ __device__ inline void chol_inplace(int n, double* A, int lane, int nl,
   }
 }
 
+// Lowest-order variant (Sec. 7): raw row of the rotation flux function phi_f = (x - x_f) / (d |T|)
+// of local facet f, int (psi_i J^{-T} E_s J^T) : kappa(phi_f).  With x - x_f = J (xhat - xhat_f) and
+// kappa(v) = (v_3 K_0 - v_2 K_1 + v_1 K_2) / 2 it is
+//   sum_c Wmom[f][c][i] (J_2c h_0s - J_1c h_1s + J_0c h_2s)      (|det J| / (d |T|) = 2, d = 3).
+__host__ __device__ inline void rotation_row(const ElemSizes& s, const ElemTables& t, const double* X, const double* h,
+                                      int f, double* row) {
+  const int ns0 = s.n_s0;
+  double Jc[9];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) Jc[a * 3 + c] = X[(c + 1) * 3 + a] - X[a];
+  for (int e = 0; e < ns0; ++e) {
+    double kc[3];
+    for (int c = 0; c < 3; ++c) kc[c] = Jc[6 + c] * h[e] - Jc[3 + c] * h[ns0 + e] + Jc[c] * h[2 * ns0 + e];
+    for (int i = 0; i < s.nk; ++i) {
+      const double* wm = t.Wmom + (f * 3) * s.nk + i;
+      row[i * ns0 + e] = wm[0] * kc[0] + wm[s.nk] * kc[1] + wm[2 * s.nk] * kc[2];
+    }
+  }
+}
+
 // Full condensation of one element: A_T (n_A x n_A, row-major) with the orientation
-// signs of the facet-BDM dofs applied.
-template <class Sync>
-__host__ __device__ inline void condense_element(const ElemSizes& s, const ElemTables& t, const double* X,
-                                                 const int* sgn, double nu, ElemWork w, int lane, int nl,
-                                                 Sync sync) {
+// signs of the facet-BDM dofs (and, for k = 1, of the rotation flux dofs) applied.
+// Lowest-order variant (k = 1, Sec. 7): the rotation is not eliminated; its flux dofs are rows
+// of Bt (coupling through kappa(omega)), the constraints are the nt conditions alone, and
+// A_T gains nu (div omega, div eta)_T on the rotation rows.
+// LO is the compile-time form of s.lowest (condense_element below dispatches at run time), so that
+// the k >= 2 instantiation carries none of the lowest-order code.
+template <bool LO, class Sync>
+__host__ __device__ inline void condense_element_t(const ElemSizes& s, const ElemTables& t, const double* X,
+                                                   const int* sgn, double nu, ElemWork w, int lane, int nl,
+                                                   Sync sync) {
   const int nraw = s.n_raw, ns0 = s.n_s0, nA = s.n_A, nu_ = s.n_u, ncc = s.n_cc, d = s.d, rs = raw_stride(s);
   if (lane == 0) {
     elem_geometry(s, X, t.nhat, w.geo);
@@ -289,6 +321,8 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
           for (int j = 0; j < nraw; ++j) row[j] -= wa * R[j];
         }
       }
+    } else if (LO && is_rot_dof(s, r)) {
+      continue;   // lowest-order rotation rows: filled below
     } else {
       const double* Bh = t.Bh + (r - nu_) * nraw;
       for (int j = 0; j < nraw; ++j) row[j] = adet * Bh[j];
@@ -304,6 +338,20 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
       }
     }
   }
+  if (LO)
+    for (int f = lane; f <= d; f += nl) {
+      double* row = w.Bt + (nu_ + f * s.nhF + s.ntF) * rs;
+      rotation_row(s, t, X, h, f, row);
+      for (int i = 0; i < s.nk; ++i) {
+        double tmp[8];
+        for (int q = 0; q < ns0; ++q) tmp[q] = row[i * ns0 + q];
+        for (int q = 0; q < ns0; ++q) {
+          double v = 0;
+          for (int p = q; p < ns0; ++p) v += tmp[p] * L[p * ns0 + q];
+          row[i * ns0 + q] = cB * v;
+        }
+      }
+    }
   // ---- Ct rows: nt constraints, then rotation constraints ----
   for (int r = lane; r < ncc; r += nl) {
     double* row = w.Ct + r * rs;
@@ -329,6 +377,7 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
   sync();
   // ---- one pass over A = Adiv + Bt Bt^T (lower), V = Ct Bt^T, Sc = Ct Ct^T (lower) ----
   const double cdiv = nu / (d * adet);
+  const double cstab = nu * 6.0 / adet;   // k = 1 (d = 3): div phi_f = 1/|T|, |T| = |det J| / 6
   const int PA = nA * (nA + 1) / 2, PV = ncc * nA, PS = ncc * (ncc + 1) / 2;
   for (int q = lane; q < PA + PV + PS; q += nl) {
     const double *a, *b;
@@ -341,6 +390,7 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
       b = w.Bt + j * rs;
       out = w.A + i * nA + j;
       if (i < nu_) add = cdiv * t.Adiv[i * nu_ + j];
+      else if (LO && is_rot_dof(s, i) && is_rot_dof(s, j)) add = cstab;   // nu (div phi_f, div phi_g)_T
     } else if (q < PA + PV) {
       const int qq = q - PA, i = qq / nA, j = qq - i * nA;
       a = w.Ct + i * rs;
@@ -380,13 +430,21 @@ __host__ __device__ inline void condense_element(const ElemSizes& s, const ElemT
     packed_ij(q, i, j);
     double v = w.A[i * nA + j];
     for (int p = 0; p < ncc; ++p) v -= w.V[p * nA + i] * w.V[p * nA + j];
-    const double si = (i < nfd) ? (double)sgn[i / s.nF] : 1.0;
-    const double sj = (j < nfd) ? (double)sgn[j / s.nF] : 1.0;
+    const double si = (i < nfd) ? (double)sgn[i / s.nF] : ((LO && is_rot_dof(s, i)) ? (double)sgn[(i - nu_) / s.nhF] : 1.0);
+    const double sj = (j < nfd) ? (double)sgn[j / s.nF] : ((LO && is_rot_dof(s, j)) ? (double)sgn[(j - nu_) / s.nhF] : 1.0);
     v *= si * sj;
     w.A[i * nA + j] = v;
     w.A[j * nA + i] = v;
   }
   sync();
+}
+
+template <class Sync>
+__host__ __device__ inline void condense_element(const ElemSizes& s, const ElemTables& t, const double* X,
+                                                 const int* sgn, double nu, ElemWork w, int lane, int nl,
+                                                 Sync sync) {
+  if (s.lowest) condense_element_t<true>(s, t, X, sgn, nu, w, lane, nl, sync);
+  else condense_element_t<false>(s, t, X, sgn, nu, w, lane, nl, sync);
 }
 
 // Local stress recovery (eq. projection): after condense_element for the same element, the
@@ -475,7 +533,7 @@ __host__ __device__ inline void recover_element(const ElemSizes& s, ElemWork w, 
           for (int bb = 0; bb < d; ++bb) v += Ji[aa * d + i] * E[aa * d + bb] * J[j * d + bb];
         out[(q * d + i) * d + j] = v;
       }
-    if (out_w) {
+    if (out_w && !s.lowest) {
       const double sc = -1.0 / (cB * w.geo[100]);
       double Wm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
       for (int r = 0; r < s.n_wskew; ++r)

@@ -59,7 +59,8 @@ struct BlockSync {
 };
 
 // Condensation of element T by the whole block (a1-a4 except D_F), workspace at base.
-template <class R>
+// LO: 0 = k >= 2, 1 = lowest-order variant, -1 = decided per element from s.lowest.
+template <class R, int LO>
 __device__ __forceinline__ void condense_one(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu,
                                              const KOp& K, R* Fs, R* G, R* Aoi, double* base, int64_t T) {
   const int lane = threadIdx.x, nl = blockDim.x;
@@ -70,7 +71,7 @@ __device__ __forceinline__ void condense_one(const ElemSizes& s, const DevTables
   double* Adt = Xs + 24;                                   // staging (FP64)
   double* Gt = Adt + s.n_c * s.n_c;
   double* Ait = Gt + s.n_bub * s.n_c;
-  ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat};
+  ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat, t.Wmom};
   const int d = s.d;
   if (lane < (d + 1) * d) {
     int v = lane / d, a = lane % d;
@@ -78,7 +79,9 @@ __device__ __forceinline__ void condense_one(const ElemSizes& s, const DevTables
   }
   if (lane <= d) sg[lane] = m.signs[T * (d + 1) + lane];
   __syncthreads();
-  condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
+  if constexpr (LO == 0) condense_element_t<false>(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
+  else if constexpr (LO == 1) condense_element_t<true>(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
+  else condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
   const int nA = s.n_A;
   if (K.AT) {  // full A_T (FP64, symmetric: row-major = column-major)
     double* out = K.AT + T * (int64_t)nA * nA;
@@ -115,12 +118,12 @@ __device__ __forceinline__ void condense_one(const ElemSizes& s, const DevTables
 
 // One thread block per element (grid-stride).  Workspace in dynamic shared memory when
 // it fits, else in a global scratch slot per resident block.
-template <class R, bool SMEM>
+template <class R, bool SMEM, int LO>
 __global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, KOp K, R* Fs,
                                                   R* G, R* Aoi, double* gscratch, int64_t slot_doubles) {
   extern __shared__ double smem[];
   double* base = SMEM ? smem : gscratch + (int64_t)blockIdx.x * slot_doubles;
-  for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) condense_one<R>(s, t, m, nu, K, Fs, G, Aoi, base, T);
+  for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) condense_one<R, LO>(s, t, m, nu, K, Fs, G, Aoi, base, T);
 }
 
 // Several problems (any d, k) in one persistent launch: the blocks walk the concatenated element
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(256) k_condense_batch(const CondenseItem<R>* _
   for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
     while (p + 1 < nitems && items[p + 1].first <= g) ++p;   // g increases: the problem index only grows
     const CondenseItem<R>& it = items[p];
-    condense_one<R>(it.s, it.t, it.m, it.nu, it.K, it.Fs, it.G, it.Aoi, base, g - it.first);
+    condense_one<R, -1>(it.s, it.t, it.m, it.nu, it.K, it.Fs, it.G, it.Aoi, base, g - it.first);
   }
 }
 
@@ -147,9 +150,20 @@ static int64_t condense_slot_doubles(const ElemSizes& s) {
 
 static int condense_threads(const ElemSizes& s) { return s.d == 2 ? 128 : 256; }
 
+template <class R, int LO>
+static cudaError_t launch_condense_t(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K,
+                                     R* Fs, R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st);
+
 template <class R>
 cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K, R* Fs,
                             R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st) {
+  return s.lowest ? launch_condense_t<R, 1>(s, t, m, nu, K, Fs, G, Aoi, scratch, scratch_doubles, st)
+                  : launch_condense_t<R, 0>(s, t, m, nu, K, Fs, G, Aoi, scratch, scratch_doubles, st);
+}
+
+template <class R, int LO>
+static cudaError_t launch_condense_t(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K,
+                                     R* Fs, R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st) {
   const int64_t slot = condense_slot_doubles(s);
   int dev = 0, nsm = 0, maxsm = 0;
   cudaGetDevice(&dev);
@@ -161,19 +175,19 @@ cudaError_t launch_condense(const ElemSizes& s, const DevTables& t, const DevMes
   if (bytes <= maxsm) {
     size_t sm = (size_t)bytes;
     // the opt-in maximum, never lowered: other threads may launch this kernel with other sizes
-    cudaFuncSetAttribute(k_condense<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+    cudaFuncSetAttribute(k_condense<R, true, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense<R, true>, threads, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_condense<R, true, LO>, threads, sm);
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)nsm * per_sm;
     if (blocks > m.ne) blocks = m.ne;
-    k_condense<R, true><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, nu, K, Fs, G, Aoi, nullptr, slot);
+    k_condense<R, true, LO><<<(unsigned)blocks, threads, sm, st>>>(s, t, m, nu, K, Fs, G, Aoi, nullptr, slot);
     note_launch();
   } else {
     int64_t blocks = scratch_doubles / slot;
     if (blocks < 1) return cudaErrorMemoryAllocation;
     if (blocks > m.ne) blocks = m.ne;
-    k_condense<R, false><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, nu, K, Fs, G, Aoi, scratch, slot);
+    k_condense<R, false, LO><<<(unsigned)blocks, threads, 0, st>>>(s, t, m, nu, K, Fs, G, Aoi, scratch, slot);
     note_launch();
   }
   {
@@ -786,7 +800,7 @@ __global__ void __launch_bounds__(256) k_recover(ElemSizes s, DevTables t, DevMe
   int* sg = (int*)(Xs + 16);
   double* a = Xs + 24;
   double* wk = a + nA;
-  ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat};
+  ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat, t.Wmom};
   const int64_t per = (int64_t)nq * d * d;
   for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) {
     if (lane < (d + 1) * d) {
@@ -798,7 +812,8 @@ __global__ void __launch_bounds__(256) k_recover(ElemSizes s, DevTables t, DevMe
     condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
     for (int i = lane; i < nA; i += nl) {
       const int64_t g = local_to_global(s, L, m.elem_rank + T * (d + 1), T, i);
-      a[i] = g < 0 ? 0.0 : x[g] * (i < nfd ? (double)sg[i / s.nF] : 1.0);
+      const double sgi = i < nfd ? (double)sg[i / s.nF] : (is_rot_dof(s, i) ? (double)sg[(i - s.n_u) / s.nhF] : 1.0);
+      a[i] = g < 0 ? 0.0 : x[g] * sgi;
     }
     __syncthreads();
     recover_element(s, w, Xs, a, nq, psi, wk, sig + T * per, om ? om + T * per : nullptr, lane, nl, BlockSync());

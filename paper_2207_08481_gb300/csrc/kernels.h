@@ -124,6 +124,7 @@ struct DevTables {
   const double* Ccon;
   const double* Adiv;
   const double* nhat;
+  const double* Wmom;      // k = 1: [d+1][d][nk]
   const double* Bp;        // [n_p][n_u]
   const float* Bp_hi;      // Bp split into float pairs (Bp = hi + lo to ~2^-48)
   const float* Bp_lo;

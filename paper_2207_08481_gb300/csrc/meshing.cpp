@@ -369,6 +369,14 @@ std::vector<double> embedding_blocks(const HostMesh& m, const RefTables& T) {
         for (int mm = 0; mm < d - 1; ++mm)
           for (int j = 0; j < s.nFm1; ++j)
             B[(s.nF + mm * s.nFm1 + j) * d * d + col] = ed[mm][a] * T.Ilam[wv * s.nF + j];
+        if (s.lowest) {
+          // k = 1 (Sec. 7): third component curl(ubar), as its flux through F along n_F.  By Stokes'
+          // theorem int_F curl(lambda_w e_a).n_F is the circulation of lambda_w e_a around the facet
+          // boundary w_0 -> w_1 -> w_2 (counter-clockwise about n_F = e_1 x e_2 / |e_1 x e_2|): with
+          // lambda_w linear on the edges it is (x_{w+1} - x_{w-1})_a / 2, indices mod 3.
+          const int wn = w[(wv + 1) % 3], wp = w[(wv + 2) % 3];
+          B[(s.nF + s.ntF) * d * d + col] = 0.5 * (m.coords[wn * d + a] - m.coords[wp * d + a]);
+        }
       }
   }
   return out;

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_condense_noalloc(ElemSizes s, DevTables
   ElemWork w = elem_work_carve(s, base);
   double* Xs = base + elem_work_doubles(s);
   int* sg = (int*)(Xs + 16);
-  ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat};
+  ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat, t.Wmom};
   const int nA2 = s.n_A * s.n_A;
   for (int64_t e = blockIdx.x; e < count; e += gridDim.x) {
     const int64_t T = T0 + e;

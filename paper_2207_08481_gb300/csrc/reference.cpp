@@ -25,7 +25,9 @@ Sizes make_sizes(int d, int k) {
   s.nFm1 = n_poly(d - 1, k - 1);
   s.n_full = d * s.nk;
   s.n_bub = s.n_full - (d + 1) * s.nF;
-  s.nhF = (d - 1) * s.nFm1;
+  s.lowest = (k == 1) ? 1 : 0;
+  s.ntF = (d - 1) * s.nFm1;
+  s.nhF = s.ntF + s.lowest;
   s.n_hat = (d + 1) * s.nhF;
   s.n_u = s.n_full;
   s.n_A = s.n_u + s.n_hat;
@@ -34,7 +36,7 @@ Sizes make_sizes(int d, int k) {
   s.n_raw = s.n_s0 * s.nk;
   s.n_con = (d + 1) * (d - 1) * (s.nF - s.nFm1);
   s.n_wskew = d * (d - 1) / 2;
-  s.n_w = s.n_wskew * s.n_p;
+  s.n_w = s.lowest ? 0 : s.n_wskew * s.n_p;
   s.n_cc = s.n_con + s.n_w;
   s.mF = s.nF + s.nhF;
   s.n_c = (d + 1) * s.mF;
@@ -338,7 +340,7 @@ void interior_tests(int d, int k, const double* x, std::vector<double>& out /* [
 }  // namespace
 
 RefTables build_reference(int d, int k) {
-  if (d < 2 || d > 3 || k < 2 || k > 8) throw std::runtime_error("unsupported (d, k)");
+  if (d < 2 || d > 3 || k < 1 || k > 8 || (k == 1 && d != 3)) throw std::runtime_error("unsupported (d, k)");
   RefTables T;
   Sizes s = make_sizes(d, k);
   T.s = s;
@@ -540,6 +542,17 @@ RefTables build_reference(int d, int k) {
       }
     }
     con_row += (d - 1) * (int)top.size();
+  }
+
+  // ---- k = 1: moments of the rotation flux functions (x - x_f) / (d |T|) against psi_i ----
+  if (s.lowest) {
+    T.Wmom.assign((d + 1) * d * nk, 0.0);
+    for (int q = 0; q < nq; ++q) {
+      dubiner_eval(d, k, &xv[q * d], psi.data(), nullptr);
+      for (int f = 0; f <= d; ++f)
+        for (int c = 0; c < d; ++c)
+          for (int i = 0; i < nk; ++i) T.Wmom[(f * d + c) * nk + i] += wv[q] * psi[i] * (xv[q * d + c] - rg.V[f][c]);
+    }
   }
 
   // ---- load vector quadrature ----

@@ -12,7 +12,10 @@
 //     kept as linear constraints, eliminated with the rotation constraints by
 //     Lagrange multipliers inside the condensation;
 //   * W_h(T) = P^{k-1}(T, skew), Vhat_h on facets q_j e_m (edge vectors e_m),
-//     Q_h = P^{k-1}(T).
+//     Q_h = P^{k-1}(T);
+//   * lowest-order variant (k = 1, Sec. 7, d = 3): W_h in H(div), P^0(T, R^3) + x P^0(T),
+//     one flux dof per facet stored behind that facet's two tangential Vhat_h dofs and kept
+//     after condensation; the constraint set is then the nt conditions alone.
 #pragma once
 #include <cstdint>
 #include <vector>
@@ -28,14 +31,16 @@ struct Sizes {
   int nFm1;      // dim P^{k-1}(F)
   int n_full;    // d * nk = n_u
   int n_bub;     // interior (bubble) BDM functions
-  int nhF;       // (d-1) * nFm1 tangential facet dofs per facet
+  int ntF;       // (d-1) * nFm1 tangential facet dofs per facet
+  int nhF;       // Vhat_h dofs per facet: ntF, plus the rotation flux for the lowest-order variant
+  int lowest;    // 1 for the lowest-order variant (k = 1, Sec. 7; d = 3)
   int n_hat;     // (d+1) * nhF
   int n_u, n_A;  // n_A = n_u + n_hat
   int n_p;       // dim P^{k-1}(T)
   int n_s0;      // d*d - 1 trace-free units
   int n_raw;     // n_s0 * nk raw stress functions
   int n_con;     // nt constraints
-  int n_w;       // rotation functions (d(d-1)/2 * n_p)
+  int n_w;       // element-local rotation functions (d(d-1)/2 * n_p; 0 for k = 1)
   int n_cc;      // n_con + n_w
   int n_c;       // coupling dofs per element: (d+1)*(nF + nhF)
   int mF;        // nF + nhF dofs per facet
@@ -54,6 +59,7 @@ struct RefTables {
   std::vector<double> Bp;     // [n_p][n_u]      int div phi_j psi_i
   std::vector<double> Mu;     // [d][d][n_u][n_u] int phi_{i,a} phi_{j,b}
   std::vector<double> nhat;   // [d+1][d] unit outward reference normals
+  std::vector<double> Wmom;   // k = 1: [d+1][d][nk]  int psi_i (xhat_c - xhat_f,c), xhat_f = vertex f
   // ---- load vector (f given at quadrature points) ----
   int nq_load;
   std::vector<double> xq_load;   // [nq][d] reference points
