@@ -23,5 +23,7 @@ The oracle is a plain, slow, literal restatement of arXiv 2207.08481:
                     facet-block Gauss-Seidel smoother, the multiplicative ASP of
                     Sec. 5.2 and the block preconditioner of eq. (mhatinvfactor).
 * ``krylov``        textbook preconditioned MinRes.
+* ``hdg``           the HDG norm eq. (nhdg_eps) on one element and the constant gamma of
+                    Corollary schur_SPD (the single-element experiment the paper mentions).
 * ``manufactured``  manufactured solutions and their right-hand sides.
 """
