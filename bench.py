@@ -233,6 +233,7 @@ def run_gpu(args):
 
     # ---------------- several degrees in one condensation launch (3D, 16^3 x 6 tets, k = 2, 3, 4)
     multi = _multi_degree(args, torch, mcs) if (rank == 0 and not args.no_multi) else None
+    smoothing = _smoothing(args, torch, mcs) if (rank == 0 and not args.no_multi) else None
 
     # ---------------- serving: Poisson trace of mixed requests through the continuous-batching loop
     serving = None
@@ -284,10 +285,47 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "serving": serving,
         "multi_degree": multi,
+        "asp_smoothing": smoothing,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _random_solve(h, torch, seed):
+    """One warm-up and one timed mcs_solve for F = M_u c, c ~ N(0, 1) on the velocity dofs (seeded)."""
+    s = h.sizes
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    c = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
+    c[:s.off_h] = torch.randn(s.off_h, dtype=torch.float64, device="cuda", generator=g)
+    F = torch.zeros_like(c)
+    h.mass_velocity(c, F)
+    x = torch.zeros_like(F)
+    h.solve(F, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x.zero_()
+    e0.record()
+    info = h.solve(F, x)
+    e1.record()
+    torch.cuda.synchronize()
+    return round(e0.elapsed_time(e1), 2), info
+
+
+def _smoothing(args, torch, mcs):
+    """Multiplicative against additive ASP (Table ST_smoothing re-run on the c3 mesh: 3D 32^3 x 6
+    tetrahedra, k = 2, nu = 1, mixed form, random F = M_u c, seeded): iterations and solve time."""
+    out = {"config": "3D unit cube, 32^3 cells x 6 = 196,608 tetrahedra, k = 2, nu = 1, mixed form, "
+                     "random F = M_u c (c ~ N(0,1)), rel. preconditioned residual 1e-8"}
+    for name, asp in (("multiplicative", 0), ("additive", 1)):
+        h = mcs.Handle.structured(3, 32, 2, 1.0, precision=mcs.MCS_MIXED, asp=asp, maxit=4000)
+        h.condense()
+        ms, info = _random_solve(h, torch, 7)
+        out[name] = {"ms": ms, "iterations": info.iterations, "rel_res": info.rel_res_precond,
+                     "ms_per_iteration": round(ms / max(info.iterations, 1), 3)}
+        h.close()
+    return out
 
 
 def _multi_degree(args, torch, mcs):
@@ -317,23 +355,8 @@ def _multi_degree(args, torch, mcs):
     mcs.condense_batch(hs)
     solves = {}
     for k, h in zip(ks, hs):
-        s = h.sizes
-        g = torch.Generator(device="cuda")
-        g.manual_seed(100 + k)
-        c = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
-        c[:s.off_h] = torch.randn(s.off_h, dtype=torch.float64, device="cuda", generator=g)
-        F = torch.zeros_like(c)
-        h.mass_velocity(c, F)
-        x = torch.zeros_like(F)
-        h.solve(F, x)
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        x.zero_()
-        e0.record()
-        info = h.solve(F, x)
-        e1.record()
-        torch.cuda.synchronize()
-        solves[f"k={k}"] = {"ndof": int(s.ndof), "ms": round(e0.elapsed_time(e1), 2), "iterations": info.iterations,
+        ms, info = _random_solve(h, torch, 100 + k)
+        solves[f"k={k}"] = {"ndof": int(h.sizes.ndof), "ms": ms, "iterations": info.iterations,
                             "rel_res": info.rel_res_precond}
     for h in hs:
         h.close()
@@ -443,7 +466,7 @@ def main():
                     help="requests of the serving trace (2000 = the full trace; 0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-slots", type=int, default=4)
-    ap.add_argument("--no-multi", action="store_true", help="skip the mixed-degree batch")
+    ap.add_argument("--no-multi", action="store_true", help="skip the mixed-degree batch and the ASP comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -22,6 +22,9 @@
                    E^d C^{-1} E^d^T on the new residual, s adjoint sweeps;
                    wrapped by the factorization eq. (factorSsigma) into
                    Ahat^ext^{-1} (bubble elimination and back substitution).
+* ``FullASP``      the ASP of Theorem aux_pc on the full velocity block (bubbles not
+                   condensed): overlapping facet blocks with the neighbours' bubbles,
+                   additive or multiplicative (colour-ordered block Gauss-Seidel).
 * ``Khat_inv``     block preconditioner eq. (mhatinvfactor) with Ahat^{-1} in
                    both factors (reading R3) and Shat_p = M_p = nu^{-1}(p, q);
                    implemented with two applications of Ahat^{-1}.
@@ -277,6 +280,68 @@ class ASP:
         x = xc
         x[om] = xo
         x[D.off_p:] = 0.0
+        return x
+
+
+class FullASP:
+    """ASP on the full (sigma, omega-condensed, bubble-uncondensed) velocity block A (Theorem aux_pc):
+    one overlapping block per interior facet F holding F's dofs (BDM facet moments, uhat) and the
+    bubbles of both elements of F; with E (all rows, bubbles included) and C.  Additive:
+    M^{-1} + E C^{-1} E^T with M the overlapping block Jacobi; multiplicative: the blocks swept colour
+    by colour (facets of one colour share no element, so their blocks are disjoint), the coarse
+    correction on the new residual, and the adjoint sweep (Sec. 5.2)."""
+
+    def __init__(self, D: system.Discretization, AT: np.ndarray, gmg: GMG,
+                 smooth: int = 2, multiplicative: bool = True):
+        self.D = D
+        m = D.mesh
+        sz = D.sz
+        n = D.ndof
+        am = D.a_map
+        self.A = system.assemble(am, am, AT, (n, n)).tocsr()
+        nF, nhF, nb = sz["nF"], sz["n_hatF"], sz["n_bub"]
+        ints = np.nonzero(m.interior)[0]
+        blocks = []
+        for r, F in enumerate(ints):
+            own = [r * nF + j for j in range(nF)] + [D.off_h + r * nhF + j for j in range(nhF)]
+            bub = [D.off_o + T * nb + j for T in m.facet_elems[F] for j in range(nb)]
+            blocks.append(np.array(own + bub, dtype=np.int64))
+        self.blocks = blocks
+        self.Dinv = [np.linalg.inv(self.A[b][:, b].toarray()) for b in blocks]
+        self.colour = meshmod.colouring(m)
+        self.ncol = int(self.colour.max()) + 1 if len(blocks) else 0
+        self.vel = np.arange(D.off_p)
+        E = embedding(D)
+        mask = np.zeros(n)
+        mask[self.vel] = 1.0
+        self.E = sp.diags(mask) @ E
+        self.gmg = gmg
+        self.smooth = smooth
+        self.multiplicative = multiplicative
+
+    def _sweep(self, x, b, order):
+        for c in order:
+            r = b - self.A @ x
+            for i in np.nonzero(self.colour == c)[0]:
+                blk = self.blocks[i]
+                x[blk] += self.Dinv[i] @ r[blk]
+        return x
+
+    def apply(self, r: np.ndarray) -> np.ndarray:
+        """Ahat^{-1} r on the velocity part of the condensed layout (p part ignored, zero on output)."""
+        b = r.copy()
+        b[self.D.off_p:] = 0.0
+        x = np.zeros_like(b)
+        if not self.multiplicative:
+            for blk, Di in zip(self.blocks, self.Dinv):
+                x[blk] += Di @ b[blk]
+            return x + self.E @ self.gmg.vcycle(self.E.T @ b)
+        for _ in range(self.smooth):
+            x = self._sweep(x, b, range(self.ncol))
+        x = x + self.E @ self.gmg.vcycle(self.E.T @ (b - self.A @ x))
+        for _ in range(self.smooth):
+            x = self._sweep(x, b, range(self.ncol - 1, -1, -1))
+        x[self.D.off_p:] = 0.0
         return x
 
 
