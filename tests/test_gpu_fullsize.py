@@ -16,7 +16,7 @@ if not torch.cuda.is_available():
 import workloads  # noqa: E402
 from oracle import fem, manufactured, mesh, system  # noqa: E402
 
-CASES = {"c2": (2, 256, 3, 1e-2, 5), "c3": (3, 32, 2, 1.0, 4)}
+CASES = {"c2": (2, 256, 3, 1e-2, 5), "c3": (3, 32, 2, 1.0, 4), "c4k1": (3, 16, 1, 1.0, -1)}
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +40,7 @@ def _coupling_perm(sz, n_c, mF):
     return np.array(perm), o
 
 
-@pytest.mark.parametrize("name", ["c2", "c3"])
+@pytest.mark.parametrize("name", ["c2", "c3", "c4k1"])
 def test_fullsize_numbering_and_sampled_operators(mcs, name):
     d, N, k, nu, lev = CASES[name]
     h = mcs.Handle.structured(d, N, k, nu, precision=mcs.MCS_MIXED, gmg_levels=lev)
@@ -70,7 +70,11 @@ def test_fullsize_numbering_and_sampled_operators(mcs, name):
         Ado = Ad_o[i][perm][:, perm]
         rows = ~np.isnan(Ad[0][:, 0])
         assert np.abs(Ad[0][rows] - Ado[rows]).max() < 2e-6 * np.abs(Ado).max()   # FP32 copies
-        assert np.abs(G[0] - G_o[i][:, perm]).max() < 2e-6 * np.abs(G_o[i]).max()
+        if sz["n_bub"]:
+            assert np.abs(G[0] - G_o[i][:, perm]).max() < 2e-6 * np.abs(G_o[i]).max()
+    if not sz["n_bub"]:     # k = 1: no bubbles, so no load entry is owned by a single element
+        h.close()
+        return
     # load vector: bubble entries (owned by one element) of the sampled elements
     s = h.sizes
     xq = torch.zeros((s.ne * s.nq_load, d), dtype=torch.float64, device="cuda")
@@ -103,6 +107,29 @@ def test_fullsize_c2_solve_properties(mcs):
     assert info.status == 0 and info.rel_res_precond <= 1e-8 and info.iterations < 120
     p0 = x[s.off_p::s.n_p].cpu().numpy()          # constant pressure mode per element (equal areas)
     assert abs(p0.sum()) <= 1e-10 * np.abs(p0).sum()
+    r = torch.zeros_like(F)
+    h.residual(F, x, r)
+    assert float(torch.linalg.norm(r) / torch.linalg.norm(F)) < 1e-4
+    h.close()
+
+
+def test_fullsize_c4_lowest_order_solve_properties(mcs):
+    """The k = 1 member of c4 as bench.py runs it (3D 16^3 x 6, mixed form, default hierarchy):
+    converged, zero-mean pressure, small true residual; the rotation fluxes are part of x."""
+    d, N, k, nu, lev = CASES["c4k1"]
+    h = mcs.Handle.structured(d, N, k, nu, precision=mcs.MCS_MIXED, maxit=8000)
+    h.condense()
+    s = h.sizes
+    assert (s.nhF, s.mF, s.n_bub) == (3, 6, 0)
+    xq = torch.zeros((s.ne * s.nq_load, d), dtype=torch.float64, device="cuda")
+    h.load_points(xq)
+    F = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
+    h.load_vector(workloads.manufactured_f(d, nu, xq), F)
+    x = torch.zeros_like(F)
+    info = h.solve(F, x)
+    assert info.status == 0 and info.rel_res_precond <= 1e-8
+    p = x[s.off_p:].cpu().numpy()                 # P^0 pressure, equal volumes
+    assert abs(p.sum()) <= 1e-10 * np.abs(p).sum()
     r = torch.zeros_like(F)
     h.residual(F, x, r)
     assert float(torch.linalg.norm(r) / torch.linalg.norm(F)) < 1e-4
