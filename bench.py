@@ -358,6 +358,13 @@ def _multi_degree(args, torch, mcs):
         ms, info = _random_solve(h, torch, 100 + k)
         solves[f"k={k}"] = {"ndof": int(h.sizes.ndof), "ms": ms, "iterations": info.iterations,
                             "rel_res": info.rel_res_precond}
+    # k = 1 with the stabilisation weight nu h_T^2 (lo_stab = 1) instead of nu: same right-hand side
+    h1 = mcs.Handle.structured(3, 16, 1, 1.0, precision=mcs.MCS_MIXED, maxit=8000, lo_stab=1)
+    h1.condense()
+    ms, info = _random_solve(h1, torch, 101)
+    solves["k=1, weight nu h_T^2"] = {"ndof": int(h1.sizes.ndof), "ms": ms, "iterations": info.iterations,
+                                      "rel_res": info.rel_res_precond}
+    h1.close()
     for h in hs:
         h.close()
     return {"config": "3D unit cube, 16^3 cells x 6 = 24,576 tetrahedra each, k = 1 (lowest-order variant), 2, 3, 4, "

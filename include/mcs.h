@@ -93,6 +93,9 @@ typedef struct {
   int asp;            /* auxiliary-space preconditioner for the condensed velocity block (Sec. 6.1):
                          0 multiplicative (smoother, coarse correction, adjoint smoother; default),
                          1 additive (facet-block Jacobi plus E^d C^{-1} E^d^T) */
+  int lo_stab;        /* k = 1 only (Sec. 7), coefficient of (div omega, div eta)_T: 0 nu (default),
+                         1 nu h_T^2 with h_T the element diameter (keeps the iteration count
+                         bounded under refinement; see Table ST_ws) */
 } mcs_options;
 
 typedef struct {

@@ -349,7 +349,18 @@ def kappa(v: np.ndarray) -> np.ndarray:
     return 0.5 * out
 
 
-def element_matrices(X, signs, k, nu):
+def stabilisation_weight(X: np.ndarray, nu: float, lo_stab: int) -> np.ndarray:
+    """Coefficient of (div omega, div eta)_T for k = 1, per element [E]: lo_stab = 0 takes nu (the
+    printed form at nu = 1, reading R21(d)); lo_stab = 1 takes nu h_T^2 with h_T the element diameter
+    (longest edge), which keeps the term within the section's norm (reading R21(d'))."""
+    if lo_stab == 0:
+        return np.full(X.shape[0], nu)
+    diam2 = np.max([np.sum((X[:, a] - X[:, b]) ** 2, axis=1)
+                    for a in range(X.shape[1]) for b in range(a + 1, X.shape[1])], axis=0)
+    return nu * diam2
+
+
+def element_matrices(X, signs, k, nu, lo_stab: int = 0):
     """Local blocks of eq. (bigfemSPmat) on every element of the batch.
 
     Returns dict of arrays [E, rows, cols]:
@@ -378,13 +389,15 @@ def element_matrices(X, signs, k, nu):
     if D.divW is not None:
         # k = 1 (Sec. 7): the rotation dofs are the third entry of each facet's hat block; they
         # couple to sigma through (phi^sigma, kappa(phi^omega))_T and carry the stabilisation
-        # nu (div omega, div eta)_T (reading R21: coefficient nu)
+        # c_T (div omega, div eta)_T with c_T = stabilisation_weight (reading R21)
         nhF = D.fH.shape[3] // (d + 1)
         rows = [f * nhF + nhF - 1 for f in range(d + 1)]
         out["Bw"] = np.zeros((X.shape[0], 0, D.S.shape[2]))
         out["Bh"][:, rows, :] = np.einsum("eq,eqjab,eqfab->efj", D.wq, D.S, D.W)
         Sh = np.zeros((X.shape[0], len(out["Bh"][0]), len(out["Bh"][0])))
-        Sh[:, np.ix_(rows, rows)[0], np.ix_(rows, rows)[1]] = nu * np.einsum("eq,eqf,eqg->efg", D.wq, D.divW, D.divW)
+        cT = stabilisation_weight(X, nu, lo_stab)
+        Sh[:, np.ix_(rows, rows)[0], np.ix_(rows, rows)[1]] = \
+            cT[:, None, None] * np.einsum("eq,eqf,eqg->efg", D.wq, D.divW, D.divW)
         out["Shat"] = Sh
     out["Adiv"] = nu / d * np.einsum("eq,eqi,eqj->eij", D.wq, D.divU, D.divU)
     out["Bp"] = -np.einsum("eq,eqj,eqi->eij", D.wq, D.divU, D.P)

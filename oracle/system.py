@@ -96,13 +96,14 @@ def dof_maps(m: meshmod.Mesh, k: int):
     return sz, u_map, h_map, p_map, n_dd, n_oo, n_hat, n_pres
 
 
-def discretize(m: meshmod.Mesh, k: int, nu: float, batch: int = 2048) -> Discretization:
+def discretize(m: meshmod.Mesh, k: int, nu: float, batch: int = 2048, lo_stab: int = 0) -> Discretization:
+    """lo_stab: weight of the k = 1 stabilisation (fem.stabilisation_weight)."""
     sz, u_map, h_map, p_map, n_dd, n_oo, n_hat, n_pres = dof_maps(m, k)
     D = Discretization(m, k, nu, sz, u_map, h_map, p_map, n_dd, n_oo, n_hat, n_pres)
     X = m.coords[m.elems]
     parts = []
     for s in range(0, X.shape[0], batch):
-        parts.append(fem.element_matrices(X[s:s + batch], m.signs[s:s + batch], k, nu))
+        parts.append(fem.element_matrices(X[s:s + batch], m.signs[s:s + batch], k, nu, lo_stab))
     D.mats = {key: np.concatenate([p[key] for p in parts]) for key in parts[0]}
     return D
 

@@ -51,7 +51,7 @@ ElemSizes elem_sizes(const Sizes& s) {
   e.d = s.d; e.k = s.k; e.nk = s.nk; e.nF = s.nF; e.nFm1 = s.nFm1; e.n_u = s.n_u; e.n_A = s.n_A;
   e.n_hat = s.n_hat; e.nhF = s.nhF; e.n_p = s.n_p; e.n_s0 = s.n_s0; e.n_raw = s.n_raw; e.n_con = s.n_con;
   e.n_w = s.n_w; e.n_wskew = s.n_wskew; e.n_cc = s.n_cc; e.n_bub = s.n_bub; e.n_c = s.n_c; e.mF = s.mF;
-  e.ntF = s.ntF; e.lowest = s.lowest;
+  e.ntF = s.ntF; e.lowest = s.lowest; e.lo_stab = 0;
   return e;
 }
 
@@ -66,6 +66,7 @@ void validate_options(const mcs_options& o) {
   if (!(o.rtol > 0) || o.maxit < 1) throw McsError(MCS_ERR_INVALID_ARG, "rtol/maxit");
   if (o.residual_dd < -1 || o.residual_dd > 1) throw McsError(MCS_ERR_INVALID_ARG, "residual_dd");
   if (o.asp < 0 || o.asp > 1) throw McsError(MCS_ERR_INVALID_ARG, "asp");
+  if (o.lo_stab < 0 || o.lo_stab > 1) throw McsError(MCS_ERR_INVALID_ARG, "lo_stab");
 }
 
 template <class R>
@@ -211,6 +212,7 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   h->sz = h->ref.s;
   if (h->sz.n_bub > 64) throw McsError(MCS_ERR_UNSUPPORTED, "more than 64 bubble functions per element");
   h->es = elem_sizes(h->sz);
+  h->es.lo_stab = h->sz.lowest ? h->opt.lo_stab : 0;
   const Sizes& s = h->sz;
   // layout
   Layout& L = h->L;
@@ -495,6 +497,7 @@ int mcs_default_options(mcs_options* o) {
   o->inner_rtol = 1e-5;
   o->residual_dd = -1;
   o->asp = 0;
+  o->lo_stab = 0;
   return MCS_OK;
 }
 

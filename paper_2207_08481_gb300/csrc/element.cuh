@@ -38,6 +38,7 @@ struct ElemSizes {
   int d, k, nk, nF, nFm1, n_u, n_A, n_hat, nhF, n_p, n_s0, n_raw, n_con, n_w, n_wskew, n_cc;
   int n_bub, n_c, mF;
   int ntF, lowest;   // tangential Vhat_h dofs per facet; 1 for the lowest-order variant (k = 1)
+  int lo_stab;       // k = 1: coefficient of (div omega, div eta)_T is nu (0) or nu h_T^2 (1)
 };
 
 // Local index i of A_T is the rotation flux dof of a facet (lowest-order variant only).
@@ -377,7 +378,18 @@ __host__ __device__ inline void condense_element_t(const ElemSizes& s, const Ele
   sync();
   // ---- one pass over A = Adiv + Bt Bt^T (lower), V = Ct Bt^T, Sc = Ct Ct^T (lower) ----
   const double cdiv = nu / (d * adet);
-  const double cstab = nu * 6.0 / adet;   // k = 1 (d = 3): div phi_f = 1/|T|, |T| = |det J| / 6
+  // k = 1 (d = 3): div phi_f = 1/|T|, |T| = |det J| / 6; coefficient nu or nu h_T^2 (h_T: longest edge)
+  double cstab = nu * 6.0 / adet;
+  if (LO && s.lo_stab) {
+    double h2 = 0.0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        double e2 = 0.0;
+        for (int c = 0; c < 3; ++c) e2 += (X[b * 3 + c] - X[a * 3 + c]) * (X[b * 3 + c] - X[a * 3 + c]);
+        h2 = e2 > h2 ? e2 : h2;
+      }
+    cstab *= h2;
+  }
   const int PA = nA * (nA + 1) / 2, PV = ncc * nA, PS = ncc * (ncc + 1) / 2;
   for (int q = lane; q < PA + PV + PS; q += nl) {
     const double *a, *b;

@@ -208,3 +208,28 @@ def test_condense_batch_with_lowest_order(mcs, prec):
         assert torch.equal(za, zb)
     for hh in ref + bat:
         hh.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_h2_stabilisation_parity(mcs, prec, tol):
+    """lo_stab = 1: coefficient nu h_T^2 of (div omega, div eta)_T (reading R21(d')); A_T and the
+    solve against the oracle with the same weight."""
+    p = mcs.MCS_FP64 if prec == "fp64" else mcs.MCS_MIXED
+    N, nu = 4, 0.8
+    h = _handle(mcs, N, nu, precision=p, lo_stab=1, rtol=1e-13 if prec == "fp64" else 1e-12, maxit=4000)
+    D = system.discretize(mesh.structured(3, N), K, nu, lo_stab=1)
+    AT = system.condense(D)
+    P = h.element_matrices(0, AT.shape[0])
+    il = np.tril_indices(AT.shape[1])
+    ref = AT[:, il[0], il[1]]
+    assert (np.abs(P - ref).max(axis=1) / np.abs(ref).max(axis=1)).max() < (1e-12 if prec == "fp64" else 1e-13)
+    F = _rhs(h, nu)
+    x = torch.zeros_like(F)
+    info = h.solve(F, x, check=False)
+    xo = system.mean_zero_pressure(D, system.solve_condensed(D, F.cpu().numpy(), AT))
+    xg = x.cpu().numpy()
+    n = D.off_p
+    assert info.status == 0, (info.status, info.iterations)
+    assert np.linalg.norm(xg[:n] - xo[:n]) / np.linalg.norm(xo[:n]) < tol
+    assert np.linalg.norm(xg[n:] - xo[n:]) / np.linalg.norm(xo[n:]) < tol
+    h.close()

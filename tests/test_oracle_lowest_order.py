@@ -203,8 +203,8 @@ def test_rotation_coupling_mistakes_are_caught(monkeypatch, scale):
     energy identity of the embedding."""
     orig = fem.element_matrices
 
-    def bad(X, signs, k, nu):
-        out = orig(X, signs, k, nu)
+    def bad(X, signs, k, nu, *rest):
+        out = orig(X, signs, k, nu, *rest)
         out["Bh"][:, 2::3, :] *= scale
         return out
     monkeypatch.setattr(fem, "element_matrices", bad)
@@ -227,10 +227,41 @@ def test_dropped_stabilisation_is_caught(monkeypatch):
     """Without nu (div omega, div eta) the energy split of test_energy_identity_and_spd fails."""
     orig = fem.element_matrices
 
-    def bad(X, signs, k, nu):
-        out = orig(X, signs, k, nu)
+    def bad(X, signs, k, nu, *rest):
+        out = orig(X, signs, k, nu, *rest)
         out["Shat"] = np.zeros_like(out["Shat"])
         return out
     monkeypatch.setattr(fem, "element_matrices", bad)
     with pytest.raises(AssertionError):
         test_energy_identity_and_spd()
+
+
+def _asp_condition(N, lo_stab):
+    D = system.discretize(mesh.structured(3, N), 1, 1.0, lo_stab=lo_stab)
+    AT = system.condense(D)
+    asp = precond.ASP(D, AT, precond.GMG(3, N, 1, 1.0))
+    cd = np.concatenate([np.arange(D.n_dd), D.off_h + np.arange(D.n_hat)])
+    P = np.zeros((len(cd), len(cd)))
+    for j, g in enumerate(cd):
+        e = np.zeros(D.ndof)
+        e[g] = 1.0
+        P[:, j] = asp.apply_ad(e)[cd]
+    ev = np.sort(np.linalg.eigvals(P @ asp.Ad_glob.toarray()[np.ix_(cd, cd)]).real)
+    return ev[-1] / ev[0]
+
+
+def test_stabilisation_weight_and_conditioning():
+    """Reading R21(d): with the coefficient nu the ASP condition number (exact C) grows under
+    refinement like h^-2; with nu h_T^2 it levels off (Table ST_ws reports h-robust k = 1 iteration
+    counts).  Both weights keep E^T A E = Abar exact (div curl = 0)."""
+    r0 = _asp_condition(3, 0) / _asp_condition(2, 0)
+    r1 = _asp_condition(3, 1) / _asp_condition(2, 1)
+    assert r0 > 2.0 and r1 < 1.5
+    D = system.discretize(mesh.structured(3, 2), 1, NU, lo_stab=1)
+    A = system.condensed_system(D, system.condense(D))
+    E = precond.embedding(D)
+    Ab = precond.abar(D.mesh, NU).toarray()
+    assert np.abs((E.T @ A @ E).toarray() - Ab).max() < 1e-12 * np.abs(Ab).max()
+    X = D.mesh.coords[D.mesh.elems]
+    w = fem.stabilisation_weight(X, NU, 1)
+    assert np.allclose(w, NU * 3.0 / 4.0)            # Kuhn tetrahedra of the N = 2 cube: diameter sqrt(3)/2

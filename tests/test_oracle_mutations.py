@@ -58,8 +58,8 @@ def test_dropped_boundary_term_is_caught(monkeypatch):
     """Bu without -(sigma_nn, u_n)_dT."""
     orig = fem.element_matrices
 
-    def bad(X, signs, k, nu):
-        out = orig(X, signs, k, nu)
+    def bad(X, signs, k, nu, *rest):
+        out = orig(X, signs, k, nu, *rest)
         D = fem.element_data(X, signs, k)
         out["Bu"] = np.einsum("eq,eqja,eqia->eij", D.wq, D.divS, D.U)
         return out
