@@ -63,6 +63,10 @@ def test_invalid_arguments_are_reported_not_raised(lib):
     bad = lib.default_options(asp=2)
     assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
     assert lib.default_options().asp == 0
+    bad = lib.default_options(lo_stab=2)
+    assert L.mcs_setup_structured(3, 2, 1, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
+    assert b"lo_stab" in L.mcs_last_error()
+    assert lib.default_options().lo_stab == 0
     assert L.mcs_apply(None, None, None) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_recover_stress(None, None, 1, None, None, None) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_residual(None, None, None, None) == lib.MCS_ERR_INVALID_ARG
