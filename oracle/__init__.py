@@ -25,5 +25,10 @@ The oracle is a plain, slow, literal restatement of arXiv 2207.08481:
 * ``krylov``        textbook preconditioned MinRes.
 * ``hdg``           the HDG norm eq. (nhdg_eps) on one element and the constant gamma of
                     Corollary schur_SPD (the single-element experiment the paper mentions).
-* ``manufactured``  manufactured solutions and their right-hand sides.
+* ``manufactured``  manufactured solutions and their right-hand sides (one with the outflow
+                    condition of eq. (stokes_NT) on x = 1).
+
+Outflow: ``mesh.with_outflow`` marks the face x_1 = 1 as Gamma_Ntilde; ``system`` then keeps BDM
+dofs but no uhat on it and imposes no pressure mean, and ``precond`` adds the tangential penalty of
+Lemma outflow to Abar and frees the conforming space on that face.
 """

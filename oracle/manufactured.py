@@ -66,3 +66,32 @@ class Manufactured:
 
     def grad_u(self, x):
         return np.stack([self._ev(row, x) for row in self._gu], axis=-2)
+
+
+@functools.lru_cache(maxsize=None)
+def _symbolic_outflow():
+    """2D, Gamma_Ntilde = {x = 1}, Dirichlet elsewhere: u = curl psi with
+    psi = x^2 (3 - 2x) y^2 (1 - y)^2, so u = 0 on x = 0 and y = 0, 1, u_y = 0 and u_x != 0 on x = 1;
+    p = nu d_x u_x + (1 - x) cos(pi y), so that ((sigma + p I) n).n = -nu d_x u_x + p = 0 on x = 1."""
+    x, y = X = sy.symbols("x y")
+    nu = sy.symbols("nu")
+    psi = x**2 * (3 - 2 * x) * y**2 * (1 - y)**2
+    u = [sy.diff(psi, y), -sy.diff(psi, x)]
+    p = nu * sy.diff(u[0], x) + (1 - x) * sy.cos(sy.pi * y)
+    eps = [[(sy.diff(u[a], X[b]) + sy.diff(u[b], X[a])) / 2 for b in range(2)] for a in range(2)]
+    f = [-sum(sy.diff(nu * eps[a][b], X[b]) for b in range(2)) + sy.diff(p, X[a]) for a in range(2)]
+    return X, nu, u, p, f
+
+
+class ManufacturedOutflow(Manufactured):
+    """Manufactured solution with the outflow condition of eq. (stokes_NT) on x = 1 (2D)."""
+
+    def __init__(self, nu: float):
+        X, nus, u, p, f = _symbolic_outflow()
+        self.dim = 2
+        self.nu = nu
+        sub = {nus: nu}
+        self._u = [sy.lambdify(X, c, "numpy") for c in u]
+        self._p = sy.lambdify(X, p.subs(sub), "numpy")
+        self._f = [sy.lambdify(X, c.subs(sub), "numpy") for c in f]
+        self._gu = [[sy.lambdify(X, sy.diff(c, v), "numpy") for v in X] for c in u]

@@ -44,10 +44,29 @@ class Mesh:
     int_rank: np.ndarray      # [nf] rank among interior facets, -1 on boundary
     normals: np.ndarray       # [nf, d] n_F
     signs: np.ndarray         # [ne, d+1] s_{T,f}
+    outflow: np.ndarray | None = None   # [nf] bool, facets on Gamma_Ntilde (None: all Dirichlet)
 
     @property
     def n_int(self) -> int:
         return int(self.interior.sum())
+
+    @property
+    def udof(self) -> np.ndarray:
+        """Facets that carry BDM (normal-flux) dofs: interior facets and facets on Gamma_Ntilde."""
+        return self.interior if self.outflow is None else (self.interior | self.outflow)
+
+    @property
+    def u_rank(self) -> np.ndarray:
+        """Rank of each BDM-dof facet in facet order (-1 elsewhere); equals int_rank without outflow."""
+        if self.outflow is None:
+            return self.int_rank
+        r = -np.ones(len(self.interior), dtype=np.int64)
+        r[self.udof] = np.arange(int(self.udof.sum()))
+        return r
+
+    @property
+    def n_udof(self) -> int:
+        return int(self.udof.sum())
 
 
 def structured(dim: int, N: int, coords: np.ndarray | None = None) -> Mesh:
@@ -120,15 +139,18 @@ def build(dim: int, N: int, coords: np.ndarray, elems: np.ndarray) -> Mesh:
 
 
 def colouring(mesh: Mesh) -> np.ndarray:
-    """Greedy colouring of interior facets; returns colour per interior-facet rank."""
-    d = mesh.dim
-    ints = np.nonzero(mesh.interior)[0]
+    """Greedy colouring of the BDM-dof facets (interior facets, plus Gamma_Ntilde facets if marked);
+    returns colour per facet rank."""
+    ints = np.nonzero(mesh.udof)[0]
+    rank = mesh.u_rank
     colour = -np.ones(len(ints), dtype=np.int64)
     for r, F in enumerate(ints):
         used = set()
         for T in mesh.facet_elems[F]:
+            if T < 0:
+                continue
             for G in mesh.elem_facets[T]:
-                g = mesh.int_rank[G]
+                g = rank[G]
                 if g >= 0 and colour[g] >= 0:
                     used.add(int(colour[g]))
         c = 0
@@ -139,11 +161,23 @@ def colouring(mesh: Mesh) -> np.ndarray:
 
 
 def interior_vertices(mesh: Mesh) -> np.ndarray:
-    """Ids of vertices not on the boundary of the unit square/cube, ascending."""
+    """Ids of the free vertices of the conforming space, ascending: vertices not on the boundary of
+    the unit square/cube, plus (with Gamma_Ntilde marked) those inside the face x_1 = 1."""
     N = mesh.N
     idx = np.rint(mesh_index(mesh)).astype(np.int64)
     inside = np.all((idx > 0) & (idx < N), axis=1)
+    if mesh.outflow is not None:
+        inside |= (idx[:, 0] == N) & np.all((idx[:, 1:] > 0) & (idx[:, 1:] < N), axis=1)
     return np.nonzero(inside)[0]
+
+
+def with_outflow(m: Mesh) -> Mesh:
+    """Marks the face x_1 = 1 of the unit square / cube as Gamma_Ntilde (outflow, Sec. 6.3: u_t = 0
+    and ((sigma + p I) n).n = 0); the other faces stay Dirichlet."""
+    idx = mesh_index(m)
+    on = np.all(idx[m.facets][:, :, 0] == m.N, axis=1) & ~m.interior
+    m.outflow = on
+    return m
 
 
 def mesh_index(mesh: Mesh) -> np.ndarray:

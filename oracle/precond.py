@@ -47,8 +47,39 @@ def p1_map(m: meshmod.Mesh):
     return rank, len(iv)
 
 
-def abar(m: meshmod.Mesh, nu: float) -> sp.csr_matrix:
-    """Abar = nu (eps(u), eps(v)) on interior-vertex P1 vector fields."""
+OUTFLOW_C = 4.0   # C of Lemma outflow (reading R23)
+
+
+def outflow_penalty(m: meshmod.Mesh, nu: float, k: int, C: float = OUTFLOW_C) -> sp.csr_matrix:
+    """Tangential penalty of Lemma outflow on the free P1 dofs:
+    sum_{F in Gamma_Ntilde} nu C k^2 / h_F int_F ubar_t . vbar_t ds, h_F the facet diameter.
+    With the P1 hat functions, int_F lambda_a lambda_b = |F| (1 + delta_ab) / (d (d + 1))."""
+    d = m.dim
+    rank, nv = p1_map(m)
+    R, Cc, V = [], [], []
+    for F in np.nonzero(m.outflow)[0]:
+        w = m.facets[F]
+        Xf = m.coords[w]
+        Ef = Xf[1:] - Xf[:1]
+        meas = np.sqrt(np.linalg.det(Ef @ Ef.T)) / np.prod(np.arange(1, d))
+        hF = max(np.linalg.norm(Xf[a] - Xf[b]) for a in range(d) for b in range(a + 1, d))
+        n = m.normals[F]
+        Pt = np.eye(d) - np.outer(n, n)
+        c = nu * C * k * k / hF
+        for a in range(d):
+            for b in range(d):
+                if rank[w[a]] < 0 or rank[w[b]] < 0:
+                    continue
+                mab = meas * (1.0 + (a == b)) / (d * (d + 1))
+                for i in range(d):
+                    for j in range(d):
+                        R.append(rank[w[a]] * d + i); Cc.append(rank[w[b]] * d + j); V.append(c * mab * Pt[i, j])
+    return sp.csr_matrix((V, (R, Cc)), shape=(nv * d, nv * d))
+
+
+def abar(m: meshmod.Mesh, nu: float, k: int | None = None, C: float = OUTFLOW_C) -> sp.csr_matrix:
+    """Abar = nu (eps(u), eps(v)) on the free P1 vector fields; with Gamma_Ntilde marked, plus the
+    tangential penalty of Lemma outflow (k required)."""
     d = m.dim
     rank, nv = p1_map(m)
     X = m.coords[m.elems]
@@ -69,7 +100,10 @@ def abar(m: meshmod.Mesh, nu: float) -> sp.csr_matrix:
     r = rank[m.elems]                                           # [ne, d+1]
     gm = np.where(r[:, :, None] >= 0, r[:, :, None] * d + np.arange(d)[None, None, :], -1)
     gm = gm.reshape(ne, nl)
-    return system.assemble(gm, gm, Ke, (nv * d, nv * d))
+    A = system.assemble(gm, gm, Ke, (nv * d, nv * d))
+    if m.outflow is not None:
+        A = (A + outflow_penalty(m, nu, k, C)).tocsr()
+    return A
 
 
 def prolongation(coarse: meshmod.Mesh, fine: meshmod.Mesh) -> sp.csr_matrix:
@@ -101,9 +135,13 @@ def prolongation(coarse: meshmod.Mesh, fine: meshmod.Mesh) -> sp.csr_matrix:
 class GMG:
     """Symmetric V-cycle for Abar on the hierarchy N0, 2 N0, ..., N (C^{-1} ~ Abar^{-1})."""
 
-    def __init__(self, dim: int, N: int, levels: int, nu: float, smooth: int = 2):
+    def __init__(self, dim: int, N: int, levels: int, nu: float, smooth: int = 2, outflow_k: int | None = None,
+                 C: float = OUTFLOW_C):
+        """outflow_k: with Gamma_Ntilde marked on every level, the degree k of the penalty."""
         self.meshes = [meshmod.structured(dim, N >> (levels - 1 - l)) for l in range(levels)]
-        self.A = [abar(m, nu) for m in self.meshes]
+        if outflow_k is not None:
+            self.meshes = [meshmod.with_outflow(m) for m in self.meshes]
+        self.A = [abar(m, nu, outflow_k, C) for m in self.meshes]
         self.P = [None] + [prolongation(self.meshes[l - 1], self.meshes[l]) for l in range(1, levels)]
         self.Dl1 = [np.asarray(abs(A).sum(axis=1)).ravel() for A in self.A]
         self.smooth = smooth
@@ -137,9 +175,12 @@ def embedding(D: system.Discretization) -> sp.csr_matrix:
     qF = polys.dubiner(d - 1, k, s)[0]
     nFm1 = polys.n_poly(d - 1, k - 1)
     ref_meas = 1.0 / np.prod(np.arange(1, d))
-    # facet rows
-    for F in np.nonzero(m.interior)[0]:
-        r = m.int_rank[F]
+    # facet rows: BDM moments on every BDM-dof facet; uhat rows on interior facets only (on
+    # Gamma_Ntilde, pi_0 of Lemma outflow zeroes them: there are no uhat dofs there)
+    urank = m.u_rank
+    for F in np.nonzero(m.udof)[0]:
+        r = urank[F]
+        ri = m.int_rank[F]
         w = m.facets[F]
         Xf = m.coords[w]
         Ef = Xf[1:] - Xf[:1]
@@ -164,10 +205,12 @@ def embedding(D: system.Discretization) -> sp.csr_matrix:
                 mom = np.einsum("q,qj,q->j", wf, qF, flux)
                 for j in range(nF):
                     R.append(r * nF + j); C.append(col); V.append(mom[j])
+                if ri < 0:
+                    continue
                 rhs = np.einsum("q,qa,qia->i", wf, ub, basis)
                 ch = np.linalg.solve(G, rhs)
                 for j in range(ntF):
-                    R.append(D.off_h + r * nhF + j); C.append(col); V.append(ch[j])
+                    R.append(D.off_h + ri * nhF + j); C.append(col); V.append(ch[j])
                 if sz["lowest"]:
                     # k = 1 (Sec. 7): third component curl(ubar), as its flux int_F curl(ubar).n_F;
                     # curl(lambda_v e_a) = grad(lambda_v) x e_a, taken on an adjacent element
@@ -178,7 +221,7 @@ def embedding(D: system.Discretization) -> sp.csr_matrix:
                     gl = np.linalg.solve(JT.T, ghat[list(m.elems[T]).index(vid)])
                     ea = np.zeros(d)
                     ea[a] = 1.0
-                    R.append(D.off_h + r * nhF + ntF); C.append(col)
+                    R.append(D.off_h + ri * nhF + ntF); C.append(col)
                     V.append(meas * float(np.cross(gl, ea) @ m.normals[F]))
     # bubble rows: interior moments I_m(ubar|T) = int_T ubar . J^{-T} g_m
     X = m.coords[m.elems]
@@ -219,13 +262,25 @@ class ASP:
         self.Ad_glob = system.assemble(self.cmap, self.cmap, self.Ad, (n, n)).tocsr()
         nF, nhF = sz["nF"], sz["n_hatF"]
         self.nint = m.n_int
-        self.fdofs = np.array([np.concatenate([r * nF + np.arange(nF), D.off_h + r * nhF + np.arange(nhF)])
-                               for r in range(self.nint)]).reshape(self.nint, nF + nhF)
         A = self.Ad_glob
-        self.Dinv = np.stack([np.linalg.inv(A[f][:, f].toarray()) for f in self.fdofs]) \
-            if self.nint else np.zeros((0, nF + nhF, nF + nhF))
         self.colour = meshmod.colouring(m)
-        self.ncol = int(self.colour.max()) + 1 if self.nint else 0
+        self.ncol = int(self.colour.max()) + 1 if len(self.colour) else 0
+        if m.outflow is None:
+            self.fdofs = np.array([np.concatenate([r * nF + np.arange(nF), D.off_h + r * nhF + np.arange(nhF)])
+                                   for r in range(self.nint)]).reshape(self.nint, nF + nhF)
+            self.Dinv = np.stack([np.linalg.inv(A[f][:, f].toarray()) for f in self.fdofs]) \
+                if self.nint else np.zeros((0, nF + nhF, nF + nhF))
+            self.fblocks = None
+        else:
+            # one block per BDM-dof facet: its nF moments, plus its uhat dofs if it is interior
+            self.fblocks = []
+            for F in np.nonzero(m.udof)[0]:
+                r, ri = m.u_rank[F], m.int_rank[F]
+                blk = list(r * nF + np.arange(nF))
+                if ri >= 0:
+                    blk += list(D.off_h + ri * nhF + np.arange(nhF))
+                self.fblocks.append(np.array(blk, dtype=np.int64))
+            self.Dinv = [np.linalg.inv(A[f][:, f].toarray()) for f in self.fblocks]
         E = embedding(D)
         cd = np.concatenate([np.arange(D.n_dd), D.off_h + np.arange(D.n_hat)])
         mask = np.zeros(n, dtype=bool)
@@ -237,6 +292,11 @@ class ASP:
 
     def _sweep(self, x, b, order):
         for c in order:
+            if self.fblocks is not None:
+                r = b - self.Ad_glob @ x
+                for i in np.nonzero(self.colour == c)[0]:
+                    x[self.fblocks[i]] += self.Dinv[i] @ r[self.fblocks[i]]
+                continue
             fs = self.fdofs[self.colour == c]
             if len(fs) == 0:
                 continue
@@ -248,8 +308,12 @@ class ASP:
         """Multiplicative (or additive) ASP for A^d on the coupling dofs."""
         if not self.multiplicative:
             x = np.zeros_like(b)
-            fs = self.fdofs
-            x[fs] = np.einsum("fij,fj->fi", self.Dinv, b[fs])
+            if self.fblocks is not None:
+                for blk, Di in zip(self.fblocks, self.Dinv):
+                    x[blk] += Di @ b[blk]
+            else:
+                fs = self.fdofs
+                x[fs] = np.einsum("fij,fj->fi", self.Dinv, b[fs])
             return x + self.Ed @ self.gmg.vcycle(self.Ed.T @ b)
         x = np.zeros_like(b)
         fwd = range(self.ncol)

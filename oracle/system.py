@@ -72,22 +72,28 @@ class Discretization:
 
 
 def dof_maps(m: meshmod.Mesh, k: int):
+    """Local -> global maps.  BDM facet dofs live on the interior facets and, when the mesh marks
+    Gamma_Ntilde, also on its facets (u_n free there, Sec. 2); uhat dofs on interior facets only
+    (uhat = 0 on Gamma_D and Gamma_Ntilde)."""
     d = m.dim
     sz = fem.local_sizes(d, k)
     ne = m.elems.shape[0]
     nF, nb, nhF, npp = sz["nF"], sz["n_bub"], sz["n_hatF"], sz["n_p"]
     nint = m.n_int
-    n_dd = nint * nF
+    n_dd = m.n_udof * nF
     n_oo = ne * nb
     n_hat = nint * nhF
     n_pres = ne * npp
     u_map = -np.ones((ne, sz["n_u"]), dtype=np.int64)
     h_map = -np.ones((ne, sz["n_hat"]), dtype=np.int64)
+    urank = m.u_rank
     for f in range(d + 1):
+        ru = urank[m.elem_facets[:, f]]
+        oku = ru >= 0
+        for j in range(nF):
+            u_map[oku, f * nF + j] = ru[oku] * nF + j
         r = m.int_rank[m.elem_facets[:, f]]
         ok = r >= 0
-        for j in range(nF):
-            u_map[ok, f * nF + j] = r[ok] * nF + j
         for j in range(nhF):
             h_map[ok, f * nhF + j] = n_dd + n_oo + r[ok] * nhF + j
     for b in range(nb):
@@ -178,10 +184,13 @@ def full_system(D: Discretization):
     return Kf, off
 
 
-def _solve_pinned(K: sp.spmatrix, rhs: np.ndarray, pin: int) -> np.ndarray:
+def _solve_pinned(K: sp.spmatrix, rhs: np.ndarray, pin: int | None) -> np.ndarray:
     """Direct solve of the singular saddle-point system whose kernel is the constant pressure:
     the constant-mode coefficient `pin` is fixed to 0 (row and column removed); the caller
-    removes the pressure mean afterwards (pure Dirichlet boundary, reading R6)."""
+    removes the pressure mean afterwards (pure Dirichlet boundary, reading R6).  pin = None: the
+    system is nonsingular (Gamma_Ntilde marked) and is solved as it is."""
+    if pin is None:
+        return spla.spsolve(K.tocsc(), rhs)
     n = K.shape[0]
     keep = np.ones(n, dtype=bool)
     keep[pin] = False
@@ -198,7 +207,7 @@ def solve_full(D: Discretization, F: np.ndarray):
     Kf, off = full_system(D)
     n = Kf.shape[0]
     rhs = np.concatenate([np.zeros(off), F])
-    sol = _solve_pinned(Kf, rhs, off + int(D.p_map[0, 0]))
+    sol = _solve_pinned(Kf, rhs, None if D.mesh.outflow is not None else off + int(D.p_map[0, 0]))
     ne = D.mesh.elems.shape[0]
     ns, nw = D.sz["n_sigma"], D.sz["n_omega"]
     sigma = sol[:ne * ns].reshape(ne, ns)
@@ -238,7 +247,7 @@ def condensed_system(D: Discretization, AT: np.ndarray | None = None):
 def solve_condensed(D: Discretization, F: np.ndarray, AT=None):
     """Direct solve of K x = F (eq. femSPmat); pressure up to a constant (see solve_full)."""
     K = condensed_system(D, AT)
-    return _solve_pinned(K, F, int(D.p_map[0, 0]))
+    return _solve_pinned(K, F, None if D.mesh.outflow is not None else int(D.p_map[0, 0]))
 
 
 def local_split(D: Discretization):
