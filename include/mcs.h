@@ -96,6 +96,9 @@ typedef struct {
   int lo_stab;        /* k = 1 only (Sec. 7), coefficient of (div omega, div eta)_T: 0 nu (default),
                          1 nu h_T^2 with h_T the element diameter (keeps the iteration count
                          bounded under refinement; see Table ST_ws) */
+  int outflow;        /* mcs_setup_structured, k >= 2 only: 1 makes the face x_1 = 1 an outflow
+                         boundary Gamma_Ntilde (eq. stokes_NT: u_t = 0, ((sigma + p I) n).n = 0);
+                         0 (default): all faces Dirichlet.  See "Outflow" below. */
 } mcs_options;
 
 typedef struct {
@@ -123,6 +126,15 @@ int mcs_version(void);
 const char* mcs_last_error(void);
 /* Fills *o with the defaults listed above. */
 int mcs_default_options(mcs_options* o);
+
+/* Outflow (opt.outflow = 1, Sec. 6.3, Lemma outflow).  The facets on the face x_1 = 1 carry BDM dofs
+ * (u_n is free there) and take a rank among the coupling facets, which are then the interior and the
+ * outflow facets in facet order: u_d, uhat and the facet-interleaved vectors use that rank.  uhat is
+ * zero on Gamma_Ntilde; its slots of outflow facets stay in the layout as phantom dofs whose rows and
+ * columns of K are those of the identity (they remain 0 for a right-hand side that is 0 there).  The
+ * pressure has no constant mode, so no mean is removed.  The conforming space is free inside the face,
+ * Abar gains nu C k^2 / h_F int_F u_t v_t on it (C = 4, h_F the facet diameter) and E^d has no uhat
+ * rows there (pi_0).  Not available with k = 1, mcs_setup_mesh or mcs_condense_noalloc. */
 
 /* Set-up on the Kuhn triangulation of [0,1]^dim with N cells per direction
  * (Sec. 7 uses unstructured meshes; the synthetic workloads use this nested

@@ -67,6 +67,7 @@ void validate_options(const mcs_options& o) {
   if (o.residual_dd < -1 || o.residual_dd > 1) throw McsError(MCS_ERR_INVALID_ARG, "residual_dd");
   if (o.asp < 0 || o.asp > 1) throw McsError(MCS_ERR_INVALID_ARG, "asp");
   if (o.lo_stab < 0 || o.lo_stab > 1) throw McsError(MCS_ERR_INVALID_ARG, "lo_stab");
+  if (o.outflow < 0 || o.outflow > 1) throw McsError(MCS_ERR_INVALID_ARG, "outflow");
 }
 
 template <class R>
@@ -248,7 +249,7 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
     fel[r * 2] = m.facet_elems[F * 2];
     fel[r * 2 + 1] = m.facet_elems[F * 2 + 1];
     floc[r * 2] = m.int_local[r * 2];
-    floc[r * 2 + 1] = m.int_local[r * 2 + 1];
+    floc[r * 2 + 1] = std::max(0, m.int_local[r * 2 + 1]);   // outflow facet: no second element, zero slab
   }
   DevMesh& dm = h->dm;
   dm.d = d;
@@ -264,8 +265,16 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   std::vector<int32_t> fsr(m.nint * 2 * (d + 1));
   for (int64_t r = 0; r < m.nint; ++r)
     for (int side = 0; side < 2; ++side)
-      for (int f = 0; f <= d; ++f) fsr[(r * 2 + side) * (d + 1) + f] = m.elem_rank[fel[r * 2 + side] * (d + 1) + f];
+      for (int f = 0; f <= d; ++f)
+        fsr[(r * 2 + side) * (d + 1) + f] = fel[r * 2 + side] < 0 ? -1 : m.elem_rank[fel[r * 2 + side] * (d + 1) + f];
   dm.fsr = h->upload(fsr);
+  h->outflow = !m.outflow.empty();
+  dm.fout = nullptr;
+  if (h->outflow) {
+    std::vector<int8_t> fout(m.nint, 0);
+    for (int64_t r = 0; r < m.nint; ++r) fout[r] = m.outflow[m.int_facets[r]];
+    dm.fout = h->upload(fout);
+  }
   // tables
   DevTables& dt = h->dt;
   const RefTables& R = h->ref;
@@ -325,7 +334,7 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   std::vector<Csr> A, Pr, Rt;
   for (size_t l = 0; l < levels.size(); ++l) {
     sp.push_back(p1_space(levels[l]));
-    A.push_back(abar_matrix(levels[l], sp[l], h->nu));
+    A.push_back(abar_matrix(levels[l], sp[l], h->nu, h->k));
   }
   Pr.resize(levels.size());
   Rt.resize(levels.size());
@@ -370,6 +379,8 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   }
   for (int i = 0; i < 11; ++i) h->kv[i] = h->dalloc<double>(L.ndof);
   h->ydd = h->dalloc<double>(4 * L.ndof);
+  // an outflow facet has one element, so one of its two row-sum slots is never written: keep it 0
+  cuda_check(cudaMemset(h->ydd, 0, sizeof(double) * 4 * L.ndof), "memset");
   cuda_check(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   h->scratch = h->dalloc<double>(4096);
   cuda_check(cudaMemset(h->scratch, 0, sizeof(double) * 4096), "memset");
@@ -392,8 +403,8 @@ mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* 
   if (dim < 2 || dim > 3) throw McsError(MCS_ERR_UNSUPPORTED, "dim must be 2 or 3");
   // k >= 5: the dual BDM basis of the dof contract (monomial interior moments) makes A_T so badly
   // scaled (2D k = 6: entries near 1e11 around a facet Schur complement near 1e2) that the
-  // condensed blocks lose about 10 digits; 3D k >= 5 also exceeds the per-thread bubble block
-  // k = 1 is the lowest-order variant of Sec. 7, which the paper states for d = 3 (vector rotations)
+  // condensed blocks lose about 10 digits; 3D k >= 5 also exceeds the per-thread bubble block.
+  // k = 1 is the lowest-order variant of Sec. 7, which the paper states for d = 3 (vector rotations).
   if (k < 1 || k > 4) throw McsError(MCS_ERR_UNSUPPORTED, "k must be in 1..4");
   if (k == 1 && dim != 3) throw McsError(MCS_ERR_UNSUPPORTED, "k = 1 (lowest-order variant) needs dim = 3");
   if (!(nu > 0)) throw McsError(MCS_ERR_INVALID_ARG, "nu must be positive");
@@ -404,6 +415,7 @@ mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* 
   if (opt) h->opt = *opt;
   else mcs_default_options(&h->opt);
   validate_options(h->opt);
+  if (h->opt.outflow && k == 1) throw McsError(MCS_ERR_UNSUPPORTED, "outflow with k = 1");
   h->stream = (cudaStream_t)stream;
   cuda_check(cudaGetDevice(&h->device), "cudaGetDevice");
   return h.release();
@@ -498,6 +510,7 @@ int mcs_default_options(mcs_options* o) {
   o->residual_dd = -1;
   o->asp = 0;
   o->lo_stab = 0;
+  o->outflow = 0;
   return MCS_OK;
 }
 
@@ -526,6 +539,7 @@ int mcs_setup_structured(int dim, int N, int k, double nu, const mcs_options* op
       int Nl = N >> (levels - 1 - l);
       h->level_N.push_back(Nl);
       lv.push_back(l + 1 == levels ? structured_mesh(dim, N) : structured_mesh(dim, Nl));
+      if (h->opt.outflow) mark_outflow(lv.back());
     }
     h->mesh = lv.back();
     finish_setup(h.get(), lv);
@@ -540,6 +554,7 @@ int mcs_setup_mesh(int dim, int64_t nv, const double* coords, int64_t ne, const 
     if (!out || !coords || !elems || nv < 1 || ne < 1) throw McsError(MCS_ERR_INVALID_ARG, "bad mesh arguments");
     *out = nullptr;
     std::unique_ptr<mcs_handle> h(new_handle(dim, k, nu, opt, stream));
+    if (h->opt.outflow) throw McsError(MCS_ERR_UNSUPPORTED, "outflow needs mcs_setup_structured");
     HostMesh m;
     m.d = dim;
     m.nv = nv;
@@ -853,7 +868,8 @@ void minres_iteration(mcs_handle* h, cudaStream_t st, double*& v_old, double*& v
   cuda_check(launch_dot(Kz, z, n, h->scratch, &S->delta, stop, st), "dot");
   cuda_check(launch_minres_lanczos(S, n, z, Kz, v, v_old, st), "lanczos");
   precond_any(h, v_old, zn, stop, st);
-  cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, zn, h->scratch, h->total_adet, stop, st), "mean");
+  if (!h->outflow)   // pure Dirichlet: p is fixed by its mean (reading R6); with Gamma_Ntilde it is unique
+    cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, zn, h->scratch, h->total_adet, stop, st), "mean");
   cuda_check(launch_dot(zn, v_old, n, h->scratch, &S->dot1, stop, st), "dot");
   cuda_check(launch_minres_scalars(S, st), "scalars");
   cuda_check(launch_minres_update(S, n, z, w, w_old, x_acc, st), "update");
@@ -920,7 +936,8 @@ void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double floor_
   cuda_check(cudaMemsetAsync(w, 0, sizeof(double) * n, st), "memset");
   cuda_check(cudaMemsetAsync(w_old, 0, sizeof(double) * n, st), "memset");
   precond_any(h, v, z, nullptr);
-  cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, z, h->scratch, h->total_adet, nullptr, st), "mean");
+  if (!h->outflow)
+    cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, z, h->scratch, h->total_adet, nullptr, st), "mean");
   cuda_check(launch_dot(z, v, n, h->scratch, &S->dot1, nullptr, st), "dot");
   cuda_check(launch_minres_init(S, st), "init");
   const int* stop = &S->stop;
@@ -988,7 +1005,8 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       }
       if (total_it >= h->opt.maxit) break;
     }
-    cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, xi, h->scratch, h->total_adet, nullptr, st), "mean");
+    if (!h->outflow)
+      cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, xi, h->scratch, h->total_adet, nullptr, st), "mean");
     cuda_check(cudaMemcpyAsync(x, xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy x");
     if (info) {
       residual(x);

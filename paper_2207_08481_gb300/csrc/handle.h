@@ -65,6 +65,7 @@ struct mcs_handle {
   PrecData<float> pf{};
   PrecData<double> pd{};
   bool condensed = false;
+  bool outflow = false;               // Gamma_Ntilde marked (phantom uhat slots, no pressure mean)
   // Krylov work
   double *kv[11] = {nullptr};  // Krylov vectors; kv[10] is the iterate the captured graph updates
   cudaStream_t cap_stream = nullptr;   // non-default stream for graph capture

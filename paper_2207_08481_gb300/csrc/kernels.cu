@@ -83,6 +83,23 @@ __device__ __forceinline__ void condense_one(const ElemSizes& s, const DevTables
   else if constexpr (LO == 1) condense_element_t<true>(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
   else condense_element(s, et, Xs, sg, nu, w, lane, nl, BlockSync());
   const int nA = s.n_A;
+  if (m.fout) {
+    // uhat of an outflow facet is 0 (Gamma_Ntilde): its slots are phantom dofs, rows and columns of
+    // the identity (the facet has this one element, so the assembled diagonal is 1)
+    bool out[4] = {false, false, false, false};
+    for (int f = 0; f <= d; ++f) {
+      const int32_t rk = m.elem_rank[T * (d + 1) + f];
+      out[f] = rk >= 0 && m.fout[rk] != 0;
+    }
+    if (out[0] || out[1] || out[2] || out[3]) {
+      for (int q = lane; q < nA * nA; q += nl) {
+        const int i = q / nA, j = q - i * nA;
+        const bool pi = i >= s.n_u && out[(i - s.n_u) / s.nhF], pj = j >= s.n_u && out[(j - s.n_u) / s.nhF];
+        if (pi || pj) w.A[q] = (i == j) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+    }
+  }
   if (K.AT) {  // full A_T (FP64, symmetric: row-major = column-major)
     double* out = K.AT + T * (int64_t)nA * nA;
     for (int q = lane; q < nA * nA; q += nl) out[q] = w.A[q];

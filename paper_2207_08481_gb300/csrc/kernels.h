@@ -55,6 +55,7 @@ struct DevMesh {
   // element 1 (d+1); unused entries -1
   const int4* frec;
   const int32_t* fpos;       // [nint] position of interior facet r in colour order (its record index)
+  const int8_t* fout;        // [nint] 1 for an outflow facet (phantom uhat slots); NULL without outflow
 };
 
 

@@ -104,6 +104,37 @@ void build_facets(HostMesh& m) {
   }
 }
 
+void mark_outflow(HostMesh& m) {
+  const int d = m.d;
+  m.outflow.assign(m.nf, 0);
+  for (int64_t F = 0; F < m.nf; ++F) {
+    if (m.facet_elems[F * 2 + 1] >= 0) continue;
+    bool on = true;
+    for (int a = 0; a < d; ++a) on = on && m.coords[(int64_t)m.facets[F * d + a] * d] == 1.0;
+    m.outflow[F] = on ? 1 : 0;
+  }
+  m.int_rank.assign(m.nf, -1);
+  m.int_facets.clear();
+  for (int64_t F = 0; F < m.nf; ++F)
+    if (m.facet_elems[F * 2 + 1] >= 0 || m.outflow[F]) {
+      m.int_rank[F] = (int32_t)m.int_facets.size();
+      m.int_facets.push_back((int32_t)F);
+    }
+  m.nint = (int64_t)m.int_facets.size();
+  for (int64_t T = 0; T < m.ne; ++T)
+    for (int f = 0; f <= d; ++f) m.elem_rank[T * (d + 1) + f] = m.int_rank[m.elem_facets[T * (d + 1) + f]];
+  m.int_local.assign(m.nint * 2, -1);
+  for (int64_t r = 0; r < m.nint; ++r) {
+    const int32_t F = m.int_facets[r];
+    for (int side = 0; side < 2; ++side) {
+      const int32_t T = m.facet_elems[F * 2 + side];
+      if (T < 0) continue;
+      for (int f = 0; f <= d; ++f)
+        if (m.elem_facets[T * (d + 1) + f] == F) m.int_local[r * 2 + side] = f;
+    }
+  }
+}
+
 HostMesh structured_mesh(int d, int N) {
   if (d < 2 || d > 3 || N < 1) throw std::runtime_error("structured_mesh: bad arguments");
   HostMesh m;
@@ -165,6 +196,7 @@ std::vector<int32_t> colour_facets(const HostMesh& m, int* ncolours) {
     std::vector<int> usedv;
     for (int side = 0; side < 2; ++side) {
       int32_t T = m.facet_elems[F * 2 + side];
+      if (T < 0) continue;   // outflow facet: one element
       for (int f = 0; f <= d; ++f) {
         int32_t g = m.elem_rank[T * (d + 1) + f];
         if (g >= 0 && col[g] >= 0) {
@@ -225,7 +257,7 @@ static Csr from_triplets(int64_t nr, int64_t nc, std::vector<std::array<int64_t,
   return A;
 }
 
-Csr abar_matrix(const HostMesh& m, const P1Space& p, double nu) {
+Csr abar_matrix(const HostMesh& m, const P1Space& p, double nu, int k) {
   const int d = m.d;
   std::vector<std::array<int64_t, 2>> ij;
   std::vector<double> v;
@@ -275,6 +307,43 @@ Csr abar_matrix(const HostMesh& m, const P1Space& p, double nu) {
           }
       }
     }
+  }
+  // Lemma outflow: nu C k^2 / h_F int_F u_t . v_t on Gamma_Ntilde, with int_F lam_a lam_b =
+  // |F| (1 + delta_ab) / (d (d + 1)) for the P1 hat functions of the facet's d vertices
+  for (int64_t F = 0; F < (int64_t)m.outflow.size(); ++F) {
+    if (!m.outflow[F]) continue;
+    const int32_t* w = &m.facets[F * d];
+    const double* n = &m.normals[F * d];
+    double e[2][3] = {{0, 0, 0}, {0, 0, 0}}, hF = 0.0;
+    for (int mm = 1; mm < d; ++mm)
+      for (int a = 0; a < d; ++a) e[mm - 1][a] = m.coords[w[mm] * d + a] - m.coords[w[0] * d + a];
+    for (int a = 0; a < d; ++a)
+      for (int b = a + 1; b < d; ++b) {
+        double l2 = 0;
+        for (int c = 0; c < d; ++c) l2 += (m.coords[w[a] * d + c] - m.coords[w[b] * d + c]) *
+                                          (m.coords[w[a] * d + c] - m.coords[w[b] * d + c]);
+        hF = std::max(hF, std::sqrt(l2));
+      }
+    double meas;
+    if (d == 2) {
+      meas = std::sqrt(e[0][0] * e[0][0] + e[0][1] * e[0][1]);
+    } else {
+      const double cx = e[0][1] * e[1][2] - e[0][2] * e[1][1], cy = e[0][2] * e[1][0] - e[0][0] * e[1][2],
+                   cz = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+      meas = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
+    const double c = nu * kOutflowC * k * k / hF;
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        const int32_t ra = p.vrank[w[a]], rb = p.vrank[w[b]];
+        if (ra < 0 || rb < 0) continue;
+        const double mab = meas * (a == b ? 2.0 : 1.0) / (d * (d + 1));
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j) {
+            ij.push_back({(int64_t)ra * d + i, (int64_t)rb * d + j});
+            v.push_back(c * mab * ((i == j ? 1.0 : 0.0) - n[i] * n[j]));
+          }
+      }
   }
   return from_triplets(p.n * d, p.n * d, ij, v);
 }
@@ -366,7 +435,8 @@ std::vector<double> embedding_blocks(const HostMesh& m, const RefTables& T) {
       for (int a = 0; a < d; ++a) {
         int col = wv * d + a;
         for (int j = 0; j < s.nF; ++j) B[j * d * d + col] = n[a] * meas / T.facet_ref_measure * T.Ilam[wv * s.nF + j];
-        for (int mm = 0; mm < d - 1; ++mm)
+        const bool out = !m.outflow.empty() && m.outflow[F];   // pi_0 of Lemma outflow: no uhat rows
+        for (int mm = 0; mm < d - 1 && !out; ++mm)
           for (int j = 0; j < s.nFm1; ++j)
             B[(s.nF + mm * s.nFm1 + j) * d * d + col] = ed[mm][a] * T.Ilam[wv * s.nF + j];
         if (s.lowest) {

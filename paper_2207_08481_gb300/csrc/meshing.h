@@ -22,11 +22,19 @@ struct HostMesh {
   std::vector<int8_t> signs;         // [ne][d+1] orientation s_{T,f}
   std::vector<int32_t> elem_rank;    // [ne][d+1] interior rank of local facet f or -1
   std::vector<double> normals;       // [nf][d]
-  std::vector<int32_t> int_local;    // [nint][2] local facet index in facet_elems[.][0/1]
+  std::vector<int32_t> int_local;    // [nint][2] local facet index in facet_elems[.][0/1] (-1: none)
+  // Gamma_Ntilde (outflow): empty for all-Dirichlet meshes.  When marked, the "interior" ranks above
+  // run over the coupling facets, i.e. the interior facets and the outflow facets (facet order).
+  std::vector<int8_t> outflow;       // [nf] 1 on Gamma_Ntilde
 };
 
 // Builds the facet structures of a mesh with ascending element vertex ids.
 void build_facets(HostMesh& m);
+// Marks the boundary facets on the face x_1 = 1 as Gamma_Ntilde and renumbers the coupling facets
+// (interior and outflow, facet order): int_rank, int_facets, nint, elem_rank, int_local.
+void mark_outflow(HostMesh& m);
+// C of the tangential penalty of Lemma outflow.
+constexpr double kOutflowC = 4.0;
 // Kuhn triangulation of [0,1]^d with N cells per direction (dof contract).
 HostMesh structured_mesh(int d, int N);
 
@@ -48,8 +56,9 @@ struct Csr {
   std::vector<double> val;
 };
 
-// nu (eps u, eps v) on P1 vector fields vanishing on the boundary.
-Csr abar_matrix(const HostMesh& m, const P1Space& p, double nu);
+// nu (eps u, eps v) on P1 vector fields vanishing on the Dirichlet boundary; with Gamma_Ntilde marked,
+// plus the tangential penalty nu C k^2 / h_F int_F u_t . v_t of Lemma outflow (h_F: facet diameter).
+Csr abar_matrix(const HostMesh& m, const P1Space& p, double nu, int k = 0);
 // P1 interpolation from the N/2 Kuhn mesh to the N mesh (structured hierarchy).
 Csr prolongation(int d, int Nc, const P1Space& pc, const P1Space& pf);
 Csr transpose(const Csr& A);

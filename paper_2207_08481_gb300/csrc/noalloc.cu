@@ -78,6 +78,7 @@ extern "C" int mcs_condense_noalloc(mcs_handle* h, int64_t T0, int64_t count, do
   try {
     if (!h || !AT_out) throw McsError(MCS_ERR_INVALID_ARG, "NULL argument");
     if (T0 < 0 || count < 0 || T0 + count > h->mesh.ne) throw McsError(MCS_ERR_INVALID_ARG, "element range");
+    if (h->outflow) throw McsError(MCS_ERR_UNSUPPORTED, "mcs_condense_noalloc with an outflow boundary");
     if (count == 0) return MCS_OK;
     int dev = 0;
     cuda_check(cudaGetDevice(&dev), "cudaGetDevice");

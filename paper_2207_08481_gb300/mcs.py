@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("smooth_steps", ctypes.c_int), ("gmg_levels", ctypes.c_int),
                 ("gmg_smooth", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("residual_dd", ctypes.c_int), ("asp", ctypes.c_int), ("lo_stab", ctypes.c_int)]
+                ("residual_dd", ctypes.c_int), ("asp", ctypes.c_int), ("lo_stab", ctypes.c_int),
+                ("outflow", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):

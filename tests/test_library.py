@@ -67,6 +67,12 @@ def test_invalid_arguments_are_reported_not_raised(lib):
     assert L.mcs_setup_structured(3, 2, 1, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
     assert b"lo_stab" in L.mcs_last_error()
     assert lib.default_options().lo_stab == 0
+    bad = lib.default_options(outflow=2)
+    assert L.mcs_setup_structured(2, 4, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
+    bad = lib.default_options(outflow=1)
+    assert L.mcs_setup_structured(3, 2, 1, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
+    assert b"outflow" in L.mcs_last_error()
+    assert lib.default_options().outflow == 0
     assert L.mcs_apply(None, None, None) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_recover_stress(None, None, 1, None, None, None) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_residual(None, None, None, None) == lib.MCS_ERR_INVALID_ARG
