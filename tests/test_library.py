@@ -78,3 +78,30 @@ def test_invalid_arguments_are_reported_not_raised(lib):
     assert L.mcs_residual(None, None, None, None) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_condense_batch(None, 0) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_destroy(None) == lib.MCS_OK
+
+
+def test_binding_structs_match_the_header(lib, tmp_path):
+    """The ctypes mirrors of the C structs have the header's size and field offsets (a mismatch would
+    corrupt every call silently); checked against a C program compiled from include/mcs.h."""
+    structs = {"mcs_options": lib.Options, "mcs_sizes_t": lib.Sizes, "mcs_solve_info": lib.SolveInfo,
+               "mcs_kernel_stat": lib.KernelStat}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mcs.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    cc = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                        capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, fname, val = line.split()
+        got[(cname, fname)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
