@@ -127,7 +127,7 @@ const char* mcs_last_error(void);
 /* Fills *o with the defaults listed above. */
 int mcs_default_options(mcs_options* o);
 
-/* Outflow (opt.outflow = 1, Sec. 6.3, Lemma outflow).  The facets on the face x_1 = 1 carry BDM dofs
+/* Outflow (opt.outflow = 1, Sec. 6.2, Lemma outflow).  The facets on the face x_1 = 1 carry BDM dofs
  * (u_n is free there) and take a rank among the coupling facets, which are then the interior and the
  * outflow facets in facet order: u_d, uhat and the facet-interleaved vectors use that rank.  uhat is
  * zero on Gamma_Ntilde; its slots of outflow facets stay in the layout as phantom dofs whose rows and

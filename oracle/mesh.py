@@ -172,7 +172,7 @@ def interior_vertices(mesh: Mesh) -> np.ndarray:
 
 
 def with_outflow(m: Mesh) -> Mesh:
-    """Marks the face x_1 = 1 of the unit square / cube as Gamma_Ntilde (outflow, Sec. 6.3: u_t = 0
+    """Marks the face x_1 = 1 of the unit square / cube as Gamma_Ntilde (outflow, Sec. 6.2: u_t = 0
     and ((sigma + p I) n).n = 0); the other faces stay Dirichlet."""
     idx = mesh_index(m)
     on = np.all(idx[m.facets][:, :, 0] == m.N, axis=1) & ~m.interior

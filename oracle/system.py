@@ -73,7 +73,7 @@ class Discretization:
 
 def dof_maps(m: meshmod.Mesh, k: int):
     """Local -> global maps.  BDM facet dofs live on the interior facets and, when the mesh marks
-    Gamma_Ntilde, also on its facets (u_n free there, Sec. 2); uhat dofs on interior facets only
+    Gamma_Ntilde, also on its facets (u_n free there, eq. stokes_NT); uhat dofs on interior facets only
     (uhat = 0 on Gamma_D and Gamma_Ntilde)."""
     d = m.dim
     sz = fem.local_sizes(d, k)
