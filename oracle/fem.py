@@ -175,8 +175,13 @@ def _ref_rules(d, q):
 
 
 def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None,
-                 velocity_only: bool = False) -> ElementData:
+                 velocity_only: bool = False, ortho_bubbles: bool = False) -> ElementData:
     """Physical bases of all spaces on the elements with vertex coordinates X[E, d+1, d].
+
+    ortho_bubbles: the interior moment functions g_m are replaced by an L2(T_hat)-orthonormal basis
+    of their span (the same BDM space and the same facet functions, a different bubble basis; for
+    quantities that eliminate the bubbles, such as A^d_T, only the rounding changes).  Not the dof
+    contract: for experiments at high k only.
 
     velocity_only: only U, DU, divU and P are evaluated (the other fields are None)."""
     E_, dp1, d = X.shape
@@ -250,6 +255,10 @@ def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None,
         flux = np.einsum("qca,ea->eqc", Phi, fn[:, f, :])       # [E, nqf, n_full]
         C[:, f * nF:(f + 1) * nF, :] = np.einsum("eq,qj,eqc->ejc", fw[:, f, :], qF, flux)
     g = interior_test_functions(d, k, xv)                       # [nq, n_bub, d]
+    if ortho_bubbles and g.shape[1]:
+        Gm = np.einsum("q,qma,qna->mn", wv, g, g)
+        Lc = np.linalg.cholesky(Gm)
+        g = np.einsum("qna,mn->qma", g, np.linalg.inv(Lc))      # rows of L^{-1}: orthonormal set
     gphys = np.einsum("eab,qmb->eqma", JinvT, g)
     Phiv = amb_vals(psi)                                        # [nq, n_full, d]
     C[:, (d + 1) * nF:, :] = np.einsum("eq,qca,eqma->emc", wq, Phiv, gphys)
@@ -360,7 +369,7 @@ def stabilisation_weight(X: np.ndarray, nu: float, lo_stab: int) -> np.ndarray:
     return nu * diam2
 
 
-def element_matrices(X, signs, k, nu, lo_stab: int = 0):
+def element_matrices(X, signs, k, nu, lo_stab: int = 0, ortho_bubbles: bool = False):
     """Local blocks of eq. (bigfemSPmat) on every element of the batch.
 
     Returns dict of arrays [E, rows, cols]:
@@ -372,7 +381,7 @@ def element_matrices(X, signs, k, nu, lo_stab: int = 0):
       Bp  = -(div phi^u_j, phi^p_i)_T                     (weak form sign, reading R18)
       Mu  = (phi^u_i, phi^u_j)_T
     """
-    D = element_data(X, signs, k)
+    D = element_data(X, signs, k, ortho_bubbles=ortho_bubbles)
     d = X.shape[2]
     out = {}
     out["M"] = np.einsum("eq,eqiab,eqjab->eij", D.wq, D.S, D.S) / nu
