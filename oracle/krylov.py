@@ -1,11 +1,14 @@
-"""Preconditioned MinRes (oracle side, test infrastructure).
+"""Preconditioned MinRes and GMRES (oracle side, test infrastructure).
 
 Textbook Lanczos-based MINRES for a symmetric (possibly indefinite) operator K
 with a symmetric positive definite preconditioner P ~ K^{-1}, minimising the
 residual in the P-norm (Paige & Saunders 1975; the preconditioned form of
-Elman, Silvester & Wathen, Alg. 4.1).  The paper solves with GMRES (Sec. 7);
+Elman, Silvester & Wathen, Alg. 4.1).  The paper solves with GMRES (Sec. 8);
 MinRes is the symmetric alternative the block preconditioner eq.
-(mhatinvfactor) permits because it is symmetric positive definite.
+(mhatinvfactor) permits because it is symmetric positive definite.  ``gmres``
+is the textbook right-preconditioned, unrestarted GMRES (Saad & Schultz 1986:
+Arnoldi with modified Gram-Schmidt, Givens rotations), minimising ||b - K x||_2,
+for comparison with the paper's iteration counts.
 """
 from __future__ import annotations
 
@@ -60,4 +63,52 @@ def minres(K, P, b, x0=None, rtol=1e-10, maxit=1000, project=None):
         gamma_old, gamma = gamma, gamma_new
         if abs(eta) <= rtol * res0 or gamma == 0.0:
             break
+    return x, it, hist
+
+
+def gmres(K, P, b, x0=None, rtol=1e-6, maxit=500, project=None):
+    """Right-preconditioned GMRES for K x = b: x = x0 + P y with y from the Krylov space of K P,
+    minimising ||b - K x||_2; stops when it falls below rtol * ||b - K x0||_2.  ``project`` is
+    applied to every preconditioned vector.  Returns (x, iterations, history of ||r||_2)."""
+    proj = project if project is not None else (lambda v: v)
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - K(x)
+    beta = float(np.linalg.norm(r))
+    hist = [beta]
+    if beta == 0.0:
+        return x, 0, hist
+    V = [r / beta]
+    Z = []
+    H = np.zeros((maxit + 1, maxit))
+    cs, sn = np.zeros(maxit), np.zeros(maxit)
+    g = np.zeros(maxit + 1)
+    g[0] = beta
+    it = 0
+    for j in range(maxit):
+        z = proj(P(V[j]))
+        Z.append(z)
+        w = K(z)
+        for i in range(j + 1):                      # modified Gram-Schmidt
+            H[i, j] = float(w @ V[i])
+            w = w - H[i, j] * V[i]
+        hn = float(np.linalg.norm(w))
+        H[j + 1, j] = hn
+        V.append(w / hn if hn > 0.0 else w)
+        for i in range(j):                          # previous rotations
+            t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+            H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+            H[i, j] = t
+        den = math.hypot(H[j, j], H[j + 1, j])
+        cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+        H[j, j] = den
+        H[j + 1, j] = 0.0
+        g[j + 1] = -sn[j] * g[j]
+        g[j] = cs[j] * g[j]
+        it = j + 1
+        hist.append(abs(g[j + 1]))
+        if abs(g[j + 1]) <= rtol * beta or hn == 0.0:
+            break
+    y = np.linalg.solve(np.triu(H[:it, :it]), g[:it])
+    for i in range(it):
+        x = x + y[i] * Z[i]
     return x, it, hist
