@@ -1,0 +1,168 @@
+"""CPU parity of the library's host-compiled code against the oracle (no GPU).
+
+The element condensation (csrc/element.cuh, the same source the CUDA kernels run with a warp or a
+block of lanes) is compiled here with g++ for a single lane, together with the host set-up code
+(csrc/reference.cpp, csrc/meshing.cpp: reference tables, numbering with an outflow face, the
+conforming operator with its penalty and the E^d blocks), and compared with the oracle element by
+element.  This checks the arithmetic of the element algorithm and of the host tables on every CPU
+run; the GPU tests check the same quantities through the C-ABI."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import mesh, precond, system
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2207_08481_gb300", "csrc")
+
+HARNESS = r'''
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include "reference.h"
+#include "meshing.h"
+#include "element.cuh"
+using namespace mcs;
+
+static ElemSizes sizes_of(const Sizes& s, int lo_stab) {
+  ElemSizes e;
+  e.d = s.d; e.k = s.k; e.nk = s.nk; e.nF = s.nF; e.nFm1 = s.nFm1; e.n_u = s.n_u; e.n_A = s.n_A;
+  e.n_hat = s.n_hat; e.nhF = s.nhF; e.n_p = s.n_p; e.n_s0 = s.n_s0; e.n_raw = s.n_raw; e.n_con = s.n_con;
+  e.n_w = s.n_w; e.n_wskew = s.n_wskew; e.n_cc = s.n_cc; e.n_bub = s.n_bub; e.n_c = s.n_c; e.mF = s.mF;
+  e.ntF = s.ntF; e.lowest = s.lowest; e.lo_stab = lo_stab;
+  return e;
+}
+
+int main(int argc, char** argv) {
+  const char* mode = argv[1];
+  const int d = atoi(argv[2]), k = atoi(argv[3]);
+  if (!strcmp(mode, "condense")) {
+    // stdin: nu lo_stab, then per element (d+1)*d coordinates and d+1 signs
+    double nu; int lo;
+    if (scanf("%lf %d", &nu, &lo) != 2) return 1;
+    RefTables R = build_reference(d, k);
+    ElemSizes e = sizes_of(R.s, lo);
+    ElemTables t{R.B0.data(), R.Rf.data(), R.Bh.data(), R.Ccon.data(), R.Adiv.data(), R.nhat.data(),
+                 R.Wmom.data()};
+    std::vector<double> ws(elem_work_doubles(e));
+    double X[12];
+    int sg[4];
+    while (true) {
+      for (int i = 0; i < (d + 1) * d; ++i)
+        if (scanf("%lf", &X[i]) != 1) return 0;
+      for (int i = 0; i <= d; ++i)
+        if (scanf("%d", &sg[i]) != 1) return 1;
+      ElemWork w = elem_work_carve(e, ws.data());
+      condense_element(e, t, X, sg, nu, w, 0, 1, []() {});
+      for (int i = 0; i < e.n_A * e.n_A; ++i) printf("%.17g\n", w.A[i]);
+    }
+  }
+  // "mesh": structured N, optional outflow face; numbering, Abar (nu = 0.7) and E^d blocks
+  const int N = atoi(argv[4]), outflow = atoi(argv[5]);
+  HostMesh m = structured_mesh(d, N);
+  if (outflow) mark_outflow(m);
+  RefTables R = build_reference(d, k);
+  const Sizes& s = R.s;
+  for (int64_t r = 0; r < m.nint; ++r) printf("CF %d\n", m.int_facets[r]);
+  P1Space p = p1_space(m);
+  for (int64_t v = 0; v < m.nv; ++v) printf("VR %d\n", p.vrank[v]);
+  Csr A = abar_matrix(m, p, 0.7, k);
+  for (int64_t r = 0; r < A.nrows; ++r)
+    for (int64_t q = A.rowptr[r]; q < A.rowptr[r + 1]; ++q) printf("A %ld %d %.17g\n", (long)r, A.col[q], A.val[q]);
+  std::vector<double> B = embedding_blocks(m, R);
+  for (int64_t r = 0; r < m.nint; ++r) {
+    const int F = m.int_facets[r];
+    for (int tt = 0; tt < s.mF; ++tt)
+      for (int w = 0; w < d; ++w)
+        for (int a = 0; a < d; ++a)
+          printf("E %ld %d %d %d %.17g\n", (long)r, tt, m.facets[F * d + w], a, B[((size_t)r * s.mF + tt) * d * d + w * d + a]);
+  }
+  return 0;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("host")
+    src = d / "harness.cpp"
+    src.write_text(HARNESS)
+    exe = d / "harness"
+    cmd = [cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), os.path.join(CSRC, "reference.cpp"),
+           os.path.join(CSRC, "meshing.cpp"), "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return str(exe)
+
+
+def _perturbed(d, N, seed=1):
+    m = mesh.structured(d, N)
+    c = m.coords.copy()
+    inner = np.all((c > 1e-12) & (c < 1 - 1e-12), axis=1)
+    c[inner] += 0.15 / N * np.random.default_rng(seed).uniform(-1, 1, size=(inner.sum(), d))
+    return mesh.structured(d, N, coords=c)
+
+
+@pytest.mark.parametrize("d,k,N,lo", [(2, 2, 3, 0), (2, 3, 2, 0), (2, 4, 1, 0), (3, 2, 1, 0), (3, 1, 2, 0),
+                                      (3, 1, 2, 1)])
+def test_element_condensation_matches_oracle(harness, d, k, N, lo):
+    """A_T of every element of a perturbed mesh (orientation signs applied), 1e-12 relative."""
+    nu = 0.7
+    m = _perturbed(d, N)
+    D = system.discretize(m, k, nu, lo_stab=lo)
+    AT = system.condense(D)
+    X = m.coords[m.elems]
+    lines = [f"{nu!r} {lo}"] + [" ".join("%.17g" % v for v in X[e].ravel()) + " " + " ".join(map(str, m.signs[e]))
+                                for e in range(X.shape[0])]
+    out = subprocess.run([harness, "condense", str(d), str(k)], input="\n".join(lines), capture_output=True,
+                         text=True, check=True).stdout
+    A = np.array(out.split(), dtype=float).reshape(AT.shape)
+    err = np.abs(A - AT).max(axis=(1, 2)) / np.abs(AT).max(axis=(1, 2))
+    assert err.max() < 1e-12
+
+
+@pytest.mark.parametrize("d,k,N,outflow", [(2, 2, 4, 0), (2, 3, 4, 1), (3, 1, 2, 0), (3, 2, 2, 1)])
+def test_numbering_abar_and_embedding_match_oracle(harness, d, k, N, outflow):
+    """Coupling facets (interior, plus the outflow face), free P1 vertices, Abar with the tangential
+    penalty of Lemma outflow, and the E^d blocks (uhat rows by L2 projection, zero on the outflow face;
+    the curl rows for k = 1) against the oracle's assembled operators."""
+    m = mesh.structured(d, N)
+    if outflow:
+        m = mesh.with_outflow(m)
+    D = system.discretize(m, k, 0.7)
+    out = subprocess.run([harness, "mesh", str(d), str(k), str(N), str(outflow)], capture_output=True, text=True,
+                         check=True).stdout.splitlines()
+    udof = np.nonzero(m.udof)[0]
+    assert [int(l.split()[1]) for l in out if l.startswith("CF ")] == list(udof)
+    rank, _ = precond.p1_map(m)
+    assert np.array_equal(np.array([int(l.split()[1]) for l in out if l.startswith("VR ")]), rank)
+    Ao = precond.abar(m, 0.7, k).toarray()
+    Ah = np.zeros_like(Ao)
+    for l in out:
+        if l.startswith("A "):
+            _, r, c, v = l.split()
+            Ah[int(r), int(c)] += float(v)
+    assert np.abs(Ah - Ao).max() < 1e-13 * np.abs(Ao).max()
+    E = precond.embedding(D).tocsr()
+    nF, nhF = D.sz["nF"], D.sz["n_hatF"]
+    err, seen = 0.0, 0
+    for l in out:
+        if not l.startswith("E "):
+            continue
+        _, r, t, vid, a, v = l.split()
+        r, t, vid, a, v = int(r), int(t), int(vid), int(a), float(v)
+        if rank[vid] < 0:
+            continue
+        ri = m.int_rank[udof[r]]
+        row = r * nF + t if t < nF else (D.off_h + ri * nhF + (t - nF) if ri >= 0 else None)
+        ref = E[row, rank[vid] * d + a] if row is not None else 0.0
+        err = max(err, abs(ref - v))
+        seen += 1
+    assert seen > 0 and err < 1e-13 * abs(E).max()
