@@ -59,6 +59,12 @@ int main(int argc, char** argv) {
       ElemWork w = elem_work_carve(e, ws.data());
       condense_element(e, t, X, sg, nu, w, 0, 1, []() {});
       for (int i = 0; i < e.n_A * e.n_A; ++i) printf("%.17g\n", w.A[i]);
+      // bubble condensation (eqs. Hcoeffs, factorSsigma): A^d (coupling order), G, A_oo^{-1}
+      const int no = e.n_bub, nc = e.n_c;
+      std::vector<double> bw(no * no + no * nc + 1), Ad(nc * nc), G(no * nc + 1), Ai(no * no + 1);
+      bubble_condense(e, w.A, bw.data(), Ad.data(), G.data(), Ai.data(), 0, 1, []() {});
+      for (int i = 0; i < nc * nc; ++i) printf("%.17g\n", Ad[i]);
+      for (int i = 0; i < no * nc; ++i) printf("%.17g\n", G[i]);
     }
   }
   // "mesh": structured N, optional outflow face; numbering, Abar (nu = 0.7) and E^d blocks
@@ -113,7 +119,8 @@ def _perturbed(d, N, seed=1):
 @pytest.mark.parametrize("d,k,N,lo", [(2, 2, 3, 0), (2, 3, 2, 0), (2, 4, 1, 0), (3, 2, 1, 0), (3, 1, 2, 0),
                                       (3, 1, 2, 1)])
 def test_element_condensation_matches_oracle(harness, d, k, N, lo):
-    """A_T of every element of a perturbed mesh (orientation signs applied), 1e-12 relative."""
+    """A_T of every element of a perturbed mesh (orientation signs applied), 1e-12 relative; the double
+    Schur complement A^d_T and G_T = A_oo^{-1} A_od (eqs. Hcoeffs, factorSsigma) to 1e-11 / 1e-10."""
     nu = 0.7
     m = _perturbed(d, N)
     D = system.discretize(m, k, nu, lo_stab=lo)
@@ -123,9 +130,23 @@ def test_element_condensation_matches_oracle(harness, d, k, N, lo):
                                 for e in range(X.shape[0])]
     out = subprocess.run([harness, "condense", str(d), str(k)], input="\n".join(lines), capture_output=True,
                          text=True, check=True).stdout
-    A = np.array(out.split(), dtype=float).reshape(AT.shape)
+    sz = D.sz
+    ne, nA = AT.shape[0], AT.shape[1]
+    nc, no = (d + 1) * (sz["nF"] + sz["n_hatF"]), sz["n_bub"]
+    vals = np.array(out.split(), dtype=float).reshape(ne, nA * nA + nc * nc + no * nc)
+    A = vals[:, :nA * nA].reshape(AT.shape)
     err = np.abs(A - AT).max(axis=(1, 2)) / np.abs(AT).max(axis=(1, 2))
     assert err.max() < 1e-12
+    # A^d and G in the library's facet-major coupling order against the oracle's [u_d | uhat] order
+    Ad_o, G_o, _ = system.bubble_condense(D, AT)
+    mF = sz["nF"] + sz["n_hatF"]
+    perm = [f * sz["nF"] + t if t < sz["nF"] else (d + 1) * sz["nF"] + f * sz["n_hatF"] + (t - sz["nF"])
+            for f in range(d + 1) for t in range(mF)]
+    Ad = vals[:, nA * nA:nA * nA + nc * nc].reshape(ne, nc, nc)
+    assert np.abs(Ad - Ad_o[:, perm][:, :, perm]).max() < 1e-11 * np.abs(Ad_o).max()
+    if no:
+        G = vals[:, nA * nA + nc * nc:].reshape(ne, no, nc)
+        assert np.abs(G - G_o[:, :, perm]).max() < 1e-10 * np.abs(G_o).max()
 
 
 @pytest.mark.parametrize("d,k,N,outflow", [(2, 2, 4, 0), (2, 3, 4, 1), (3, 1, 2, 0), (3, 2, 2, 1)])
