@@ -13,7 +13,7 @@ import subprocess
 import numpy as np
 import pytest
 
-from oracle import mesh, precond, system
+from oracle import fem, mesh, precond, system
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2207_08481_gb300", "csrc")
@@ -65,6 +65,37 @@ int main(int argc, char** argv) {
       bubble_condense(e, w.A, bw.data(), Ad.data(), G.data(), Ai.data(), 0, 1, []() {});
       for (int i = 0; i < nc * nc; ++i) printf("%.17g\n", Ad[i]);
       for (int i = 0; i < no * nc; ++i) printf("%.17g\n", G[i]);
+    }
+  }
+  if (!strcmp(mode, "recover")) {
+    // stdin: nu nq, nq reference points, then per element: coordinates, signs, n_A local coefficients
+    double nu; int nq;
+    if (scanf("%lf %d", &nu, &nq) != 2) return 1;
+    RefTables R = build_reference(d, k);
+    ElemSizes e = sizes_of(R.s, 0);
+    ElemTables t{R.B0.data(), R.Rf.data(), R.Bh.data(), R.Ccon.data(), R.Adiv.data(), R.nhat.data(),
+                 R.Wmom.data()};
+    std::vector<double> xh(nq * d), psi(nq * e.nk);
+    for (int i = 0; i < nq * d; ++i)
+      if (scanf("%lf", &xh[i]) != 1) return 1;
+    for (int q = 0; q < nq; ++q) dubiner_eval(d, k, &xh[q * d], &psi[q * e.nk], nullptr);
+    std::vector<double> ws(elem_work_doubles(e)), a(e.n_A), wk(e.n_cc + 2 * e.n_raw), sig(nq * d * d),
+        om(nq * d * d);
+    double X[12];
+    int sg[4];
+    while (true) {
+      for (int i = 0; i < (d + 1) * d; ++i)
+        if (scanf("%lf", &X[i]) != 1) return 0;
+      for (int i = 0; i <= d; ++i)
+        if (scanf("%d", &sg[i]) != 1) return 1;
+      for (int i = 0; i < e.n_A; ++i)
+        if (scanf("%lf", &a[i]) != 1) return 1;
+      ElemWork w = elem_work_carve(e, ws.data());
+      condense_element(e, t, X, sg, nu, w, 0, 1, []() {});
+      recover_element(e, w, X, a.data(), nq, psi.data(), wk.data(), sig.data(), e.lowest ? nullptr : om.data(), 0, 1,
+                      []() {});
+      for (int i = 0; i < nq * d * d; ++i) printf("%.17g\n", sig[i]);
+      for (int i = 0; i < nq * d * d; ++i) printf("%.17g\n", e.lowest ? 0.0 : om[i]);
     }
   }
   // "mesh": structured N, optional outflow face; numbering, Abar (nu = 0.7) and E^d blocks
@@ -187,3 +218,38 @@ def test_numbering_abar_and_embedding_match_oracle(harness, d, k, N, outflow):
         err = max(err, abs(ref - v))
         seen += 1
     assert seen > 0 and err < 1e-13 * abs(E).max()
+
+
+@pytest.mark.parametrize("d,k,N", [(2, 3, 2), (3, 2, 1), (3, 1, 2)])
+def test_stress_recovery_matches_oracle(harness, d, k, N):
+    """Local solves of eq. (projection) for a random coefficient vector: sigma_h (and omega_h for
+    k >= 2) at the oracle's quadrature points, from the element code against the oracle's solves."""
+    nu = 0.9
+    m = _perturbed(d, N, seed=4)
+    D = system.discretize(m, k, nu)
+    x = np.random.default_rng(8).standard_normal(D.ndof)
+    sig, om = system.recover_stress(D, x)
+    X = m.coords[m.elems]
+    E = fem.element_data(X, m.signs, k)
+    so = np.einsum("ej,eqjab->eqab", sig, E.S)
+    # local coefficients with the orientation signs removed (facet BDM dofs; rotation fluxes for k = 1)
+    sz = D.sz
+    am = D.a_map
+    a = np.where(am >= 0, x[np.maximum(am, 0)], 0.0)
+    nfd = (d + 1) * sz["nF"]
+    a[:, :nfd] *= np.repeat(m.signs, sz["nF"], axis=1)
+    if sz["lowest"]:
+        a[:, sz["n_u"] + 2::3] *= m.signs
+    J0 = (X[0, 1:, :] - X[0, :1, :]).T
+    xhat = np.linalg.solve(J0, (E.xq[0] - X[0, 0]).T).T
+    nq = xhat.shape[0]
+    lines = [f"{nu!r} {nq}", " ".join("%.17g" % v for v in xhat.ravel())]
+    lines += [" ".join("%.17g" % v for v in X[e].ravel()) + " " + " ".join(map(str, m.signs[e])) + " " +
+              " ".join("%.17g" % v for v in a[e]) for e in range(X.shape[0])]
+    out = subprocess.run([harness, "recover", str(d), str(k)], input="\n".join(lines), capture_output=True,
+                         text=True, check=True).stdout
+    vals = np.array(out.split(), dtype=float).reshape(X.shape[0], 2, nq, d, d)
+    assert np.abs(vals[:, 0] - so).max() < 1e-11 * np.abs(so).max()
+    if not sz["lowest"]:
+        wo = np.einsum("ej,eqjab->eqab", om, E.W)
+        assert np.abs(vals[:, 1] - wo).max() < 1e-10 * np.abs(wo).max()
