@@ -22,7 +22,7 @@ The oracle is a plain, slow, literal restatement of arXiv 2207.08481:
                     eq. defED), the geometric multigrid V-cycle used as C, the
                     facet-block Gauss-Seidel smoother, the multiplicative ASP of
                     Sec. 5.2 and the block preconditioner of eq. (mhatinvfactor).
-* ``krylov``        textbook preconditioned MinRes.
+* ``krylov``        textbook preconditioned MinRes, and GMRES (the paper's solver) for comparison.
 * ``hdg``           the HDG norm eq. (nhdg_eps) on one element and the constant gamma of
                     Corollary schur_SPD (the single-element experiment the paper mentions).
 * ``manufactured``  manufactured solutions and their right-hand sides (one with the outflow
