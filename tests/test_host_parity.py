@@ -105,6 +105,9 @@ int main(int argc, char** argv) {
   RefTables R = build_reference(d, k);
   const Sizes& s = R.s;
   for (int64_t r = 0; r < m.nint; ++r) printf("CF %d\n", m.int_facets[r]);
+  int ncol = 0;
+  std::vector<int32_t> col = colour_facets(m, &ncol);
+  for (int64_t r = 0; r < m.nint; ++r) printf("CL %d\n", col[r]);
   P1Space p = p1_space(m);
   for (int64_t v = 0; v < m.nv; ++v) printf("VR %d\n", p.vrank[v]);
   Csr A = abar_matrix(m, p, 0.7, k);
@@ -182,7 +185,7 @@ def test_element_condensation_matches_oracle(harness, d, k, N, lo):
 
 @pytest.mark.parametrize("d,k,N,outflow", [(2, 2, 4, 0), (2, 3, 4, 1), (3, 1, 2, 0), (3, 2, 2, 1)])
 def test_numbering_abar_and_embedding_match_oracle(harness, d, k, N, outflow):
-    """Coupling facets (interior, plus the outflow face), free P1 vertices, Abar with the tangential
+    """Coupling facets (interior, plus the outflow face) and their colouring, free P1 vertices, Abar with the tangential
     penalty of Lemma outflow, and the E^d blocks (uhat rows by L2 projection, zero on the outflow face;
     the curl rows for k = 1) against the oracle's assembled operators."""
     m = mesh.structured(d, N)
@@ -193,6 +196,12 @@ def test_numbering_abar_and_embedding_match_oracle(harness, d, k, N, outflow):
                          check=True).stdout.splitlines()
     udof = np.nonzero(m.udof)[0]
     assert [int(l.split()[1]) for l in out if l.startswith("CF ")] == list(udof)
+    col = np.array([int(l.split()[1]) for l in out if l.startswith("CL ")])
+    assert np.array_equal(col, mesh.colouring(m))            # greedy colouring of the coupling facets
+    for c in range(col.max() + 1):                           # one colour: no two facets share an element
+        els = m.facet_elems[udof[col == c]].ravel()
+        els = els[els >= 0]
+        assert len(els) == len(np.unique(els))
     rank, _ = precond.p1_map(m)
     assert np.array_equal(np.array([int(l.split()[1]) for l in out if l.startswith("VR ")]), rank)
     Ao = precond.abar(m, 0.7, k).toarray()
