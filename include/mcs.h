@@ -25,6 +25,8 @@
  *     owns every buffer it passes; the library owns the handle and the
  *     operators it keeps resident on the device.
  *   - Calls are asynchronous on the handle's stream unless stated otherwise.
+ *   - Threads: one handle must not be used by two host threads at once; different handles are
+ *     independent and may be used concurrently, each on its own stream (the serving loop does so).
  *   - Vectors of the condensed system have length ndof, layout
  *       [u_d | u_o | uhat | p]
  *     u_d: BDM facet moments (interior facet rank r, mode j) at r*nF + j;
