@@ -143,100 +143,136 @@ __host__ __device__ inline void small_inverse(int n, double* A, double* Inv) {
   }
 }
 
-// Geometric factors of one element (single lane).
+// Nonzeros of the trace-free unit E_s (same order as tf_unit): rows a[], columns b[], values c[];
+// returns their number (1 for an off-diagonal unit e_i e_j^T, 2 for e_t e_t^T - e_{t+1} e_{t+1}^T).
+__host__ __device__ inline int tf_nonzeros(int d, int s, int* a, int* b, double* c) {
+  const int noff = d * (d - 1);
+  if (s < noff) {
+    const int i = s / (d - 1), jj = s - i * (d - 1);
+    a[0] = i;
+    b[0] = jj < i ? jj : jj + 1;
+    c[0] = 1.0;
+    return 1;
+  }
+  const int t = s - noff;
+  a[0] = b[0] = t;
+  c[0] = 1.0;
+  a[1] = b[1] = t + 1;
+  c[1] = -1.0;
+  return 2;
+}
+
+// The pair (a, b), a < b, of the r-th skew unit K_r = e_b e_a^T - e_a e_b^T (order (0,1), (0,2), (1,2)).
+__host__ __device__ inline void skew_pair(int d, int r, int& a, int& b) {
+  int cnt = 0;
+  for (int i = 0; i < d; ++i)
+    for (int j = i + 1; j < d; ++j) {
+      if (cnt == r) { a = i; b = j; }
+      ++cnt;
+    }
+}
+
+// Geometric factors of one element, computed by nl cooperating lanes.
 // geo: [0..63] L (n_s0 x n_s0, lower, g^{-1} = L L^T), [64..87] h (n_wskew x n_s0),
 //      [88..99] w (d+1 x d), [100] |det J|, [101] det J
-__host__ __device__ inline void elem_geometry(const ElemSizes& s, const double* X, const double* nhat, double* geo) {
+// tmp: 164 doubles of scratch (J, J^{-1}, G, G^{-1}, g, g^{-1}).
+// With g_st = tr(E_s^T G^{-1} E_t G) written out over the nonzeros of the units and
+// h_rs = K_r : (J^{-T} E_s J^T) = sum over E_s's nonzeros (a, b, c) of c (Ji[a][q] J[p][b] - Ji[a][p] J[q][b])
+// for the pair (p, q) of K_r (Ji[a][i] = (J^{-1})_{ai}, J[j][b] = J_{jb}).
+template <class Sync>
+__host__ __device__ inline void elem_geometry(const ElemSizes& s, const double* X, const double* nhat, double* geo,
+                                              double* tmp, int lane, int nl, Sync sync) {
   const int d = s.d, ns0 = s.n_s0;
-  double J[9], Ji[9], G[9], Gi[9];
-  for (int a = 0; a < d; ++a)
-    for (int i = 0; i < d; ++i) J[a * d + i] = X[(i + 1) * d + a] - X[a];  // column i = x_{i+1} - x_0
-  double det;
-  if (d == 2) {
-    det = J[0] * J[3] - J[1] * J[2];
-    Ji[0] = J[3] / det; Ji[1] = -J[1] / det; Ji[2] = -J[2] / det; Ji[3] = J[0] / det;
-  } else {
-    det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
-    Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det;
-    Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
-    Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
-    Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det;
-    Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
-    Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
-    Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det;
-    Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
-    Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
-  }
-  for (int a = 0; a < d; ++a)
-    for (int b = 0; b < d; ++b) {
-      double g = 0, gi = 0;
-      for (int c = 0; c < d; ++c) {
-        g += J[c * d + a] * J[c * d + b];
-        gi += Ji[a * d + c] * Ji[b * d + c];
-      }
-      G[a * d + b] = g;
-      Gi[a * d + b] = gi;
-    }
-  // g_st = tr(E_s^T Gi E_t G) = sum_{a,b,c,e} E_s[a,b] Gi[a,c] E_t[c,e] G[e,b]
-  double gm[64], gmc[64], ginv[64];
-  for (int s1 = 0; s1 < ns0; ++s1)
-    for (int t = 0; t < ns0; ++t) {
-      double v = 0;
-      for (int a = 0; a < d; ++a)
-        for (int b = 0; b < d; ++b) {
-          double es = tf_unit(d, s1, a, b);
-          if (es == 0.0) continue;
-          for (int c = 0; c < d; ++c)
-            for (int e = 0; e < d; ++e) {
-              double et = tf_unit(d, t, c, e);
-              if (et == 0.0) continue;
-              v += es * Gi[a * d + c] * et * G[e * d + b];
-            }
-        }
-      gm[s1 * ns0 + t] = v;
-    }
-  for (int i = 0; i < ns0 * ns0; ++i) gmc[i] = gm[i];
-  small_inverse(ns0, gmc, ginv);
-  // symmetrise and Cholesky g^{-1} = L L^T
-  double* L = geo;
-  for (int i = 0; i < 64; ++i) L[i] = 0.0;
-  for (int j = 0; j < ns0; ++j) {
-    double sdiag = 0.5 * (ginv[j * ns0 + j] + ginv[j * ns0 + j]);
-    for (int p = 0; p < j; ++p) sdiag -= L[j * ns0 + p] * L[j * ns0 + p];
-    double ljj = sqrt(sdiag);
-    L[j * ns0 + j] = ljj;
-    for (int i = j + 1; i < ns0; ++i) {
-      double v = 0.5 * (ginv[i * ns0 + j] + ginv[j * ns0 + i]);
-      for (int p = 0; p < j; ++p) v -= L[i * ns0 + p] * L[j * ns0 + p];
-      L[i * ns0 + j] = v / ljj;
-    }
-  }
-  // h_rs = K_r : (J^{-T} E_s J^T) = sum_{ij} K[i,j] (J^{-T} E_s J^T)[i,j]
-  double* h = geo + 64;
-  for (int r = 0; r < s.n_wskew; ++r)
-    for (int s1 = 0; s1 < ns0; ++s1) {
-      double v = 0;
-      for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d; ++j) {
-          double K = skew_unit(d, r, i, j);
-          if (K == 0.0) continue;
-          double m = 0;  // (J^{-T} E J^T)[i,j] = sum_{a,b} Ji[a,i] E[a,b] J[j,b]
-          for (int a = 0; a < d; ++a)
-            for (int b = 0; b < d; ++b) m += Ji[a * d + i] * tf_unit(d, s1, a, b) * J[j * d + b];
-          v += K * m;
-        }
-      h[r * ns0 + s1] = v;
-    }
-  double* w = geo + 88;
-  for (int f = 0; f <= d; ++f) {
-    double gn[3] = {0, 0, 0}, nn = 0;
+  double* J = tmp;
+  double* Ji = tmp + 9;
+  double* G = tmp + 18;
+  double* Gi = tmp + 27;
+  double* gm = tmp + 36;
+  double* ginv = tmp + 100;
+  if (lane == 0) {
     for (int a = 0; a < d; ++a)
-      for (int b = 0; b < d; ++b) gn[a] += Gi[a * d + b] * nhat[f * d + b];
-    for (int a = 0; a < d; ++a) nn += gn[a] * nhat[f * d + a];
-    for (int a = 0; a < d; ++a) w[f * d + a] = gn[a] / nn;
+      for (int i = 0; i < d; ++i) J[a * d + i] = X[(i + 1) * d + a] - X[a];  // column i = x_{i+1} - x_0
+    double det;
+    if (d == 2) {
+      det = J[0] * J[3] - J[1] * J[2];
+      Ji[0] = J[3] / det; Ji[1] = -J[1] / det; Ji[2] = -J[2] / det; Ji[3] = J[0] / det;
+    } else {
+      det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+      Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+      Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+      Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+      Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+      Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+      Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+      Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+      Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+      Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+    }
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        double g = 0, gi = 0;
+        for (int c = 0; c < d; ++c) {
+          g += J[c * d + a] * J[c * d + b];
+          gi += Ji[a * d + c] * Ji[b * d + c];
+        }
+        G[a * d + b] = g;
+        Gi[a * d + b] = gi;
+      }
+    geo[100] = fabs(det);
+    geo[101] = det;
   }
-  geo[100] = fabs(det);
-  geo[101] = det;
+  sync();
+  // g (n_s0^2 entries), h (n_wskew * n_s0) and the facet weights w (d + 1) over the lanes
+  const int ng = ns0 * ns0, nh = s.n_wskew * ns0;
+  for (int q = lane; q < ng + nh + d + 1; q += nl) {
+    if (q < ng) {
+      const int s1 = q / ns0, t = q - s1 * ns0;
+      int a1[2], b1[2], a2[2], b2[2];
+      double c1[2], c2[2];
+      const int n1 = tf_nonzeros(d, s1, a1, b1, c1), n2 = tf_nonzeros(d, t, a2, b2, c2);
+      double v = 0;
+      for (int u = 0; u < n1; ++u)
+        for (int w2 = 0; w2 < n2; ++w2) v += c1[u] * c2[w2] * Gi[a1[u] * d + a2[w2]] * G[b2[w2] * d + b1[u]];
+      gm[q] = v;
+    } else if (q < ng + nh) {
+      const int r = (q - ng) / ns0, s1 = (q - ng) - r * ns0;
+      int p, qq;
+      skew_pair(d, r, p, qq);
+      int a1[2], b1[2];
+      double c1[2];
+      const int n1 = tf_nonzeros(d, s1, a1, b1, c1);
+      double v = 0;
+      for (int u = 0; u < n1; ++u)
+        v += c1[u] * (Ji[a1[u] * d + qq] * J[p * d + b1[u]] - Ji[a1[u] * d + p] * J[qq * d + b1[u]]);
+      geo[64 + r * ns0 + s1] = v;
+    } else {
+      const int f = q - ng - nh;
+      double gn[3] = {0, 0, 0}, nn = 0;
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) gn[a] += Gi[a * d + b] * nhat[f * d + b];
+      for (int a = 0; a < d; ++a) nn += gn[a] * nhat[f * d + a];
+      for (int a = 0; a < d; ++a) geo[88 + f * d + a] = gn[a] / nn;
+    }
+  }
+  sync();
+  if (lane == 0) {
+    small_inverse(ns0, gm, ginv);
+    // symmetrise and Cholesky g^{-1} = L L^T
+    double* L = geo;
+    for (int i = 0; i < 64; ++i) L[i] = 0.0;
+    for (int j = 0; j < ns0; ++j) {
+      double sdiag = ginv[j * ns0 + j];
+      for (int p = 0; p < j; ++p) sdiag -= L[j * ns0 + p] * L[j * ns0 + p];
+      const double ljj = sqrt(sdiag);
+      L[j * ns0 + j] = ljj;
+      for (int i = j + 1; i < ns0; ++i) {
+        double v = 0.5 * (ginv[i * ns0 + j] + ginv[j * ns0 + i]);
+        for (int p = 0; p < j; ++p) v -= L[i * ns0 + p] * L[j * ns0 + p];
+        L[i * ns0 + j] = v / ljj;
+      }
+    }
+  }
+  sync();
 }
 
 // Row i and column j (j <= i) of packed lower-triangle position q = i(i+1)/2 + j.
@@ -248,23 +284,45 @@ __host__ __device__ inline void packed_ij(int q, int& i, int& j) {
   j = q - r * (r + 1) / 2;
 }
 
-// Lane-parallel Cholesky of the n x n SPD matrix A (row-major, lower factor in place).
+// Lane-parallel Cholesky of the n x n SPD matrix A (row-major, lower triangle used), applied at
+// the same time to the m right-hand-side columns of V (row-major [n][m]):  on return the lower
+// triangle of A holds the factor Lc (A = Lc Lc^T) and V holds Lc^{-1} V.  Right-looking
+// elimination on the augmented matrix [A | V] without pivoting: for pivot j every entry (i, c),
+// j < c <= i, of A and every V[i][.], i > j, takes its update from column j and row j, which no
+// lane writes during that step, so one barrier per pivot suffices.  The scaling by the square
+// roots of the pivots follows in two passes.
 template <class Sync>
-__host__ __device__ inline void chol_inplace(int n, double* A, int lane, int nl, Sync sync) {
-  for (int j = 0; j < n; ++j) {
-    if (lane == 0) A[j * n + j] = sqrt(A[j * n + j]);
-    sync();
-    double ljj = A[j * n + j];
-    for (int i = j + 1 + lane; i < n; i += nl) A[i * n + j] /= ljj;
-    sync();
-    // trailing update of the lower triangle
-    int m = n - j - 1;
-    for (int t = lane; t < m * m; t += nl) {
-      int i = j + 1 + t / m, l = j + 1 + t % m;
-      if (l <= i) A[i * n + l] -= A[i * n + j] * A[l * n + j];
+__host__ __device__ inline void chol_solve_inplace(int n, double* A, int m, double* V, int lane, int nl, Sync sync) {
+  for (int j = 0; j + 1 < n; ++j) {
+    const double inv = 1.0 / A[j * n + j];
+    const int r = n - j - 1;   // rows below the pivot
+    const int wa = r, wt = r + m;
+    for (int t = lane; t < r * wt; t += nl) {
+      const int i = j + 1 + t / wt, c = t - (t / wt) * wt;
+      const double f = A[i * n + j] * inv;
+      if (c < wa) {
+        const int cc = j + 1 + c;
+        if (cc <= i) A[i * n + cc] -= f * A[cc * n + j];
+      } else {
+        const int cv = c - wa;
+        V[i * m + cv] -= f * V[j * m + cv];
+      }
     }
     sync();
   }
+  // A = L D L^T with unit L (stored as L D); Lc = L D^{1/2}, Lc^{-1} V = D^{-1/2} (L^{-1} V)
+  for (int t = lane; t < n * (n + m); t += nl) {
+    const int i = t / (n + m), c = t - i * (n + m);
+    const double di = A[i * n + i];
+    if (c < n) {
+      if (c < i) A[i * n + c] /= sqrt(A[c * n + c]);
+    } else {
+      V[i * m + (c - n)] /= sqrt(di);
+    }
+  }
+  sync();
+  for (int i = lane; i < n; i += nl) A[i * n + i] = sqrt(A[i * n + i]);
+  sync();
 }
 
 // Lowest-order variant (Sec. 7): raw row of the rotation flux function phi_f = (x - x_f) / (d |T|)
@@ -299,44 +357,53 @@ __host__ __device__ inline void condense_element_t(const ElemSizes& s, const Ele
                                                    const int* sgn, double nu, ElemWork w, int lane, int nl,
                                                    Sync sync) {
   const int nraw = s.n_raw, ns0 = s.n_s0, nA = s.n_A, nu_ = s.n_u, ncc = s.n_cc, d = s.d, rs = raw_stride(s);
-  if (lane == 0) {
-    elem_geometry(s, X, t.nhat, w.geo);
-    w.geo[102] = nu;
-  }
-  sync();
+  elem_geometry(s, X, t.nhat, w.geo, w.A, lane, nl, sync);   // w.A is free until the product pass
+  if (lane == 0) w.geo[102] = nu;
   const double* L = w.geo;
   const double* h = w.geo + 64;
   const double* wf = w.geo + 88;
   const double adet = w.geo[100];
   const double cB = sqrt(nu / adet);
-  // ---- Bt rows ----
-  for (int r = lane; r < nA; r += nl) {
-    double* row = w.Bt + r * rs;
-    if (r < nu_) {
-      for (int j = 0; j < nraw; ++j) row[j] = t.B0[r * nraw + j];
-      if (r < (d + 1) * s.nF) {
-        int f = r / s.nF, jF = r % s.nF;
-        for (int a = 0; a < d; ++a) {
-          double wa = wf[f * d + a];
-          const double* R = t.Rf + ((f * d + a) * s.nF + jF) * nraw;
-          for (int j = 0; j < nraw; ++j) row[j] -= wa * R[j];
+  // ---- rows of Bt and Ct, one work item per (row, polynomial block i): the n_s0 raw entries of
+  // block i are formed and transformed by L, times cB for Bt (the whitening (I (x) L)) ----
+  const int nkb = s.nk, nrows = nA + ncc;
+  for (int q = lane; q < nrows * nkb; q += nl) {
+    const int r = q / nkb, i = q - r * nkb;
+    double tmp[8];
+    double scale = 1.0;
+    bool zero = false;
+    if (r < nA) {
+      scale = cB;
+      if (r < nu_) {
+        for (int p = 0; p < ns0; ++p) tmp[p] = t.B0[r * nraw + i * ns0 + p];
+        if (r < (d + 1) * s.nF) {
+          const int f = r / s.nF, jF = r % s.nF;
+          for (int a2 = 0; a2 < d; ++a2) {
+            const double wa = wf[f * d + a2];
+            const double* R = t.Rf + ((f * d + a2) * s.nF + jF) * nraw + i * ns0;
+            for (int p = 0; p < ns0; ++p) tmp[p] -= wa * R[p];
+          }
         }
+      } else if (LO && is_rot_dof(s, r)) {
+        continue;   // lowest-order rotation rows: filled below
+      } else {
+        const double* Bh = t.Bh + (r - nu_) * nraw + i * ns0;
+        for (int p = 0; p < ns0; ++p) tmp[p] = adet * Bh[p];
       }
-    } else if (LO && is_rot_dof(s, r)) {
-      continue;   // lowest-order rotation rows: filled below
+    } else if (r - nA < s.n_con) {
+      const double* C = t.Ccon + (r - nA) * nraw + i * ns0;
+      for (int p = 0; p < ns0; ++p) tmp[p] = C[p];
     } else {
-      const double* Bh = t.Bh + (r - nu_) * nraw;
-      for (int j = 0; j < nraw; ++j) row[j] = adet * Bh[j];
+      const int rr = r - nA - s.n_con, kr = rr / s.n_p, ip = rr - kr * s.n_p;
+      zero = i != ip;
+      for (int p = 0; p < ns0; ++p) tmp[p] = zero ? 0.0 : h[kr * ns0 + p];
     }
-    // transform by (I (x) L) * cB
-    for (int i = 0; i < s.nk; ++i) {
-      double tmp[8];
-      for (int q = 0; q < ns0; ++q) tmp[q] = row[i * ns0 + q];
-      for (int q = 0; q < ns0; ++q) {
-        double v = 0;
-        for (int p = q; p < ns0; ++p) v += tmp[p] * L[p * ns0 + q];
-        row[i * ns0 + q] = cB * v;
-      }
+    double* row = (r < nA ? w.Bt + r * rs : w.Ct + (r - nA) * rs) + i * ns0;
+    for (int q2 = 0; q2 < ns0; ++q2) {
+      double v = 0;
+      if (!zero)
+        for (int p = q2; p < ns0; ++p) v += tmp[p] * L[p * ns0 + q2];
+      row[q2] = scale * v;
     }
   }
   if (LO)
@@ -353,28 +420,6 @@ __host__ __device__ inline void condense_element_t(const ElemSizes& s, const Ele
         }
       }
     }
-  // ---- Ct rows: nt constraints, then rotation constraints ----
-  for (int r = lane; r < ncc; r += nl) {
-    double* row = w.Ct + r * rs;
-    if (r < s.n_con) {
-      const double* C = t.Ccon + r * nraw;
-      for (int i = 0; i < s.nk; ++i)
-        for (int q = 0; q < ns0; ++q) {
-          double v = 0;
-          for (int p = q; p < ns0; ++p) v += C[i * ns0 + p] * L[p * ns0 + q];
-          row[i * ns0 + q] = v;
-        }
-    } else {
-      int rr = r - s.n_con;
-      int kr = rr / s.n_p, ip = rr % s.n_p;
-      for (int j = 0; j < nraw; ++j) row[j] = 0.0;
-      for (int q = 0; q < ns0; ++q) {
-        double v = 0;
-        for (int p = q; p < ns0; ++p) v += h[kr * ns0 + p] * L[p * ns0 + q];
-        row[ip * ns0 + q] = v;
-      }
-    }
-  }
   sync();
   // ---- one pass over A = Adiv + Bt Bt^T (lower), V = Ct Bt^T, Sc = Ct Ct^T (lower) ----
   const double cdiv = nu / (d * adet);
@@ -425,16 +470,8 @@ __host__ __device__ inline void condense_element_t(const ElemSizes& s, const Ele
     *out = v0 + v1 + add;
   }
   sync();
-  chol_inplace(ncc, w.Sc, lane, nl, sync);
-  // ---- Z = Lc^{-1} V, column by column (each lane owns columns) ----
-  for (int c = lane; c < nA; c += nl) {
-    for (int i = 0; i < ncc; ++i) {
-      double v = w.V[i * nA + c];
-      for (int p = 0; p < i; ++p) v -= w.Sc[i * ncc + p] * w.V[p * nA + c];
-      w.V[i * nA + c] = v / w.Sc[i * ncc + i];
-    }
-  }
-  sync();
+  // ---- Sc = Lc Lc^T and Z = Lc^{-1} V in one elimination ----
+  chol_solve_inplace(ncc, w.Sc, nA, w.V, lane, nl, sync);
   // ---- A -= Z^T Z (packed lower), signs, symmetric fill ----
   const int nfd = (d + 1) * s.nF;
   for (int q = lane; q < PA; q += nl) {
@@ -584,15 +621,7 @@ __host__ __device__ inline void bubble_condense(const ElemSizes& s, const double
     Tm[t] = A[(ob + i) * nA + coupling_to_local(s, c)];
   }
   sync();
-  chol_inplace(no, Lo, lane, nl, sync);
-  // forward substitution Lo Y = Aoc (columns per lane)
-  for (int c = lane; c < nc; c += nl)
-    for (int i = 0; i < no; ++i) {
-      double v = Tm[i * nc + c];
-      for (int p = 0; p < i; ++p) v -= Lo[i * no + p] * Tm[p * nc + c];
-      Tm[i * nc + c] = v / Lo[i * no + i];
-    }
-  sync();
+  chol_solve_inplace(no, Lo, nc, Tm, lane, nl, sync);   // Aoo = Lo Lo^T, Tm = Lo^{-1} Aoc
   // Ad = Acc - Y^T Y
   for (int t = lane; t < nc * nc; t += nl) {
     int i = t / nc, j = t % nc;

@@ -64,11 +64,13 @@ template <class R, int LO>
 __device__ __forceinline__ void condense_one(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu,
                                              const KOp& K, R* Fs, R* G, R* Aoi, double* base, int64_t T) {
   const int lane = threadIdx.x, nl = blockDim.x;
-  ElemWork w = elem_work_carve(s, base);
-  double* bw = base + elem_work_doubles(s);                // bubble work
-  double* Xs = bw + s.n_bub * s.n_bub + s.n_bub * s.n_c;   // (d+1)*d coords
+  // slot layout: coordinates and signs (24 doubles), then the element workspace; the bubble
+  // condensation's work and staging reuse the rows of Bt and Ct, which are dead once A_T is formed
+  double* Xs = base;                                       // (d+1)*d coords
   int* sg = (int*)(Xs + 16);
-  double* Adt = Xs + 24;                                   // staging (FP64)
+  ElemWork w = elem_work_carve(s, base + 24);
+  double* bw = w.Bt;                                       // bubble work
+  double* Adt = bw + s.n_bub * s.n_bub + s.n_bub * s.n_c;  // staging (FP64)
   double* Gt = Adt + s.n_c * s.n_c;
   double* Ait = Gt + s.n_bub * s.n_c;
   ElemTables et{t.B0, t.Rf, t.Bh, t.Ccon, t.Adiv, t.nhat, t.Wmom};
@@ -136,7 +138,7 @@ __device__ __forceinline__ void condense_one(const ElemSizes& s, const DevTables
 // One thread block per element (grid-stride).  Workspace in dynamic shared memory when
 // it fits, else in a global scratch slot per resident block.
 template <class R, bool SMEM, int LO>
-__global__ void __launch_bounds__(256) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, KOp K, R* Fs,
+__global__ void __launch_bounds__(256, 2) k_condense(ElemSizes s, DevTables t, DevMesh m, double nu, KOp K, R* Fs,
                                                   R* G, R* Aoi, double* gscratch, int64_t slot_doubles) {
   extern __shared__ double smem[];
   double* base = SMEM ? smem : gscratch + (int64_t)blockIdx.x * slot_doubles;
@@ -159,9 +161,16 @@ __global__ void __launch_bounds__(256) k_condense_batch(const CondenseItem<R>* _
   }
 }
 
+// Doubles of the bubble condensation's work and staging, which condense_one places over the rows of
+// Bt and Ct ((n_A + n_cc) * raw_stride doubles); the host checks that they fit there.
+static int64_t bubble_doubles(const ElemSizes& s) {
+  return 2 * (int64_t)s.n_bub * s.n_bub + 2 * (int64_t)s.n_bub * s.n_c + (int64_t)s.n_c * s.n_c;
+}
+static bool bubble_fits(const ElemSizes& s) {
+  return bubble_doubles(s) <= (int64_t)(s.n_A + s.n_cc) * raw_stride(s);
+}
 static int64_t condense_slot_doubles(const ElemSizes& s) {
-  int64_t v = elem_work_doubles(s) + s.n_bub * s.n_bub + s.n_bub * s.n_c + 24 + s.n_c * s.n_c + s.n_bub * s.n_c +
-              s.n_bub * s.n_bub;
+  const int64_t v = 24 + elem_work_doubles(s);
   return (v + 31) / 32 * 32;
 }
 
@@ -182,6 +191,7 @@ template <class R, int LO>
 static cudaError_t launch_condense_t(const ElemSizes& s, const DevTables& t, const DevMesh& m, double nu, KOp K,
                                      R* Fs, R* G, R* Aoi, double* scratch, int64_t scratch_doubles, cudaStream_t st) {
   const int64_t slot = condense_slot_doubles(s);
+  if (!bubble_fits(s)) return cudaErrorInvalidValue;
   int dev = 0, nsm = 0, maxsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -227,6 +237,7 @@ cudaError_t launch_condense_batch(const CondenseItem<R>* items_dev, const Conden
                                   double* scratch, int64_t scratch_doubles, cudaStream_t st) {
   int64_t slot = 0, total = 0;
   for (int i = 0; i < nitems; ++i) {
+    if (!bubble_fits(items_host[i].s)) return cudaErrorInvalidValue;
     slot = std::max<int64_t>(slot, condense_slot_doubles(items_host[i].s));
     total += items_host[i].m.ne;
   }
@@ -519,6 +530,83 @@ __global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m,
   }
 }
 
+// y = K x from the FP32 leading parts hi = fl(A_T) of the packed float pairs alone, with FP32 products
+// and sums (x rounded to FP32): half the bytes of the double-float apply and one FMA per entry.
+// Used inside the refinement cycles of the mixed form, whose residuals are formed exactly.
+template <class S>
+__global__ void __launch_bounds__(256) k_apply_K_f32(S s, DevTables t, DevMesh m, Layout L,
+                                                     const float* __restrict__ Ahi, const double* __restrict__ x,
+                                                     double* y, int EB, const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ float skf[];
+  const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d, nfd = (s.d + 1) * s.nF;
+  const int per = nA + np_, pp = packed_pad(s);
+  float* Ah = skf;                    // [EB][pp]
+  float* xs = Ah + EB * pp;           // [EB][per]
+  int* er = (int*)(xs + EB * per);    // [EB][4]
+  float* sg = (float*)(er + EB * 4);  // [EB][4]
+  const int tid = threadIdx.x;
+  const int64_t T0 = (int64_t)blockIdx.x * EB;
+  const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
+  if (tid < EB * 4) {
+    int e = tid >> 2, f = tid & 3;
+    int64_t T = T0 + e;
+    bool ok = e < nvalid && f <= d;
+    er[tid] = ok ? m.elem_rank[T * (d + 1) + f] : -1;
+    sg[tid] = ok ? (float)m.signs[T * (d + 1) + f] : 0.f;
+  }
+  vcopy16<float>(Ah, Ahi + T0 * pp, nvalid * pp, tid, blockDim.x);
+  __syncthreads();
+  for (int q = tid; q < nvalid * per; q += blockDim.x) {
+    const int e = q / per, i = q - e * per;
+    const int64_t T = T0 + e;
+    double v;
+    if (i < nA) {
+      int64_t g = local_to_global(s, L, er + e * 4, T, i);
+      v = g < 0 ? 0.0 : x[g];
+    } else {
+      v = x[L.off_p + T * np_ + (i - nA)];
+    }
+    xs[q] = (float)v;
+  }
+  __syncthreads();
+  for (int q = tid; q < nvalid * per; q += blockDim.x) {
+    const int e = q / per, i = q - e * per;
+    const int64_t T = T0 + e;
+    const float* xe = xs + e * per;
+    float v0 = 0.f, v1 = 0.f;
+    if (i < nA) {
+      const float* ah = Ah + e * pp;
+      const int row = i * (i + 1) / 2;
+      int j = 0;
+      for (; j + 1 <= i; j += 2) {
+        v0 = __fmaf_rn(ah[row + j], xe[j], v0);
+        v1 = __fmaf_rn(ah[row + j + 1], xe[j + 1], v1);
+      }
+      if (j <= i) v0 = __fmaf_rn(ah[row + j], xe[j], v0);
+      for (int jj = i + 1; jj < nA; ++jj) v1 = __fmaf_rn(ah[jj * (jj + 1) / 2 + i], xe[jj], v1);
+      if (i < nu_) {  // (B^T x_p)_i = -s_i sum_j Bhat[j][i] x_p[j]
+        const float sgn = i < nfd ? sg[e * 4 + i / s.nF] : 1.f;
+        float bt = 0.f;
+        for (int p = 0; p < np_; ++p) bt = __fmaf_rn(t.Bp_hi[p * nu_ + i], xe[nA + p], bt);
+        v0 -= sgn * bt;
+      }
+      const double v = (double)v0 + (double)v1;
+      int64_t g = local_to_global(s, L, er + e * 4, T, i);
+      if (g < 0) continue;
+      if (i >= nfd && i < nu_) y[g] = v;     // bubble: owned by T
+      else atomicAdd(&y[g], v);             // facet dof: exactly two contributions into 0
+    } else {
+      const int jp = i - nA;
+      for (int c = 0; c < nu_; ++c) {
+        const float sgn = c < nfd ? sg[e * 4 + c / s.nF] : 1.f;
+        v0 = __fmaf_rn(-sgn * t.Bp_hi[jp * nu_ + c], xe[c], v0);
+      }
+      y[L.off_p + T * np_ + jp] = (double)v0;
+    }
+  }
+}
+
 __global__ void k_zero_facet(const Layout L, double* y, const int* stop) {
   if (stop && *stop) return;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -586,6 +674,36 @@ cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh
       k_apply_K<decltype(sz), true><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.AT, x, y, EB, stop);
     else
       k_apply_K<decltype(sz), false><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.AT, x, y, EB, stop);
+    note_launch();
+    prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_K_f32(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, KOp K,
+                               const double* x, double* y, const int* stop, cudaStream_t st) {
+  if (!K.Ahi) return cudaErrorInvalidValue;
+  k_zero_facet<<<sm_count() * 4, 256, 0, st>>>(L, y, stop);
+  note_launch();
+  const int per = s.n_A + s.n_p;
+  // algorithmic: packed symmetric A_T in FP32, x read once, y written once
+  const double alg_bytes = (double)m.ne * s.n_A * (s.n_A + 1) / 2 * 4.0 + 16.0 * L.ndof;
+  const double alg_flops = 2.0 * (double)m.ne * ((double)s.n_A * s.n_A + 2.0 * s.n_u * s.n_p);
+  const size_t per_bytes = ((size_t)packed_pad(s) + per) * sizeof(float) + 4 * (sizeof(int) + sizeof(float));
+  int EB = (int)((24 * 1024) / per_bytes);
+  if (EB < 1) EB = 1;
+  if (EB > 16) EB = 16;
+  const int threads = EB * per <= 128 ? 128 : 256;
+  const size_t sm = (size_t)EB * per_bytes + 64;
+  const int64_t blocks = (m.ne + EB - 1) / EB;
+  dispatch_sizes(s, [&](auto sz) {
+    static std::atomic<bool> set{false};
+    if (!set.load(std::memory_order_acquire)) {
+      cudaFuncSetAttribute(k_apply_K_f32<decltype(sz)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set.store(true, std::memory_order_release);
+    }
+    prof_begin(PROF_APPLY, st);
+    k_apply_K_f32<decltype(sz)><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.Ahi, x, y, EB, stop);
     note_launch();
     prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
   });
