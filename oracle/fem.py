@@ -13,7 +13,8 @@ Spaces (Sec. 3, eqs. fes_V .. fes_Vbar), for k >= 2 on a simplex T:
       (ii) d=2: (-y, x) x^a y^b, a+b = k-2, a descending;
            d=3: x cross (x^alpha e_c), |alpha| = k-2, alpha in descending
            lexicographic order, c minor, skipping c = 3 when alpha_3 >= 1
-      (the first-kind Nedelec space N_{k-1}).
+      (the first-kind Nedelec space N_{k-1}), this list made L2(T_hat)-orthonormal in
+      list order (Gram-Schmidt) so that the dual basis stays well scaled at high k.
   Global facet functions carry the orientation sign s_{T,f} so that their
   moment is taken against the global facet normal n_F.
 * Vhat_h: on each facet q_j(s) e_m with q_j of degree <= k-1 and e_m the facet
@@ -84,8 +85,33 @@ def facet_local_vertices(d, f):
     return [v for v in range(d + 1) if v != f]
 
 
-def interior_test_functions(d: int, k: int, xh: np.ndarray) -> np.ndarray:
-    """g_m(xhat) at reference points xh[nq, d] -> [nq, n_bub, d] (list (i)+(ii))."""
+def interior_test_functions(d: int, k: int, xh: np.ndarray, basis: str = "orthonormal") -> np.ndarray:
+    """g_m(xhat) at reference points xh[nq, d] -> [nq, n_bub, d].
+
+    The dof contract's interior moment functions are the list (i)+(ii) below made L2(T_hat)-orthonormal
+    in list order (Gram-Schmidt, i.e. the rows of L^{-1} for the Cholesky factor L of the list's Gram
+    matrix on T_hat).  Without it the monomial part (ii) makes the dual BDM basis badly scaled at high k
+    (2D k = 6: element matrices with entries near 1e11 around facet Schur complements near 1e2).
+    basis="monomial": the list itself (the same BDM space, another bubble basis)."""
+    raw = _interior_list(d, k, xh)
+    if basis == "monomial" or raw.shape[1] == 0:
+        return raw
+    return np.einsum("qna,mn->qma", raw, _interior_orthonormaliser(d, k))
+
+
+@functools.lru_cache(maxsize=None)
+def _interior_orthonormaliser(d: int, k: int) -> np.ndarray:
+    """L^{-1} with L L^T the Gram matrix of the interior list on T_hat (exact collapsed Gauss rule)."""
+    x, w = polys.quadrature(d, k + 1)
+    g = _interior_list(d, k, x)
+    G = np.einsum("q,qma,qna->mn", w, g, g)
+    return np.linalg.inv(np.linalg.cholesky(G))
+
+
+def _interior_list(d: int, k: int, xh: np.ndarray) -> np.ndarray:
+    """The list (i) psi_a e_c, deg psi_a <= k-2 (a-major, c-minor), then (ii) the Nedelec-type
+    functions (-y, x) x^a y^b (2D, a descending) or x cross (x^alpha e_c) (3D, alpha descending
+    lexicographic, c minor, c = 3 skipped when alpha_3 >= 1), |alpha| = k-2, at xh[nq, d]."""
     out = []
     if k >= 2:
         psi, _ = polys.dubiner(d, k - 2, xh)
@@ -175,13 +201,12 @@ def _ref_rules(d, q):
 
 
 def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None,
-                 velocity_only: bool = False, ortho_bubbles: bool = False) -> ElementData:
+                 velocity_only: bool = False, bubble_basis: str = "orthonormal") -> ElementData:
     """Physical bases of all spaces on the elements with vertex coordinates X[E, d+1, d].
 
-    ortho_bubbles: the interior moment functions g_m are replaced by an L2(T_hat)-orthonormal basis
-    of their span (the same BDM space and the same facet functions, a different bubble basis; for
-    quantities that eliminate the bubbles, such as A^d_T, only the rounding changes).  Not the dof
-    contract: for experiments at high k only.
+    bubble_basis: "orthonormal" (the dof contract) or "monomial" (the unorthonormalised interior list;
+    the same BDM space and facet functions, another bubble basis: quantities that eliminate the bubbles,
+    such as A^d_T, change only by rounding).
 
     velocity_only: only U, DU, divU and P are evaluated (the other fields are None)."""
     E_, dp1, d = X.shape
@@ -254,11 +279,7 @@ def element_data(X: np.ndarray, signs: np.ndarray, k: int, q: int | None = None,
         Phi = amb_vals(pv)                                      # [nqf, n_full, d]
         flux = np.einsum("qca,ea->eqc", Phi, fn[:, f, :])       # [E, nqf, n_full]
         C[:, f * nF:(f + 1) * nF, :] = np.einsum("eq,qj,eqc->ejc", fw[:, f, :], qF, flux)
-    g = interior_test_functions(d, k, xv)                       # [nq, n_bub, d]
-    if ortho_bubbles and g.shape[1]:
-        Gm = np.einsum("q,qma,qna->mn", wv, g, g)
-        Lc = np.linalg.cholesky(Gm)
-        g = np.einsum("qna,mn->qma", g, np.linalg.inv(Lc))      # rows of L^{-1}: orthonormal set
+    g = interior_test_functions(d, k, xv, bubble_basis)         # [nq, n_bub, d]
     gphys = np.einsum("eab,qmb->eqma", JinvT, g)
     Phiv = amb_vals(psi)                                        # [nq, n_full, d]
     C[:, (d + 1) * nF:, :] = np.einsum("eq,qca,eqma->emc", wq, Phiv, gphys)
@@ -369,7 +390,7 @@ def stabilisation_weight(X: np.ndarray, nu: float, lo_stab: int) -> np.ndarray:
     return nu * diam2
 
 
-def element_matrices(X, signs, k, nu, lo_stab: int = 0, ortho_bubbles: bool = False):
+def element_matrices(X, signs, k, nu, lo_stab: int = 0, bubble_basis: str = "orthonormal"):
     """Local blocks of eq. (bigfemSPmat) on every element of the batch.
 
     Returns dict of arrays [E, rows, cols]:
@@ -381,7 +402,7 @@ def element_matrices(X, signs, k, nu, lo_stab: int = 0, ortho_bubbles: bool = Fa
       Bp  = -(div phi^u_j, phi^p_i)_T                     (weak form sign, reading R18)
       Mu  = (phi^u_i, phi^u_j)_T
     """
-    D = element_data(X, signs, k, ortho_bubbles=ortho_bubbles)
+    D = element_data(X, signs, k, bubble_basis=bubble_basis)
     d = X.shape[2]
     out = {}
     out["M"] = np.einsum("eq,eqiab,eqjab->eij", D.wq, D.S, D.S) / nu

@@ -21,7 +21,7 @@ largest eigenvalue is not 1: the proof of Lemma SPD squares a sum of d + 2 terms
 sum of squares, so the upper bound holds with d + 2 in place of 1 (reading R22).  With the dual BDM
 basis of the dof contract the element matrices lose digits as k grows (the rigid-body kernel is no
 longer resolved at k = 8); the bubble Schur complements do not depend on the bubble basis, so the
-table is computed with an L2-orthonormal bubble basis (fem.element_data(ortho_bubbles=True)), which
+table is computed with the contract's L2-orthonormal bubble basis (fem.interior_test_functions), which
 keeps the kernel gap near 1e12 up to k = 8 and reproduces the contract basis's values where both hold.
 """
 from __future__ import annotations
@@ -40,18 +40,18 @@ def unit_tetrahedron(d: int = 3) -> np.ndarray:
     return np.vstack([np.zeros(d), np.eye(d)])[None]
 
 
-def element_forms(k: int, nu: float = 1.0, X: np.ndarray | None = None, ortho_bubbles: bool = False):
+def element_forms(k: int, nu: float = 1.0, X: np.ndarray | None = None, bubble_basis: str = "orthonormal"):
     """(A_T, N_T, sizes) on one element: the condensed matrix and the HDG-norm matrix over the local
-    (u, uhat) dofs, local order [u_d | u_o | uhat].  ortho_bubbles: an L2-orthonormal bubble basis
+    (u, uhat) dofs, local order [u_d | u_o | uhat].  bubble_basis: "orthonormal" (the contract) or "monomial"
     (fem.element_data); both forms then eliminate the same bubble space in a better-scaled basis."""
     X = unit_tetrahedron() if X is None else X
     d = X.shape[2]
     signs = np.ones((1, d + 1), dtype=np.int64)
     sz = fem.local_sizes(d, k)
-    mats = fem.element_matrices(X, signs, k, nu, ortho_bubbles=ortho_bubbles)
+    mats = fem.element_matrices(X, signs, k, nu, bubble_basis=bubble_basis)
     AT = system.condense(SimpleNamespace(mats=mats, sz=sz))[0]
     q = k + 2
-    D = fem.element_data(X, signs, k, q=q, ortho_bubbles=ortho_bubbles)
+    D = fem.element_data(X, signs, k, q=q, bubble_basis=bubble_basis)
     nu_, nA, nhF = sz["n_u"], sz["n_A"], sz["n_hatF"]
     # ||eps(u)||_T^2
     eps = 0.5 * (D.DU + np.swapaxes(D.DU, -1, -2))                    # [1, nq, n_u, d, d]
@@ -94,11 +94,11 @@ def schur_on_coupling(M: np.ndarray, sz: dict) -> np.ndarray:
     return Mcc - Mco @ np.linalg.solve(Moo, Mco.T)
 
 
-def gamma(k: int, nu: float = 1.0, X: np.ndarray | None = None, ortho_bubbles: bool = False):
+def gamma(k: int, nu: float = 1.0, X: np.ndarray | None = None, bubble_basis: str = "orthonormal"):
     """(gamma, lambda_max, gap) of the pencil (A^d_T, nu N^d_T) on one element.  The common kernel is
     the d(d+1)/2 rigid-body motions; gap = (smallest nonzero) / (largest kernel) eigenvalue of the
     scaled N^d_T tells whether the element matrices still resolve it (about 1e10 and more when they do)."""
-    AT, N, sz = element_forms(k, nu, X, ortho_bubbles)
+    AT, N, sz = element_forms(k, nu, X, bubble_basis)
     Ad = schur_on_coupling(AT, sz)
     Nd = schur_on_coupling(N, sz)
     Ad, Nd = 0.5 * (Ad + Ad.T), 0.5 * (Nd + Nd.T)
@@ -116,7 +116,7 @@ def gamma(k: int, nu: float = 1.0, X: np.ndarray | None = None, ortho_bubbles: b
 
 if __name__ == "__main__":
     # the table of gamma(k) on the unit tetrahedron, k = 2..8 (about three minutes), in the
-    # orthonormal bubble basis (the dual basis of the dof contract loses the kernel at k = 8)
+    # the contract's orthonormal bubble basis (the monomial one loses the kernel at k = 8)
     for k in range(2, 9):
-        g, lmax, gap = gamma(k, ortho_bubbles=True)
+        g, lmax, gap = gamma(k)
         print(f"k = {k}: gamma = {g:.3f}, lambda_max = {lmax:.3f}, kernel gap = {gap:.1e}", flush=True)

@@ -1,6 +1,7 @@
 // Reference-element tables of the MCS discretization (see reference.h).
 #include "reference.h"
 
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -78,6 +79,85 @@ static void gauss_legendre01(int q, std::vector<double>& x, std::vector<double>&
     x[i] = 0.5 * (1.0 - t);
     w[i] = 1.0 / ((1.0 - t * t) * dp * dp);  // 2/((1-t^2) P'^2) halved for [0,1]
   }
+}
+
+// Gauss-Jacobi rule with q nodes on [-1, 1] for the weight (1 - x)^alpha: Newton's method on
+// P_q^{(alpha,0)} (three-term recurrence), each root deflated by the ones already found;
+// weights 2^{alpha+1} / ((1 - x^2) P_q'(x)^2).
+static void jacobi_p(int q, double alpha, double x, double& p, double& dp) {
+  double p0 = 1.0, p1 = 0.5 * ((alpha + 2.0) * x + alpha);
+  if (q == 0) { p = 1.0; dp = 0.0; return; }
+  for (int n = 2; n <= q; ++n) {
+    const double c = 2.0 * n + alpha;
+    const double a1 = 2.0 * n * (n + alpha) * (c - 2.0);
+    const double a2 = (c - 1.0) * (c * (c - 2.0) * x + alpha * alpha);
+    const double a3 = 2.0 * (n + alpha - 1.0) * (n - 1.0) * c;
+    const double p2 = (a2 * p1 - a3 * p0) / a1;
+    p0 = p1;
+    p1 = p2;
+  }
+  p = p1;
+  // (2q + alpha)(1 - x^2) P_q' = q (alpha - (2q + alpha) x) P_q + 2 (q + alpha) q P_{q-1}
+  const double c = 2.0 * q + alpha;
+  dp = (q * (alpha - c * x) * p1 + 2.0 * (q + alpha) * q * p0) / (c * (1.0 - x * x));
+}
+
+static void gauss_jacobi(int q, double alpha, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(q, 0.0);
+  w.assign(q, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < q; ++i) {
+    double t = -std::cos(pi * (i + 0.75) / (q + 0.5));   // ascending starting points
+    for (int it = 0; it < 200; ++it) {
+      double p, dp;
+      jacobi_p(q, alpha, t, p, dp);
+      double sdef = 0.0;                                 // deflation by the roots found
+      for (int j = 0; j < i; ++j) sdef += 1.0 / (t - x[j]);
+      const double dt = p / (dp - sdef * p);
+      t -= dt;
+      if (std::fabs(dt) < 1e-15) break;
+    }
+    double p, dp;
+    jacobi_p(q, alpha, t, p, dp);
+    x[i] = t;
+    w[i] = std::pow(2.0, alpha + 1.0) / ((1.0 - t * t) * dp * dp);
+  }
+  // ascending nodes
+  for (int i = 1; i < q; ++i)
+    for (int j = i; j > 0 && x[j] < x[j - 1]; --j) {
+      std::swap(x[j], x[j - 1]);
+      std::swap(w[j], w[j - 1]);
+    }
+}
+
+// Collapsed Gauss rule on the reference simplex T_n with q points per direction (the load rule of the
+// dof contract): Gauss-Jacobi nodes a (alpha 0), b (alpha 1), c (alpha 2) on [-1, 1] mapped by
+// z = (1 + c)/2, y = (1 + b)(1 - c)/4, x = (1 + a)(1 - b)(1 - c)/8 (2D: y = (1 + b)/2,
+// x = (1 + a)(1 - b)/4), weights w_a w_b w_c / 64 (2D: / 8).
+void collapsed_gauss_rule(int n, int q, std::vector<double>& pts, std::vector<double>& w) {
+  std::vector<double> a, wa, b, wb, c, wc;
+  gauss_jacobi(q, 0.0, a, wa);
+  gauss_jacobi(q, 1.0, b, wb);
+  gauss_jacobi(q, 2.0, c, wc);
+  pts.clear();
+  w.clear();
+  if (n == 2) {
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) {
+        pts.push_back((1 + a[i]) * (1 - b[j]) / 4);
+        pts.push_back((1 + b[j]) / 2);
+        w.push_back(wa[i] * wb[j] / 8);
+      }
+    return;
+  }
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j)
+      for (int l = 0; l < q; ++l) {
+        pts.push_back((1 + a[i]) * (1 - b[j]) * (1 - c[l]) / 8);
+        pts.push_back((1 + b[j]) * (1 - c[l]) / 4);
+        pts.push_back((1 + c[l]) / 2);
+        w.push_back(wa[i] * wb[j] * wc[l] / 64);
+      }
 }
 
 void duffy_rule(int n, int q, std::vector<double>& pts, std::vector<double>& w) {
@@ -304,7 +384,8 @@ RefGeom ref_geom(int d) {
   return g;
 }
 
-// interior test functions g_m(xhat): the first-kind Nedelec list of the dof contract
+// interior test functions g_m(xhat) before orthonormalisation: the first-kind Nedelec list of the dof
+// contract (build_reference makes it L2(T_hat)-orthonormal)
 void interior_tests(int d, int k, const double* x, std::vector<double>& out /* [nb][d] */) {
   out.clear();
   int nkm2 = n_poly(d, k - 2);
@@ -408,14 +489,56 @@ RefTables build_reference(int d, int k) {
         for (int j = 0; j < nF; ++j) C[(f * nF + j) * s.n_full + c] += ws * fl * qF[q * nF + j];
       }
     }
+  // interior moment functions: the contract's list made L2(T_hat)-orthonormal in list order, i.e.
+  // g = Lg^{-1} g_list with Lg Lg^T the Gram matrix of the list on T_hat (the rule is exact for it)
+  const int nb = s.n_bub;
+  std::vector<double> Lgi(std::max(1, nb * nb), 0.0);
   std::vector<double> gt;
+  if (nb > 0) {
+    std::vector<double> Gm(nb * nb, 0.0);
+    for (int q = 0; q < nq; ++q) {
+      interior_tests(d, k, &xv[q * d], gt);
+      for (int m = 0; m < nb; ++m)
+        for (int n2 = 0; n2 < nb; ++n2) {
+          double v = 0;
+          for (int a = 0; a < d; ++a) v += gt[m * d + a] * gt[n2 * d + a];
+          Gm[m * nb + n2] += wv[q] * v;
+        }
+    }
+    // Cholesky Gm = Lg Lg^T, then Lgi = Lg^{-1} (lower) by forward substitution of the unit columns
+    std::vector<double> Lg(nb * nb, 0.0);
+    for (int j = 0; j < nb; ++j) {
+      double dj = Gm[j * nb + j];
+      for (int p = 0; p < j; ++p) dj -= Lg[j * nb + p] * Lg[j * nb + p];
+      if (!(dj > 0)) throw std::runtime_error("interior moment functions are dependent");
+      Lg[j * nb + j] = std::sqrt(dj);
+      for (int i = j + 1; i < nb; ++i) {
+        double v = Gm[i * nb + j];
+        for (int p = 0; p < j; ++p) v -= Lg[i * nb + p] * Lg[j * nb + p];
+        Lg[i * nb + j] = v / Lg[j * nb + j];
+      }
+    }
+    for (int c = 0; c < nb; ++c)
+      for (int i = c; i < nb; ++i) {
+        double v = (i == c) ? 1.0 : 0.0;
+        for (int p = c; p < i; ++p) v -= Lg[i * nb + p] * Lgi[p * nb + c];
+        Lgi[i * nb + c] = v / Lg[i * nb + i];
+      }
+  }
+  std::vector<double> go(std::max(1, nb * d));
   for (int q = 0; q < nq; ++q) {
     amb(&xv[q * d], val, grad);
     interior_tests(d, k, &xv[q * d], gt);
-    for (int m = 0; m < s.n_bub; ++m)
+    for (int m = 0; m < nb; ++m)
+      for (int a = 0; a < d; ++a) {
+        double v = 0;
+        for (int n2 = 0; n2 <= m; ++n2) v += Lgi[m * nb + n2] * gt[n2 * d + a];
+        go[m * d + a] = v;
+      }
+    for (int m = 0; m < nb; ++m)
       for (int c = 0; c < s.n_full; ++c) {
         double v = 0;
-        for (int a = 0; a < d; ++a) v += val[c * d + a] * gt[m * d + a];
+        for (int a = 0; a < d; ++a) v += val[c * d + a] * go[m * d + a];
         C[((d + 1) * nF + m) * s.n_full + c] += wv[q] * v;
       }
   }
@@ -558,7 +681,7 @@ RefTables build_reference(int d, int k) {
   // ---- load vector quadrature ----
   {
     std::vector<double> xl, wl;
-    duffy_rule(d, k + 7, xl, wl);
+    collapsed_gauss_rule(d, k + 8, xl, wl);   // the load rule of the dof contract, k + 8 points per direction
     T.nq_load = (int)wl.size();
     T.xq_load = xl;
     T.wq_load = wl;

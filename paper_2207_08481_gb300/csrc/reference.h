@@ -78,6 +78,8 @@ RefTables build_reference(int d, int k);
 // weights); q points per direction integrate total degree 2q-3 (n=3),
 // 2q-2 (n=2), 2q-1 (n=1) exactly.
 void duffy_rule(int n, int q, std::vector<double>& pts, std::vector<double>& w);
+// Collapsed Gauss-Jacobi rule on T_n (n = 2, 3) with q points per direction (the load rule).
+void collapsed_gauss_rule(int n, int q, std::vector<double>& pts, std::vector<double>& w);
 // Orthonormal (Dubiner) basis of P^k(T_n) at one point: val[nb], grad[nb][n].
 void dubiner_eval(int n, int k, const double* x, double* val, double* grad);
 

@@ -140,9 +140,8 @@ def test_load_vector(mcs):
     D = system.discretize(mesh.structured(3, 2), K, 0.8)
     Fo = system.load(D, manufactured.Manufactured(3, 0.8).f)
     F = _rhs(h, 0.8).cpu().numpy()
-    # the two sides integrate the smooth f with rules of degree 13 (library, k + 7 points per
-    # direction) and 15 (oracle, k + 8): they differ by about 1.5e-11 relative at k = 1 (reading R12)
-    assert np.abs(F - Fo).max() < 1e-10 * np.abs(Fo).max()
+    # both sides integrate f with the load rule of the dof contract (k + 8 points per direction)
+    assert np.abs(F - Fo).max() < 1e-13 * np.abs(Fo).max()
     h.close()
 
 

@@ -98,6 +98,14 @@ int main(int argc, char** argv) {
       for (int i = 0; i < nq * d * d; ++i) printf("%.17g\n", e.lowest ? 0.0 : om[i]);
     }
   }
+  if (!strcmp(mode, "loadrule")) {
+    RefTables R = build_reference(d, k);
+    for (int q = 0; q < R.nq_load; ++q) {
+      for (int a = 0; a < d; ++a) printf("%.17g ", R.xq_load[q * d + a]);
+      printf("%.17g\n", R.wq_load[q]);
+    }
+    return 0;
+  }
   // "mesh": structured N, optional outflow face; numbering, Abar (nu = 0.7) and E^d blocks
   const int N = atoi(argv[4]), outflow = atoi(argv[5]);
   HostMesh m = structured_mesh(d, N);
@@ -151,7 +159,7 @@ def _perturbed(d, N, seed=1):
 
 
 @pytest.mark.parametrize("d,k,N,lo", [(2, 2, 3, 0), (2, 3, 2, 0), (2, 4, 1, 0), (3, 2, 1, 0), (3, 1, 2, 0),
-                                      (3, 1, 2, 1)])
+                                      (3, 1, 2, 1), (2, 5, 1, 0), (2, 6, 1, 0), (3, 5, 1, 0), (3, 6, 1, 0)])
 def test_element_condensation_matches_oracle(harness, d, k, N, lo):
     """A_T of every element of a perturbed mesh (orientation signs applied), 1e-12 relative; the double
     Schur complement A^d_T and G_T = A_oo^{-1} A_od (eqs. Hcoeffs, factorSsigma) to 1e-11 / 1e-10."""
@@ -170,7 +178,7 @@ def test_element_condensation_matches_oracle(harness, d, k, N, lo):
     vals = np.array(out.split(), dtype=float).reshape(ne, nA * nA + nc * nc + no * nc)
     A = vals[:, :nA * nA].reshape(AT.shape)
     err = np.abs(A - AT).max(axis=(1, 2)) / np.abs(AT).max(axis=(1, 2))
-    assert err.max() < 1e-12
+    assert err.max() < (1e-12 if k <= 4 else 1e-10), err.max()   # rounding grows with the local sizes (3D k = 6: 3.5e-11)
     # A^d and G in the library's facet-major coupling order against the oracle's [u_d | uhat] order
     Ad_o, G_o, _ = system.bubble_condense(D, AT)
     mF = sz["nF"] + sz["n_hatF"]
@@ -262,3 +270,18 @@ def test_stress_recovery_matches_oracle(harness, d, k, N):
     if not sz["lowest"]:
         wo = np.einsum("ej,eqjab->eqab", om, E.W)
         assert np.abs(vals[:, 1] - wo).max() < 1e-10 * np.abs(wo).max()
+
+
+@pytest.mark.parametrize("d,k", [(2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3), (3, 4)])
+def test_load_rule_is_the_oracle_rule(harness, d, k):
+    """The load quadrature of the dof contract (collapsed Gauss-Jacobi, k + 8 points per direction) is
+    implemented on both sides independently: the library's points and weights equal the oracle's
+    (SciPy Gauss-Jacobi nodes) to rounding, so both load vectors agree to rounding too."""
+    from oracle import polys
+    out = subprocess.run([harness, "loadrule", str(d), str(k), "0", "0"], capture_output=True, text=True,
+                         check=True).stdout
+    got = np.array(out.split(), dtype=float).reshape(-1, d + 1)
+    x, w = polys.quadrature(d, k + 8)
+    assert got.shape[0] == len(w)
+    assert np.abs(got[:, :d] - x).max() < 1e-14
+    assert np.abs(got[:, d] - w).max() < 1e-15 * max(1.0, np.abs(w).max()) * 10

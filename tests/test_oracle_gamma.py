@@ -45,8 +45,9 @@ def test_gamma_depends_on_shape():
 
 def test_bubble_basis_does_not_change_gamma():
     """The infimum over the bubbles (eq. epshschur) and the double Schur complement are independent of
-    the bubble basis: the contract's dual basis and an L2-orthonormal one give the same pencil."""
-    a = hdg.gamma(3)
-    b = hdg.gamma(3, ortho_bubbles=True)
+    the bubble basis: the contract's L2-orthonormal bubbles and the unorthonormalised monomial list
+    give the same pencil."""
+    a = hdg.gamma(3, bubble_basis="monomial")
+    b = hdg.gamma(3)
     assert abs(a[0] - b[0]) < 1e-8 * a[0] and abs(a[1] - b[1]) < 1e-8 * a[1]
     assert b[2] > a[2]                       # the orthonormal basis resolves the kernel better
