@@ -1,24 +1,30 @@
 #!/usr/bin/env python
-"""Benchmark of the MCS Stokes hot path on GB300: solves per second.
+"""Benchmark of the MCS Stokes hot path on GB300: Stokes solves per second.
 
-One step = static condensation (mcs_condense) + the ASP-preconditioned MinRes solve
-(mcs_solve) to relative preconditioned residual 1e-8, on the workload c2: the unit
-square with 256x256 cells (131,072 triangles), k = 3, nu = 1e-2, manufactured
-solution, 5-level geometric multigrid (16^2 coarsest) for the conforming space.
-`value` is the mixed form (FP32 preconditioner, FP64 outer Krylov and operator);
-the FP64 form is reported beside it.
+One step = static condensation (mcs_condense) + the ASP-preconditioned MinRes solve (mcs_solve) of
+the workload c3: the unit cube with 32^3 cubes x 6 = 196,608 tetrahedra, k = 2, nu = 1, manufactured
+solution, 4-level geometric multigrid (4^3 coarsest) for the conforming space; 6,610,944 condensed
+dofs.  A solve ends when the relative preconditioned residual is <= 1e-8 and the a-posteriori error
+estimate of the solution (mcs_options.etol) is <= the form's accuracy bar: 1e-8 relative L2 error of
+u and of p for the mixed form (FP32 preconditioner, FP64 outer Krylov), 1e-10 for the FP64 form.
+`value` is the mixed form; the FP64 form, the same forms on c2 (2D, 256^2 x 2 triangles, k = 3,
+nu = 1e-2) and the residual-only stopping rule are reported beside it.  `err_vs_oracle` states the
+error of both forms against the CPU FP64 oracle's direct solve on cases of the same element types
+the oracle finishes in seconds (the oracle runs only in the cpu_baseline leg).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+  python bench.py --profile-case c3s [--form mixed|fp64]     (one condense + apply + precond, for ncu)
 
-Under torchrun each rank solves its own copy of the workload (independent problems,
-"replicas": the path has no exchange between problems), value = total solves / max time.
---impl reference times the CPU FP64 oracle (the test oracle of this repository) on a
-bounded sample of the same workload and scales it to the full problem size.
+Under torchrun each rank solves its own copy of the workload (independent problems, "replicas":
+the path has no exchange between problems), value = total solves / max time over ranks.
+--impl reference times the CPU FP64 oracle (the test oracle of this repository) on bounded samples
+of the same workload and extrapolates with the cost exponent fitted over three sample sizes.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -29,9 +35,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Stokes solves/s to rel. res 1e-8, mixed vs FP64 form; HBM roofline %; p50/p99"
-WORKLOAD = dict(dim=2, N=256, k=3, nu=1e-2, levels=5, rtol=1e-8)
-WORKLOAD_NAME = ("c2: 2D unit square, 256x256 cells split into 131,072 triangles (4 uniform refinements of "
-                 "16x16 for the multigrid), MCS k=3, nu=1e-2, manufactured solution")
+WORKLOADS = {
+    "c3": dict(dim=3, N=32, k=2, nu=1.0, levels=4,
+               name="c3: 3D unit cube, 32^3 cubes x 6 = 196,608 tetrahedra (3 refinements of 4^3 for the "
+                    "multigrid), MCS k=2, nu=1, manufactured solution"),
+    "c2": dict(dim=2, N=256, k=3, nu=1e-2, levels=5,
+               name="c2: 2D unit square, 256x256 cells split into 131,072 triangles (4 refinements of 16x16 "
+                    "for the multigrid), MCS k=3, nu=1e-2, manufactured solution"),
+}
+HEADLINE = "c3"
+# The timed forms: rel. preconditioned residual 1e-8 and the error estimate at the form's accuracy bar.
+ERR_BAR = {"mixed": 1e-8, "fp64": 1e-10}
+FORMS = {
+    "mixed": dict(precision=1, rtol=1e-8, etol=1e-8),
+    "fp64": dict(precision=0, rtol=1e-8, etol=1e-10),
+}
+# Cases of the two element types small enough for the oracle's direct solve (err_vs_oracle).
+ORACLE_CASES = {
+    "c3": dict(dim=3, N=4, k=2, nu=1.0, levels=2),
+    "c2": dict(dim=2, N=32, k=3, nu=1e-2, levels=2),
+}
+PROFILE_CASES = {"c2": dict(dim=2, N=256, k=3, nu=1e-2, levels=5), "c3": dict(dim=3, N=32, k=2, nu=1.0, levels=4),
+                 "c3s": dict(dim=3, N=16, k=2, nu=1.0, levels=3)}
 
 
 def _dist():
@@ -99,9 +124,9 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it is current."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_c2.txt")
+def _traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary of this workload, if any."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_launch:"):
@@ -121,14 +146,13 @@ def _over_ranks(values, dist, device, op="max"):
     return [float(v) for v in t.tolist()]
 
 
-def _make_handle(mcs, precision):
-    w = WORKLOAD
-    return mcs.Handle.structured(w["dim"], w["N"], w["k"], w["nu"], precision=precision, gmg_levels=w["levels"],
-                                 rtol=w["rtol"])
+def _make_handle(mcs, w, form, **extra):
+    o = dict(FORMS[form])
+    o.update(extra)
+    return mcs.Handle.structured(w["dim"], w["N"], w["k"], w["nu"], gmg_levels=w["levels"], **o)
 
 
-def _rhs(h, torch, workloads):
-    w = WORKLOAD
+def _rhs(h, torch, workloads, w):
     s = h.sizes
     xq = torch.zeros((s.ne * s.nq_load, w["dim"]), dtype=torch.float64, device="cuda")
     h.load_points(xq)
@@ -136,6 +160,13 @@ def _rhs(h, torch, workloads):
     h.load_vector(workloads.manufactured_f(w["dim"], w["nu"], xq), F)
     del xq
     return F
+
+
+def _s8d_bytes_per_colour_launch(s, ncol):
+    """Algorithmic bytes of one facet-block Gauss-Seidel colour launch by the packed-triangle count: one
+    A^d pass = s*E*n_d(n_d+1)/2 (each element's Schur complement read once as a packed triangle) plus
+    the block solves s*F_int*m_F^2, divided over the colours of a sweep (s = 4 in the mixed form)."""
+    return 4.0 * (s.ne * s.n_c * (s.n_c + 1) / 2 + s.nint * s.mF * s.mF) / ncol
 
 
 def run_gpu(args):
@@ -154,6 +185,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     import paper_2207_08481_gb300.mcs as mcs
+    dd = dist if world > 1 else None
 
     def barrier():
         if world > 1:
@@ -162,12 +194,13 @@ def run_gpu(args):
 
     launches = [0]      # library kernels launched in the last timed region (its own counter)
 
-    def timed(h, F, x, steps, profile=False):
+    def timed(h, F, x, steps, warmup, profile=False):
         def step():
             h.condense()
             x.zero_()
             return h.solve(F, x)
-        for _ in range(0 if profile else args.warmup):
+        info = None
+        for _ in range(warmup):
             info = step()
         if profile:
             h.profile(True)
@@ -182,26 +215,31 @@ def run_gpu(args):
         ev1.record()
         launches[0] = mcs.launch_count() - n0
         barrier()
-        ms = _over_ranks([ev0.elapsed_time(ev1)], dist if world > 1 else None, "cuda")[0]
+        ms = _over_ranks([ev0.elapsed_time(ev1)], dd, "cuda")[0]
         stats = h.profile_read() if profile else None
         if profile:
             h.profile(False)
         return ms, its, info, stats
 
+    def info_dict(info):
+        return {"iterations": info.iterations, "cycles": info.refinements,
+                "rel_res": {"precond": info.rel_res_precond, "true": info.rel_res_true},
+                "err_est": info.err_est}
+
+    w = WORKLOADS[HEADLINE]
     # ---------------- mixed form (headline)
-    hm = _make_handle(mcs, mcs.MCS_MIXED)
-    F = _rhs(hm, torch, workloads)
+    hm = _make_handle(mcs, w, "mixed")
+    F = _rhs(hm, torch, workloads, w)
     x = torch.zeros_like(F)
     ndof = hm.sizes.ndof
     with ClockSampler(local) as clk:
-        ms_mixed, its_mixed, info_m, _ = timed(hm, F, x, args.steps)
+        ms_mixed, its_mixed, info_m, _ = timed(hm, F, x, args.steps, args.warmup)
     gpu_launches = launches[0]
     value = args.steps * world / (ms_mixed / 1e3)
-    # per-kernel CUDA-event timers: one further step of the same workload with the library's
-    # timers on (the timed loop above runs the captured-graph path without per-launch events)
-    _, _, _, stats = timed(hm, F, x, 1, profile=True)
-    # error of the solution against the exact one is not part of the metric; residuals are
-    resid_m = dict(precond=info_m.rel_res_precond, true=info_m.rel_res_true)
+    # per-kernel CUDA-event timers: one further step of the same workload with the library's timers
+    # on (the timed loop runs the captured-graph path without per-launch events)
+    _, _, _, stats = timed(hm, F, x, 1, 0, profile=True)
+    sizes = hm.sizes
 
     # ---------------- end to end through the host-buffer entry point
     import numpy as np
@@ -218,27 +256,56 @@ def run_gpu(args):
         xh[:] = 0.0
         hm.solve_host(Fh, xh)
     barrier()
-    e2e_s = _over_ranks([time.perf_counter() - t0], dist if world > 1 else None, "cuda")[0]
+    e2e_s = _over_ranks([time.perf_counter() - t0], dd, "cuda")[0]
     e2e_value = args.steps * world / e2e_s
-
+    x_mixed = x.clone()
     hm.close()
 
     # ---------------- FP64 form
-    hd = _make_handle(mcs, mcs.MCS_FP64)
+    hd = _make_handle(mcs, w, "fp64")
     xd = torch.zeros_like(F)
-    fp64_steps = max(1, args.steps // 2)
-    ms_fp64, its_fp64, info_d, _ = timed(hd, F, xd, fp64_steps)
+    fp64_steps = max(1, args.steps // 4)
+    ms_fp64, its_fp64, info_d, _ = timed(hd, F, xd, fp64_steps, min(args.warmup, 1))
     value_fp64 = fp64_steps * world / (ms_fp64 / 1e3)
     hd.close()
+    # the two forms' solutions agree within the mixed form's bar (a property at full size)
+    n_p = sizes.off_p
+    agree = {"u": float(torch.linalg.norm(x_mixed[:n_p] - xd[:n_p]) / torch.linalg.norm(xd[:n_p])),
+             "p": float(torch.linalg.norm(x_mixed[n_p:] - xd[n_p:]) / torch.linalg.norm(xd[n_p:]))}
+    del x_mixed
 
-    # ---------------- several degrees in one condensation launch (3D, 16^3 x 6 tets, k = 2, 3, 4)
-    multi = _multi_degree(args, torch, mcs) if (rank == 0 and not args.no_multi) else None
-    smoothing = _smoothing(args, torch, mcs) if (rank == 0 and not args.no_multi) else None
+    # ---------------- the residual-only stopping rule (rel. res 1e-8 alone), for context
+    resid_only = {}
+    for form in ("mixed", "fp64"):
+        h = _make_handle(mcs, w, form, etol=0.0)
+        xr = torch.zeros_like(F)
+        ms_r, _, info_r, _ = timed(h, F, xr, 2, 1)
+        resid_only[form] = {"value": round(2 * world / (ms_r / 1e3), 4), "unit": "solves/s",
+                            "ms_per_step": round(ms_r / 2, 2), **info_dict(info_r)}
+        h.close()
+        del xr
+    del F, x, xd
 
-    # ---------------- serving: Poisson trace of mixed requests through the continuous-batching loop
+    # ---------------- c2: the same forms on the 2D workload
+    c2 = _c2(args, torch, mcs, workloads, timed, info_dict) if not args.quick else None
+
+    # ---------------- iteration counts under h-refinement, several degrees in one launch, ASP forms
+    h_series = _h_series(torch, mcs, workloads) if (rank == 0 and not args.quick) else None
+    multi = _multi_degree(args, torch, mcs) if (rank == 0 and not args.quick) else None
+    smoothing = _smoothing(args, torch, mcs) if (rank == 0 and not args.quick) else None
+
+    # ---------------- serving: Poisson traces of mixed requests through the continuous-batching loop
     serving = None
-    if args.serve_requests > 0:
-        serving = _serving(args, rank, world, torch, dist if world > 1 else None)
+    if args.serve_requests > 0 and not args.quick:
+        serving = {"at_trace_rate": _serving(args, rank, world, torch, dd, args.serve_requests, args.serve_rate)}
+        if args.serve_rate2 > 0:
+            serving["at_sustainable_rate"] = _serving(args, rank, world, torch, dd, args.serve_requests2,
+                                                      args.serve_rate2)
+
+    # ---------------- error against the oracle (cpu_baseline leg: the only place the oracle runs)
+    cpu, err_vs_oracle = (None, None)
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, err_vs_oracle = _cpu_baseline(args, torch, mcs, workloads)
 
     if rank != 0:
         if world > 1:
@@ -247,42 +314,53 @@ def run_gpu(args):
 
     # ---------------- roofline of the dominant kernel class
     peak, peak_kind = _peaks()
-    dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
-    name, st = dom
-    per_launch_ms = st["ms"] / max(st["launches"], 1)
-    if name in ("condense", "apply_K"):
-        achieved = st["flops"] / max(st["launches"], 1) / (per_launch_ms * 1e-3) / 1e12
+    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    nl = max(st["launches"], 1)
+    per_launch_ms = st["ms"] / nl
+    if name in ("condense",):
+        achieved = st["flops"] / nl / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": 1.20, "unit": "TFLOP/s",
                 "frac": achieved / 1.20, "traffic": None, "peak_kind": "measured FP64 FMA probe"}
     else:
-        achieved = st["bytes"] / max(st["launches"], 1) / (per_launch_ms * 1e-3) / 1e9
+        achieved = st["bytes"] / nl / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": _traffic(name),
-                "algorithmic_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+                "frac": round(achieved / peak, 4), "traffic": _traffic(name, HEADLINE),
+                "algorithmic_bytes_per_launch": st["bytes"] / nl,
                 "avg_launch_us": round(per_launch_ms * 1e3, 2), "peak_kind": peak_kind,
-                "measured": "CUDA events around each launch, one profiled step after the timed loop"}
+                "measured": "CUDA events around each launch on the handle's stream, one profiled step after "
+                            "the timed loop"}
+        if name == "facet_gs_step":
+            s8 = _s8d_bytes_per_colour_launch(sizes, sizes.ncolours)
+            roof["s8d_bytes_per_launch"] = s8
+            roof["frac_s8d"] = round(s8 / (per_launch_ms * 1e-3) / 1e9 / peak, 4)
+            roof["layout_over_s8d"] = round(st["bytes"] / nl / s8, 3)
     share = {k: round(v["ms"] / sum(u["ms"] for u in stats.values()), 4) for k, v in stats.items() if v["launches"]}
 
-    cpu = _cpu_baseline(args) if not args.no_cpu_baseline else None
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_mixed / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 outer Krylov + K, f32 preconditioner",
         "data": "synthetic (manufactured solution on a structured Kuhn mesh)",
-        "config": {"workload": WORKLOAD_NAME, "step": "mcs_condense + mcs_solve (MinRes, rel. preconditioned "
-                   "residual 1e-8)", "ndof": ndof, "form": "mixed", "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (resident operators ~1.7 GB per problem)"},
-        "iterations": its_mixed[-1], "rel_res": resid_m,
+        "config": {"workload": w["name"], "step": "mcs_condense + mcs_solve (MinRes with refinement cycles: rel. "
+                   "preconditioned residual <= 1e-8 and estimated relative L2 error of u and p <= 1e-8)",
+                   "ndof": ndof, "form": "mixed", "options": FORMS["mixed"], "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (resident operators ~4.4 GB per problem)"},
+        **info_dict(info_m),
         "condensed_dofs_per_s": round(value * ndof, 1),
-        "fp64_form": {"value": round(value_fp64, 4), "unit": "solves/s", "ms_per_step": round(ms_fp64 / fp64_steps, 3),
-                      "steps": fp64_steps, "iterations": its_fp64[-1],
-                      "rel_res": dict(precond=info_d.rel_res_precond, true=info_d.rel_res_true)},
+        "fp64_form": {"value": round(value_fp64, 4), "unit": "solves/s",
+                      "ms_per_step": round(ms_fp64 / fp64_steps, 3), "steps": fp64_steps,
+                      "options": FORMS["fp64"], **info_dict(info_d)},
+        "forms_agree_full_size": agree,
+        "residual_only_stopping": resid_only,
+        "err_vs_oracle": err_vs_oracle,
         "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": 2 * ndof * 8,
                 "d2h_bytes_per_step": ndof * 8},
         "roofline": roof, "kernel_time_share": share,
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "c2": c2,
+        "h_series": h_series,
         "serving": serving,
         "multi_degree": multi,
         "asp_smoothing": smoothing,
@@ -290,6 +368,23 @@ def run_gpu(args):
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _c2(args, torch, mcs, workloads, timed, info_dict):
+    w = WORKLOADS["c2"]
+    out = {"workload": w["name"]}
+    F = None
+    for form in ("mixed", "fp64"):
+        h = _make_handle(mcs, w, form)
+        if F is None:
+            F = _rhs(h, torch, workloads, w)
+        x = torch.zeros_like(F)
+        steps = 5 if form == "mixed" else 2
+        ms, _, info, _ = timed(h, F, x, steps, 1)
+        out[form] = {"value": round(steps / (ms / 1e3), 4), "unit": "solves/s", "ms_per_step": round(ms / steps, 2),
+                     **info_dict(info)}
+        h.close()
+    return out
 
 
 def _random_solve(h, torch, seed):
@@ -313,6 +408,35 @@ def _random_solve(h, torch, seed):
     return round(e0.elapsed_time(e1), 2), info
 
 
+def _h_series(torch, mcs, workloads):
+    """MinRes iterations of the mixed form (headline stopping rule) under uniform refinement of both
+    workload types (Theorem aux_pc_schur: bounded in h), manufactured right-hand side."""
+    out = {"stopping": FORMS["mixed"]}
+    for key, Ns in (("c3_type", (8, 16, 32)), ("c2_type", (32, 64, 128, 256))):
+        base = WORKLOADS["c3" if key == "c3_type" else "c2"]
+        rows = []
+        for N in Ns:
+            w = dict(base, N=N, levels=-1)
+            h = _make_handle(mcs, w, "mixed")
+            h.condense()
+            F = _rhs(h, torch, workloads, w)
+            x = torch.zeros_like(F)
+            h.solve(F, x)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record()
+            info = h.solve(F, x)
+            e1.record()
+            torch.cuda.synchronize()
+            rows.append({"N": N, "ne": int(h.sizes.ne), "ndof": int(h.sizes.ndof), "levels": int(h.sizes.gmg_levels),
+                         "iterations": info.iterations, "cycles": info.refinements,
+                         "solve_ms": round(e0.elapsed_time(e1), 2)})
+            h.close()
+        out[key] = rows
+    return out
+
+
 def _smoothing(args, torch, mcs):
     """Multiplicative against additive ASP (Table ST_smoothing re-run on the c3 mesh: 3D 32^3 x 6
     tetrahedra, k = 2, nu = 1, mixed form, random F = M_u c, seeded): iterations and solve time."""
@@ -329,55 +453,55 @@ def _smoothing(args, torch, mcs):
 
 
 def _multi_degree(args, torch, mcs):
-    """Mixed-degree batch: one persistent condensation launch for four problems (the lowest-order
-    variant k = 1 and k = 2, 3, 4) against one launch per problem, then the four solves (random
-    F = M_u c, seeded)."""
-    ks = (1, 2, 3, 4)
+    """The batched degree sweep: six problems on 3D 16^3 x 6 tetrahedra, the lowest-order variant k = 1 and
+    k = 2..6, condensed in one persistent launch (against one launch per problem), then solved one by one
+    (mixed form with the headline's stopping rule, random F = M_u c, c ~ N(0, 1), seeded)."""
+    ks = (1, 2, 3, 4, 5, 6)
     # k = 1: the ASP condition number grows under refinement (stabilisation weight nu), hence more
     # MinRes iterations
-    hs = [mcs.Handle.structured(3, 16, k, 1.0, precision=mcs.MCS_MIXED, maxit=8000 if k == 1 else 1000)
-          for k in ks]
+    hs = [mcs.Handle.structured(3, 16, k, 1.0, maxit=8000 if k == 1 else 2000, **FORMS["mixed"]) for k in ks]
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def timed(fn, reps=2):
-        fn()
+    def timed(fn):
+        fn()                     # warm-up
         torch.cuda.synchronize()
         e0, e1 = ev(), ev()
         e0.record()
-        for _ in range(reps):
-            fn()
+        fn()
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1)
 
+    t_sep = {}
+    for k, h in zip(ks, hs):
+        t_sep[f"k={k}"] = round(timed(h.condense), 2)
     t_batch = timed(lambda: mcs.condense_batch(hs))
-    t_sep = timed(lambda: [h.condense() for h in hs])
-    mcs.condense_batch(hs)
     solves = {}
     for k, h in zip(ks, hs):
         ms, info = _random_solve(h, torch, 100 + k)
         solves[f"k={k}"] = {"ndof": int(h.sizes.ndof), "ms": ms, "iterations": info.iterations,
-                            "rel_res": info.rel_res_precond}
+                            "cycles": info.refinements, "rel_res": info.rel_res_precond, "err_est": info.err_est,
+                            "resident_gb": round(h.sizes.bytes_resident / 1e9, 2)}
+    for h in hs:
+        h.close()
     # k = 1 with the stabilisation weight nu h_T^2 (lo_stab = 1) instead of nu: same right-hand side
-    h1 = mcs.Handle.structured(3, 16, 1, 1.0, precision=mcs.MCS_MIXED, maxit=8000, lo_stab=1)
+    h1 = mcs.Handle.structured(3, 16, 1, 1.0, maxit=8000, lo_stab=1, **FORMS["mixed"])
     h1.condense()
     ms, info = _random_solve(h1, torch, 101)
     solves["k=1, weight nu h_T^2"] = {"ndof": int(h1.sizes.ndof), "ms": ms, "iterations": info.iterations,
-                                      "rel_res": info.rel_res_precond}
+                                      "cycles": info.refinements, "rel_res": info.rel_res_precond}
     h1.close()
-    for h in hs:
-        h.close()
-    return {"config": "3D unit cube, 16^3 cells x 6 = 24,576 tetrahedra each, k = 1 (lowest-order variant), 2, 3, 4, "
-                      "nu = 1, mixed form, random F = M_u c (c ~ N(0,1)); k = 5, 6 of the six-problem batch are "
-                      "not supported",
-            "condense_batched_ms": round(t_batch, 2), "condense_separate_ms": round(t_sep, 2), "solves": solves}
+    return {"config": "3D unit cube, 16^3 cells x 6 = 24,576 tetrahedra each, k = 1 (lowest-order variant), 2, 3, 4, 5, 6, "
+                      "nu = 1, mixed form (rel. residual 1e-8, error estimate <= 1e-8), random F = M_u c (c ~ N(0,1))",
+            "condense_batched_ms": round(t_batch, 2), "condense_separate_ms": round(sum(t_sep.values()), 2),
+            "condense_separate_by_k_ms": t_sep, "solves": solves}
 
 
-def _serving(args, rank, world, torch, dist):
+def _serving(args, rank, world, torch, dist, n, rate):
     """Replays a seeded trace (each rank its own replica) through serve.SolveServer from a cold
     operator cache.  Latency = completion - arrival; throughput = requests / wall time."""
     from paper_2207_08481_gb300 import serve
-    reqs = serve.make_trace(args.serve_requests, args.serve_rate, seed=2207 + rank)
+    reqs = serve.make_trace(n, rate, seed=2207 + rank)
     srv = serve.SolveServer(serve.GpuBackend(), slots=args.serve_slots, budget_bytes=120e9)
     t0 = time.perf_counter()
     res = srv.run(reqs, realtime=True)
@@ -385,80 +509,173 @@ def _serving(args, rank, world, torch, dist):
     wall = time.perf_counter() - t0
     srv.close()
     summ = serve.summarize(res, wall)
-    hits = [r for r in res if r.cache_hit]
-    if hits:
-        lat = [r.latency * 1e3 for r in hits]
-        import numpy as np
-        summ["p50_ms_cache_hit"] = float(np.percentile(lat, 50))
-        summ["p99_ms_cache_hit"] = float(np.percentile(lat, 99))
+    import numpy as np
+    for label, sel in (("cache_hit", [r for r in res if r.cache_hit]), ("cache_miss", [r for r in res if not r.cache_hit])):
+        if sel:
+            lat = [r.latency * 1e3 for r in sel]
+            summ[f"p50_ms_{label}"] = round(float(np.percentile(lat, 50)), 3)
+            summ[f"p99_ms_{label}"] = round(float(np.percentile(lat, 99)), 3)
+    by_size = {}
+    for r in res:
+        rq = reqs[r.rid]
+        cls = "small (< 2^10 elements)" if rq.e < 10 else ("medium (2^10..2^13)" if rq.e < 14 else "large (>= 2^14)")
+        by_size.setdefault(cls, []).append(r.latency * 1e3)
+    summ["by_size"] = {c: {"requests": len(v), "p50_ms": round(float(np.percentile(v, 50)), 3),
+                           "p99_ms": round(float(np.percentile(v, 99)), 3)} for c, v in sorted(by_size.items())}
     if dist is not None:
         total = _over_ranks([summ["requests"]], dist, "cuda", op="sum")[0]
         wall_max = _over_ranks([wall], dist, "cuda")[0]
         summ["throughput_solves_per_s"] = total / wall_max
-    summ.update({"rate_per_s": args.serve_rate, "slots": args.serve_slots, "budget_gb": 120,
+    summ.update({"rate_per_s": rate, "slots": args.serve_slots, "budget_gb": 120,
                  "peak_resident_gb": round(srv.peak_bytes / 1e9, 3), "evictions": srv.evictions,
-                 "trace": f"{args.serve_requests} requests, Poisson {args.serve_rate}/s, dim in {{2,3}}, "
-                          f"2^3..2^17 elements, k in {{2,3,4}}, nu log-uniform [1e-3,1], N(0,1) body force; "
-                          f"cold operator cache; mixed form, rtol 1e-8"})
+                 "trace": f"{n} requests, Poisson {rate}/s, dim in {{2,3}}, 2^3..2^17 elements, k in {{2,3,4}}, "
+                          f"nu log-uniform [1e-3,1], N(0,1) body force; cold operator cache; mixed form, rtol 1e-8, "
+                          f"error estimate <= 1e-8"})
     for key in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "throughput_solves_per_s"):
         summ[key] = round(summ[key], 3)
     return summ
 
 
-def _oracle_sample(N: int):
-    """Oracle (CPU, FP64) on the c2 workload type at N cells per direction: discretize,
-    condense, load and direct solve.  Returns seconds."""
+# ------------------------------------------------------------------ CPU legs (the oracle)
+def _oracle_sample(case: dict, F=None):
+    """The oracle (CPU, FP64) on one case: discretize, condense, load, direct solve of the condensed
+    system, mean-zero pressure.  F: a given right-hand side (else the oracle's own load vector).
+    Returns (seconds, solution)."""
     from oracle import manufactured, mesh, system
-    w = WORKLOAD
     t0 = time.perf_counter()
     c0 = time.process_time()
-    D = system.discretize(mesh.structured(w["dim"], N), w["k"], w["nu"])
+    D = system.discretize(mesh.structured(case["dim"], case["N"]), case["k"], case["nu"])
     AT = system.condense(D)
-    F = system.load(D, manufactured.Manufactured(w["dim"], w["nu"]).f)
-    x = system.solve_condensed(D, F, AT)
-    system.mean_zero_pressure(D, x)
+    if F is None:
+        F = system.load(D, manufactured.Manufactured(case["dim"], case["nu"]).f)
+    x = system.mean_zero_pressure(D, system.solve_condensed(D, F, AT))
     wall = time.perf_counter() - t0
     _oracle_sample.threads = (time.process_time() - c0) / max(wall, 1e-9)   # CPU time / wall time
-    return wall
+    return wall, x, D.off_p
 
 
-def _cpu_baseline(args, N=48):
-    secs = _oracle_sample(N)
-    w = WORKLOAD
-    scale = (w["N"] / N) ** w["dim"]
-    est = secs * scale
+def _fit(samples):
+    """Least-squares fit t = a * ne^b over (ne, t) samples; returns (a, b)."""
+    import numpy as np
+    X = np.log([s[0] for s in samples])
+    Y = np.log([s[1] for s in samples])
+    b, loga = np.polyfit(X, Y, 1)
+    return math.exp(loga), b
+
+
+def _cpu_baseline(args, torch, mcs, workloads):
+    """The oracle timed on the machine's host cores at three sizes of the headline's element type, its cost
+    fitted as a power of the element count and extrapolated to the headline mesh; and the error of both
+    GPU forms (the timed options) against the oracle's direct solve on the ORACLE_CASES."""
+    w = WORKLOADS[HEADLINE]
+    samples = []
+    for N in (2, 3, 4):
+        case = dict(w, N=N)
+        secs, _, _ = _oracle_sample(case)
+        ne = 6 * N ** 3 if w["dim"] == 3 else 2 * N * N
+        samples.append((ne, secs))
+    a, b = _fit(samples)
+    ne_full = 6 * w["N"] ** 3 if w["dim"] == 3 else 2 * w["N"] ** 2
+    est = a * ne_full ** b
     thr = getattr(_oracle_sample, "threads", 1.0)
-    return {"value": round(1.0 / est, 6), "unit": "solves/s", "cores": max(1, round(thr)), "kind": "oracle",
-            "sample": f"oracle (discretize + condense + sparse direct solve) on the c2 workload type at "
-                      f"{N}x{N} cells ({2 * N * N} triangles) took {secs:.1f} s; scaled linearly by elements "
-                      f"(x{scale:.1f}) to 256x256; cores = CPU time / wall time of the sample ({thr:.2f}) "
-                      f"of {os.cpu_count()} available (NumPy/SciPy, sparse LU single-threaded)"}
+    cpu = {"value": round(1.0 / est, 8), "unit": "solves/s", "cores": max(1, round(thr)), "kind": "fitted",
+           "exponent": round(b, 3),
+           "sample": f"oracle (discretize + condense + load + sparse direct solve of the condensed system, CPU FP64) on "
+                     f"the headline's element type at N = 2, 3, 4 ({', '.join(f'{ne} tets: {t:.2f} s' for ne, t in samples)}); "
+                     f"time fitted as a*ne^b (b = {b:.2f}) and evaluated at {ne_full} tets; cores = CPU time / wall "
+                     f"time ({thr:.2f}) of {os.cpu_count()} available"}
+    err = {}
+    import numpy as np
+    for key, case in ORACLE_CASES.items():
+        entry = {"case": f"{case['dim']}D N={case['N']} k={case['k']} nu={case['nu']} ({'x6 tets' if case['dim'] == 3 else 'x2 triangles'}), "
+                         f"{case['levels']} GMG levels, manufactured f; both sides take the library's load vector"}
+        F = None
+        for form in ("mixed", "fp64"):
+            h = _make_handle(mcs, case, form)
+            h.condense()
+            if F is None:
+                F = _rhs(h, torch, workloads, case)
+                _, xo, n_p = _oracle_sample(case, F.cpu().numpy())
+            x = torch.zeros_like(F)
+            info = h.solve(F, x)
+            xg = x.cpu().numpy()
+            eu = float(np.linalg.norm(xg[:n_p] - xo[:n_p]) / np.linalg.norm(xo[:n_p]))
+            ep = float(np.linalg.norm(xg[n_p:] - xo[n_p:]) / np.linalg.norm(xo[n_p:]))
+            entry[form] = {"rel_l2_u": eu, "rel_l2_p": ep, "bar": ERR_BAR[form],
+                           "meets_bar": eu <= ERR_BAR[form] and ep <= ERR_BAR[form],
+                           "iterations": info.iterations, "err_est": info.err_est}
+            h.close()
+        if not all(entry[f]["meets_bar"] for f in ("mixed", "fp64")):
+            # the FP64 rounding floor of the discrete problem: the oracle's condensed against its full solve
+            from oracle import mesh, system
+            D = system.discretize(mesh.structured(case["dim"], case["N"]), case["k"], case["nu"])
+            xf, _, _ = system.solve_full(D, F.cpu().numpy())
+            xf = system.mean_zero_pressure(D, xf)
+            entry["oracle_condensed_vs_full"] = {
+                "rel_l2_u": float(np.linalg.norm(xo[:n_p] - xf[:n_p]) / np.linalg.norm(xf[:n_p])),
+                "rel_l2_p": float(np.linalg.norm(xo[n_p:] - xf[n_p:]) / np.linalg.norm(xf[n_p:]))}
+        err[key] = entry
+    return cpu, err
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step one bounded sample (N = 3 of the headline's element
+    type), extrapolated to the headline mesh with the exponent fitted over N = 2, 3, 4 in the warm-up."""
     rank, world, local = _dist()
     if rank != 0:
         return
+    w = WORKLOADS[HEADLINE]
+    ne_of = lambda N: 6 * N ** 3 if w["dim"] == 3 else 2 * N * N
+    fit_samples = []
+    for i in range(max(args.warmup, 3)):
+        N = (2, 3, 4)[i % 3]
+        secs, _, _ = _oracle_sample(dict(w, N=N))
+        fit_samples.append((ne_of(N), secs))
+    _, b = _fit(fit_samples)
     times = []
-    for _ in range(args.warmup):
-        _oracle_sample(args.ref_N)
     for _ in range(args.steps):
-        times.append(_oracle_sample(args.ref_N))
-    w = WORKLOAD
-    scale = (w["N"] / args.ref_N) ** w["dim"]
-    per = sum(times) / len(times) * scale
+        secs, _, _ = _oracle_sample(dict(w, N=3))
+        times.append(secs)
+    ne_full = ne_of(w["N"])
+    per = sum(times) / len(times) * (ne_full / ne_of(3)) ** b
     value = 1.0 / per
     thr = getattr(_oracle_sample, "threads", 1.0)
-    cpu = {"value": round(value, 6), "unit": "solves/s", "cores": max(1, round(thr)), "kind": "oracle",
-           "sample": f"each step: oracle on {args.ref_N}x{args.ref_N} cells, scaled linearly by elements "
-                     f"(x{scale:.0f}); cores = CPU time / wall time ({thr:.2f}) of {os.cpu_count()} available"}
-    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
+    cpu = {"value": round(value, 8), "unit": "solves/s", "cores": max(1, round(thr)), "kind": "fitted",
+           "exponent": round(b, 3),
+           "sample": f"each step: oracle (direct solve of the condensed system) on N = 3 ({ne_of(3)} tets), "
+                     f"extrapolated by (ne ratio)^{b:.2f} to {ne_full} tets, exponent fitted over N = 2, 3, 4 in the "
+                     f"warm-up; cores = CPU time / wall time ({thr:.2f}) of {os.cpu_count()} available"}
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per * 1e3, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD_NAME, "form": "oracle: direct solve of the condensed system"},
+           "config": {"workload": w["name"], "form": "oracle: direct solve of the condensed system"},
            "cpu_baseline": cpu,
-           "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": round(value, 8), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def run_profile_case(args):
+    """One condense, one K apply and one preconditioner application of a case, for ncu to capture
+    (c3s: the c3 element type on 16^3 x 6 cells, small enough for full captures)."""
+    import torch
+
+    import paper_2207_08481_gb300.mcs as mcs
+    import workloads
+    from paper_2207_08481_gb300 import build
+    build.build()
+    w = PROFILE_CASES[args.profile_case]
+    torch.cuda.set_device(0)
+    opts = dict(FORMS[args.form])
+    opts.pop("etol", None)
+    h = mcs.Handle.structured(w["dim"], w["N"], w["k"], w["nu"], gmg_levels=w["levels"], **opts)
+    h.condense()
+    F = _rhs(h, torch, workloads, w)
+    y = torch.zeros_like(F)
+    h.apply(F, y)
+    h.precond(F, y)
+    torch.cuda.synchronize()
+    h.close()
+    print("profile case done", flush=True)
 
 
 def main():
@@ -467,15 +684,32 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--ref-N", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline only (no c2, series, serving, batch)")
     ap.add_argument("--serve-requests", type=int, default=300,
-                    help="requests of the serving trace (2000 = the full trace; 0 = skip)")
+                    help="requests of the serving trace at --serve-rate (2000 = the full trace; 0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-requests2", type=int, default=200)
+    ap.add_argument("--serve-rate2", type=float, default=8.0,
+                    help="second trace at an arrival rate the GPU sustains (0 = skip)")
     ap.add_argument("--serve-slots", type=int, default=4)
-    ap.add_argument("--no-multi", action="store_true", help="skip the mixed-degree batch and the ASP comparison")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving traces (--serve-requests at --serve-rate, then --serve-requests2 at "
+                         "--serve-rate2) and print their summaries")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None)
+    ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.serve_only:
+        import torch
+        from paper_2207_08481_gb300 import build
+        build.build()
+        out = {"at_trace_rate": _serving(args, 0, 1, torch, None, args.serve_requests, args.serve_rate)}
+        if args.serve_rate2 > 0 and args.serve_requests2 > 0:
+            out["at_sustainable_rate"] = _serving(args, 0, 1, torch, None, args.serve_requests2, args.serve_rate2)
+        print(json.dumps({"serving": out}), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

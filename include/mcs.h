@@ -46,9 +46,9 @@
  *     * orthonormal Dubiner polynomials (homogeneous Jacobi products, total degree
  *       ascending) on the reference simplex and on the facet parameter simplex;
  *     * V_h = BDM^k as the dual basis of the facet moments int_F u.n_F q_j and of
- *       interior moments of the Piola pull-back against psi_a e_c (deg <= k-2) and
- *       the Nedelec-type functions (-y, x) x^a y^b (2D) or x cross (x^alpha e_c) (3D),
- *       |alpha| = k-2;
+ *       interior moments of the Piola pull-back against the list psi_a e_c (deg <= k-2),
+ *       then the Nedelec-type functions (-y, x) x^a y^b (2D) or x cross (x^alpha e_c) (3D),
+ *       |alpha| = k-2, made L2-orthonormal on the reference simplex in list order;
  *     * uhat: q_j(s) e_m on each interior facet, deg q_j <= k-1; p: Dubiner, deg <= k-1;
  *     * structured meshes: the Kuhn split of N^dim cells, vertex (i,j[,l]) has id
  *       i + (N+1)(j + (N+1) l); element cell*dim! + (permutation index).
@@ -88,10 +88,10 @@ typedef struct {
   double rtol;        /* stop when ||r||_{Khat^{-1}} <= rtol * ||F - K x0||_{Khat^{-1}} (1e-8) */
   int maxit;          /* total MinRes iterations (1000) */
   int max_refine;     /* outer refinement cycles after the first (8); MCS_FP64 uses at most 2 of them */
-  double inner_rtol;  /* MCS_MIXED: relative reduction per refinement cycle (1e-5) */
+  double inner_rtol;  /* MCS_MIXED, and both forms with etol > 0: relative reduction per refinement cycle (1e-5) */
   int residual_dd;    /* residual of each refinement cycle in double-double: 1 always, 0 never (plain
                          FP64 K x, whose rounding floors the attainable residual near 1e-12 relative
-                         for k = 4), -1 auto: when rtol < 1e-10 (-1) */
+                         for k = 4), -1 auto: when rtol < 1e-10 or etol > 0 (-1) */
   int asp;            /* auxiliary-space preconditioner for the condensed velocity block (Sec. 6.1):
                          0 multiplicative (smoother, coarse correction, adjoint smoother; default),
                          1 additive (facet-block Jacobi plus E^d C^{-1} E^d^T) */
@@ -101,6 +101,19 @@ typedef struct {
   int outflow;        /* mcs_setup_structured, k >= 2 only: 1 makes the face x_1 = 1 an outflow
                          boundary Gamma_Ntilde (eq. stokes_NT: u_t = 0, ((sigma + p I) n).n = 0);
                          0 (default): all faces Dirichlet.  See "Outflow" below. */
+  double etol;        /* > 0: stop on the solution's error as well as on the residual (0 = off, the
+                         default).  Then both forms run refinement cycles, each restarted from the exact
+                         residual: the correction d_c of cycle c (relative size rho_c = max(|d_u|/|x_u|,
+                         |d_p|/|x_p|), 2-norms of the u and p blocks) estimates the error entering it, and
+                         the error leaving it is bounded by est_c = 10 lag_c R_c rho_c with R_c the cycle's
+                         achieved residual reduction and lag_c = max(1, (rho_c / rho_{c-1}) / R_{c-1}) (from
+                         the third cycle on; else 1) how much less the previous cycle reduced the error
+                         than its residual; the next cycle is asked for the reduction that brings that
+                         bound to etol (at least inner_rtol in the mixed form).  The solve ends at
+                         the first cycle start after est_c <= etol whose recomputed residual meets rtol.
+                         With a pressure-dominated right-hand side (nu << 1) the velocity error exceeds
+                         the relative residual by orders of magnitude, which the residual test alone does
+                         not see. */
 } mcs_options;
 
 typedef struct {
@@ -120,6 +133,7 @@ typedef struct {
   int status;                /* MCS_OK, MCS_ERR_NOT_CONVERGED or MCS_ERR_BREAKDOWN */
   double rel_res_precond;    /* ||F - K x||_{Khat^{-1}} / ||F - K x0||_{Khat^{-1}} */
   double rel_res_true;       /* ||F - K x||_2 / ||F||_2 (FP64) */
+  double err_est;            /* opt.etol > 0: estimated relative error of x (see etol), else 0 */
 } mcs_solve_info;
 
 /* Version of the library (e.g. 100 = 0.1.0). */
@@ -141,7 +155,7 @@ int mcs_default_options(mcs_options* o);
 /* Set-up on the Kuhn triangulation of [0,1]^dim with N cells per direction
  * (Sec. 7 uses unstructured meshes; the synthetic workloads use this nested
  * family so that the conforming space has a geometric multigrid hierarchy).
- * dim in {2, 3}, k = 2..4 (Sec. 3), or k = 1 with dim = 3 (the lowest-order variant of Sec. 7),
+ * dim in {2, 3}, k = 2..6 (Sec. 3), or k = 1 with dim = 3 (the lowest-order variant of Sec. 7),
  * nu > 0 as printed in eq. (stokes).  stream: a cudaStream_t (NULL = default).
  * Builds mesh, facets, dof maps, colouring and the multigrid hierarchy on the
  * host and uploads them; allocates the resident operators.  Synchronous.
@@ -181,7 +195,7 @@ int mcs_condense(mcs_handle* h);
  * precision.  Runs on the stream of handles[0]; it waits for the work already enqueued on the other
  * handles' streams and their streams wait for it (events, no host synchronisation).  Takes a
  * temporary workspace from the stream-ordered allocator (largest element workspace x 4 blocks per
- * SM).  Errors: INVALID_ARG (NULL, count < 1, mixed precisions or devices), OOM, CUDA. */
+ * SM, fewer where that exceeds 2 GiB).  Errors: INVALID_ARG (NULL, count < 1, mixed precisions or devices), OOM, CUDA. */
 int mcs_condense_batch(mcs_handle* const* handles, int count);
 
 /* Copies the packed lower triangle of A_T (FP64, [count][n_A(n_A+1)/2], row-major
@@ -261,15 +275,15 @@ int mcs_profile_read(mcs_handle* h, mcs_kernel_stat* out, int max_n);
 int mcs_launch_count(uint64_t* count);
 
 /* Condensed element matrices without any device allocation, for callers that cannot let the
- * library allocate at call time (work enqueued during CUDA-graph stream capture, where
- * cudaMalloc is not allowed; applications that own the whole device through their own pool
- * or run under a fixed memory budget).  The paper has no counterpart: this is a deployment
- * variant of the condensation of Sec. 4.2.
+ * library allocate at call time: applications that own the whole device through their own pool
+ * or run under a fixed memory budget, and code paths that must not block on the allocator
+ * (cudaMalloc / cudaFree can synchronise the device).  The paper has no counterpart: this is a
+ * deployment variant of the condensation of Sec. 4.2.
  *   AT_out: device buffer [count][n_A][n_A] (FP64, full symmetric, local order u_d | u_o | uhat,
  *           orientation signs applied) receiving A_T of elements T0 .. T0+count-1 of the handle.
  * Workspace: a file-scope 4 MiB device array, held by every GPU that loads the library until
- * the process exits; one element's workspace must fit in it (3D k = 4 needs 1.1 MiB, the
- * largest supported case), else MCS_ERR_UNSUPPORTED.  Nothing is allocated or freed: no cudaMalloc, no allocating library
+ * the process exits; one element's workspace must fit in it (3D k = 4 needs 1.1 MiB and 3D k = 5
+ * 2.8 MiB; 3D k = 6, 6 MiB, is refused), else MCS_ERR_UNSUPPORTED.  Nothing is allocated or freed: no cudaMalloc, no allocating library
  * routine.  The first call on a device looks up the array's device address (with that device
  * current); make that first call before any stream capture.  All calls share the array, so
  * calls whose kernels overlap on the GPU (other streams, other host threads) race: order them

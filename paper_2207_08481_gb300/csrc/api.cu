@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <limits>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -68,6 +69,8 @@ void validate_options(const mcs_options& o) {
   if (o.asp < 0 || o.asp > 1) throw McsError(MCS_ERR_INVALID_ARG, "asp");
   if (o.lo_stab < 0 || o.lo_stab > 1) throw McsError(MCS_ERR_INVALID_ARG, "lo_stab");
   if (o.outflow < 0 || o.outflow > 1) throw McsError(MCS_ERR_INVALID_ARG, "outflow");
+  if (!(o.etol >= 0)) throw McsError(MCS_ERR_INVALID_ARG, "etol");
+  if (o.etol > 0 && !(o.inner_rtol > 0 && o.inner_rtol < 1)) throw McsError(MCS_ERR_INVALID_ARG, "inner_rtol");
 }
 
 template <class R>
@@ -211,7 +214,6 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   HostMesh& m = h->mesh;
   h->ref = build_reference(d, h->k);
   h->sz = h->ref.s;
-  if (h->sz.n_bub > 64) throw McsError(MCS_ERR_UNSUPPORTED, "more than 64 bubble functions per element");
   h->es = elem_sizes(h->sz);
   h->es.lo_stab = h->sz.lowest ? h->opt.lo_stab : 0;
   const Sizes& s = h->sz;
@@ -377,7 +379,7 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   } else {
     h->K.AT = h->dalloc<double>(m.ne * (int64_t)s.n_A * s.n_A);
   }
-  for (int i = 0; i < 11; ++i) h->kv[i] = h->dalloc<double>(L.ndof);
+  for (int i = 0; i < 12; ++i) h->kv[i] = h->dalloc<double>(L.ndof);
   h->ydd = h->dalloc<double>(4 * L.ndof);
   // an outflow facet has one element, so one of its two row-sum slots is never written: keep it 0
   cuda_check(cudaMemset(h->ydd, 0, sizeof(double) * 4 * L.ndof), "memset");
@@ -391,7 +393,7 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
   h->cond_scratch_doubles = condense_scratch_doubles(h->es, nsm);
   int maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  if (h->cond_scratch_doubles / ((int64_t)nsm * 8) * 8 > maxsm)
+  if (condense_slot_bytes(h->es) > maxsm || recover_slot_doubles(h->es) * 8 > maxsm)
     h->cond_scratch = h->dalloc<double>(h->cond_scratch_doubles);
   // wait for this set-up's own work only (legacy-stream memsets, the handle's stream): work of
   // other handles on other streams keeps running
@@ -401,11 +403,8 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
 
 mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* stream) {
   if (dim < 2 || dim > 3) throw McsError(MCS_ERR_UNSUPPORTED, "dim must be 2 or 3");
-  // k >= 5: the dual BDM basis of the dof contract (monomial interior moments) makes A_T so badly
-  // scaled (2D k = 6: entries near 1e11 around a facet Schur complement near 1e2) that the
-  // condensed blocks lose about 10 digits; 3D k >= 5 also exceeds the per-thread bubble block.
   // k = 1 is the lowest-order variant of Sec. 7, which the paper states for d = 3 (vector rotations).
-  if (k < 1 || k > 4) throw McsError(MCS_ERR_UNSUPPORTED, "k must be in 1..4");
+  if (k < 1 || k > 6) throw McsError(MCS_ERR_UNSUPPORTED, "k must be in 1..6");
   if (k == 1 && dim != 3) throw McsError(MCS_ERR_UNSUPPORTED, "k = 1 (lowest-order variant) needs dim = 3");
   if (!(nu > 0)) throw McsError(MCS_ERR_INVALID_ARG, "nu must be positive");
   auto h = std::make_unique<mcs_handle>();
@@ -461,7 +460,9 @@ void condense_batch(mcs_handle* const* hs, int count) {
     if (hs[i]->stream != st) cuda_check(cudaStreamWaitEvent(st, event_on(hs[i]->stream), 0), "wait");
   int nsm = 0;
   cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->device), "attribute");
-  const int64_t blocks = std::min<int64_t>((int64_t)nsm * 4, std::max<int64_t>(total, 1));
+  // up to 4 blocks per SM, fewer where their workspaces would exceed 2 GiB (3D k = 6: 6 MB each)
+  int64_t blocks = std::min<int64_t>((int64_t)nsm * 4, std::max<int64_t>(total, 1));
+  while (blocks > nsm && blocks * slot_bytes > (int64_t(2) << 30)) blocks -= nsm;
   const int64_t scratch_doubles = blocks * (slot_bytes / 8);
   void* items_dev = nullptr;
   double* scratch = nullptr;
@@ -491,7 +492,7 @@ void condense_batch(mcs_handle* const* hs, int count) {
 
 extern "C" {
 
-int mcs_version(void) { return 100; }
+int mcs_version(void) { return 200; }
 
 
 
@@ -511,6 +512,7 @@ int mcs_default_options(mcs_options* o) {
   o->asp = 0;
   o->lo_stab = 0;
   o->outflow = 0;
+  o->etol = 0.0;
   return MCS_OK;
 }
 
@@ -919,14 +921,15 @@ void capture_iterations(mcs_handle* h, double* x_acc) {
 
 // One MinRes cycle on K d = rhs from d = 0, accumulating d into x_acc.
 // g_first: preconditioned norm of the first cycle's residual (< 0 before the first cycle).
-void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double floor_rtol, int maxit, double g_first) {
+void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double rtol, double floor_rtol, int maxit,
+                  double g_first) {
   const int64_t n = h->L.ndof;
   cudaStream_t st = h->stream;
   double *v_old = h->kv[0], *v = h->kv[1], *z = h->kv[2], *zn = h->kv[3];
   double *w_old = h->kv[4], *w = h->kv[5], *Kz = h->kv[6];
   MinresScalars* S = h->S;
   MinresScalars init{};
-  init.rtol = h->opt.rtol;
+  init.rtol = rtol;
   init.floor_rtol = floor_rtol;
   init.g_first = g_first;
   init.maxit = maxit;
@@ -972,11 +975,17 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
     double* xi = h->kv[10];  // the iterate (fixed address for the captured iterations)
     cuda_check(cudaMemcpyAsync(xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy x");
     const bool mixed = h->opt.precision == MCS_MIXED;
+    const double etol = h->opt.etol;
     // FP64 form: cycles to rtol, restarted from the recomputed residual (at most 3).  Mixed
-    // form: iterative refinement, each cycle asked for at least inner_rtol reduction.
-    const int max_cycles = mixed ? std::max(2, h->opt.max_refine + 1) : std::min(3, std::max(2, h->opt.max_refine + 1));
-    const double floor_rtol = mixed ? h->opt.inner_rtol : 0.0;
-    const bool dd = h->opt.residual_dd == 1 || (h->opt.residual_dd == -1 && h->opt.rtol < 1e-10);
+    // form, and both forms with an error target: iterative refinement, each cycle asked for at
+    // least inner_rtol reduction.
+    const int max_cycles = (mixed || etol > 0) ? std::max(2, h->opt.max_refine + 1)
+                                               : std::min(3, std::max(2, h->opt.max_refine + 1));
+    const double floor_rtol = (mixed || etol > 0) ? h->opt.inner_rtol : 0.0;
+    // an error target needs the exact residual: with nu << 1 the velocity part of F - K x is a small
+    // difference of O(1) terms whose FP64 rounding floors the attainable velocity error
+    const bool dd = h->opt.residual_dd == 1 ||
+                    (h->opt.residual_dd == -1 && (h->opt.rtol < 1e-10 || h->opt.etol > 0));
     auto residual = [&](const double* xv) {  // r = F - K xv
       if (dd) {
         cuda_check(launch_residual_dd(h->es, h->dt, h->dm, h->L, h->K, F, xv, h->ydd, r, st), "residual");
@@ -987,9 +996,29 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
     };
     int total_it = 0, cycles = 0, status = MCS_ERR_NOT_CONVERGED;
     double g_first = -1.0, g_now = 0.0;
+    // Error target (etol > 0): cycle c's correction d_c estimates the error entering it (relative size
+    // rho_c, the larger of the u and p blocks).  The error leaving it is taken as lag * R_c * rho_c, R_c
+    // the cycle's achieved residual reduction and lag = max(1, (rho_c / rho_{c-1}) / R_{c-1}) how much
+    // less the previous cycle reduced the error than the residual (from the second correction on), and
+    // bounded by est_c = kSafety lag R_c rho_c.  The next cycle is asked for the reduction that brings
+    // this bound to etol.
+    constexpr double kSafety = 10.0;
+    const double r_min = mixed ? h->opt.inner_rtol : 1e-12;   // least reduction asked of one cycle
+    double est = std::numeric_limits<double>::infinity();
+    double rho_prev = -1.0, red_prev = -1.0;
+    int ncorr = 0;   // corrections measured so far
+    double r_next = mixed ? std::max(h->opt.rtol, h->opt.inner_rtol) : h->opt.rtol;
+    double* xprev = h->kv[11];
+    double* res = h->scratch + 3002;   // [|d_u|^2, |d_p|^2, |x_u|^2, |x_p|^2]
+    const int64_t nu_blk = h->L.off_p, np_blk = n - h->L.off_p;
     while (cycles < max_cycles) {
       residual(xi);
-      minres_cycle(h, r, xi, floor_rtol, std::max(1, h->opt.maxit - total_it), g_first);
+      if (etol > 0) cuda_check(cudaMemcpyAsync(xprev, xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+      // the residual test may end the solve only once the error bound meets etol
+      const bool err_ok = etol > 0 && est <= etol;
+      const double rtol_now = (etol > 0 && !err_ok) ? 0.0 : h->opt.rtol;
+      const double floor_now = etol > 0 ? (err_ok ? r_min : r_next) : floor_rtol;
+      minres_cycle(h, r, xi, rtol_now, floor_now, std::max(1, h->opt.maxit - total_it), g_first);
       const MinresScalars& Sh = *h->S_host;
       g_first = Sh.g_first;
       g_now = Sh.res0;
@@ -1002,6 +1031,31 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       if (Sh.it == 0 && (g_now <= h->opt.rtol * g_first || g_now == 0.0)) {
         status = MCS_OK;  // the recomputed residual meets the tolerance
         break;
+      }
+      if (etol > 0) {
+        const double achieved = Sh.res0 > 0 ? std::fabs(Sh.eta) / Sh.res0 : 0.0;
+        // d = xi - xprev, the cycle's correction; block norms of d and of the iterate
+        if (!h->outflow)
+          cuda_check(launch_mean_zero(h->dm, h->L, h->sz.n_p, xi, h->scratch, h->total_adet, nullptr, st), "mean");
+        cuda_check(launch_axpby(n, 1.0, xi, -1.0, xprev, st), "axpby");
+        cuda_check(launch_dot(xprev, xprev, nu_blk, h->scratch, res, nullptr, st), "dot");
+        cuda_check(launch_dot(xprev + nu_blk, xprev + nu_blk, np_blk, h->scratch, res + 1, nullptr, st), "dot");
+        cuda_check(launch_dot(xi, xi, nu_blk, h->scratch, res + 2, nullptr, st), "dot");
+        cuda_check(launch_dot(xi + nu_blk, xi + nu_blk, np_blk, h->scratch, res + 3, nullptr, st), "dot");
+        double hv[4];
+        cuda_check(cudaMemcpyAsync(hv, res, sizeof(hv), cudaMemcpyDeviceToHost, st), "copy");
+        cuda_check(cudaStreamSynchronize(st), "sync");
+        const double ru = hv[2] > 0 ? std::sqrt(hv[0] / hv[2]) : 0.0;
+        const double rp = hv[3] > 0 ? std::sqrt(hv[1] / hv[3]) : 0.0;
+        const double rho = std::min(1.0, std::max(ru, rp));
+        double lag = 1.0;
+        if (ncorr >= 2 && rho_prev > 0 && red_prev > 0) lag = std::max(1.0, (rho / rho_prev) / red_prev);
+        const double e_now = lag * achieved * rho;   // nominal error leaving this cycle
+        est = kSafety * e_now;
+        r_next = e_now > 0 ? std::min(0.1, std::max(r_min, etol / (kSafety * lag * e_now))) : 0.1;
+        rho_prev = rho;
+        red_prev = achieved;
+        ++ncorr;
       }
       if (total_it >= h->opt.maxit) break;
     }
@@ -1021,6 +1075,7 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       info->status = status;
       info->rel_res_true = hv[1] > 0 ? std::sqrt(hv[0] / hv[1]) : 0.0;
       info->rel_res_precond = g_first > 0 ? g_now / g_first : 0.0;
+      info->err_est = etol > 0 ? est : 0.0;
     }
     {
       // a bounded wait inside the preconditioner that gave up marks the solve as timed out

@@ -636,16 +636,16 @@ __host__ __device__ inline void bubble_condense(const ElemSizes& s, const double
       for (int p = i + 1; p < no; ++p) v -= Lo[p * no + i] * G[p * nc + c];
       G[i * nc + c] = v / Lo[i * no + i];
     }
-  // Aoo^{-1} = Lo^{-T} Lo^{-1}: column j solves
+  // Aoo^{-1} = Lo^{-T} Lo^{-1}: column j solves, the forward result kept in the output column itself
+  // (the backward pass reads y_i before it overwrites it)
   for (int j = lane; j < no; j += nl) {
-    double y[64];
     for (int i = 0; i < no; ++i) {
       double v = (i == j) ? 1.0 : 0.0;
-      for (int p = 0; p < i; ++p) v -= Lo[i * no + p] * y[p];
-      y[i] = v / Lo[i * no + i];
+      for (int p = 0; p < i; ++p) v -= Lo[i * no + p] * Aoo_inv[p * no + j];
+      Aoo_inv[i * no + j] = v / Lo[i * no + i];
     }
     for (int i = no - 1; i >= 0; --i) {
-      double v = y[i];
+      double v = Aoo_inv[i * no + j];
       for (int p = i + 1; p < no; ++p) v -= Lo[p * no + i] * Aoo_inv[p * no + j];
       Aoo_inv[i * no + j] = v / Lo[i * no + i];
     }

@@ -67,7 +67,8 @@ struct mcs_handle {
   bool condensed = false;
   bool outflow = false;               // Gamma_Ntilde marked (phantom uhat slots, no pressure mean)
   // Krylov work
-  double *kv[11] = {nullptr};  // Krylov vectors; kv[10] is the iterate the captured graph updates
+  double *kv[12] = {nullptr};  // Krylov vectors; kv[10] is the iterate the captured graph updates,
+                               // kv[11] the previous iterate of a refinement cycle (error estimate)
   cudaStream_t cap_stream = nullptr;   // non-default stream for graph capture
   cudaGraphExec_t gexec = nullptr;     // two MinRes iterations
   uint64_t graph_kernels = 0;          // kernel nodes of gexec

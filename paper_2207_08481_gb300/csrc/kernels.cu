@@ -49,6 +49,56 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// 1D bulk copy (TMA, cp.async.bulk) global -> shared completing on an mbarrier of this CTA, with an L2
+// cache policy; dst and src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar,
+                                              uint64_t pol) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(d),
+      "l"(src), "r"(bytes), "r"(b), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Waits for the phase `parity` of bar to complete, at most about limit_ns nanoseconds (and at most
+// 2^24 polls); false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;   // the common case: no timer read
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
 struct WarpSync {
   __device__ void operator()() const { __syncwarp(); }
 };
@@ -257,8 +307,14 @@ template cudaError_t launch_condense_batch<double>(const CondenseItem<double>*, 
                                                    double*, int64_t, cudaStream_t);
 int64_t condense_slot_bytes(const ElemSizes& s) { return condense_slot_doubles(s) * 8; }
 
+// Global workspace of the condensation when one element's does not fit in shared memory: a slot per
+// resident block, up to 8 blocks per SM, fewer where that would exceed 2 GiB (3D k = 5, 6: 2.8 and
+// 6 MB per element).
 int64_t condense_scratch_doubles(const ElemSizes& s, int nsm) {
-  return condense_slot_doubles(s) * (int64_t)nsm * 8;
+  const int64_t slot = condense_slot_doubles(s);
+  int64_t per_sm = 8;
+  while (per_sm > 1 && slot * nsm * per_sm * 8 > (int64_t(2) << 30)) --per_sm;
+  return slot * (int64_t)nsm * per_sm;
 }
 
 // ---------------------------------------------------------------- facet blocks
@@ -317,7 +373,8 @@ __global__ void k_facet_blocks(ElemSizes s, DevMesh m, R* Fs) {
 template <class R>
 cudaError_t launch_facet_blocks(const ElemSizes& s, const DevMesh& m, R* Fs, cudaStream_t st) {
   if (m.nint == 0) return cudaSuccess;
-  int wpb = 4;
+  int wpb = 4;   // warps per block, each with two m_F x m_F FP64 work matrices (fewer for large m_F)
+  while (wpb > 1 && (size_t)wpb * 2 * s.mF * s.mF * sizeof(double) > 200 * 1024) --wpb;
   size_t sm = (size_t)wpb * 2 * s.mF * s.mF * sizeof(double);
   cudaFuncSetAttribute(k_facet_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int64_t blocks = (m.nint + wpb - 1) / wpb;
@@ -503,11 +560,15 @@ __global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m,
     if (i < nA) {
       const float* ah = Ah + e * pp;
       const float* al = Al + e * pp;
+      // one loop over the row, the packed index chosen per entry (row part j <= i, column part
+      // j > i), so the lanes of a warp, which hold rows of different lengths, do not diverge
       const int row = i * (i + 1) / 2;
-      for (int j = 0; j <= i; ++j) df_mac(acc, ah[row + j], al[row + j], xe[j], xle[j]);
-      for (int j = i + 1; j < nA; ++j) {
-        const int idx = j * (j + 1) / 2 + i;
+      int colidx = row + i;               // j(j+1)/2 + i for j = i
+#pragma unroll 4
+      for (int j = 0; j < nA; ++j) {
+        const int idx = j <= i ? row + j : colidx;
         df_mac(acc, ah[idx], al[idx], xe[j], xle[j]);
+        if (j >= i) colidx += j + 1;      // next: (j+1)(j+2)/2 + i
       }
       if (i < nu_) {  // (B^T x_p)_i = -s_i sum_j Bhat[j][i] x_p[j]
         const float sgn = i < nfd ? sg[e * 4 + i / s.nF] : 1.f;
@@ -530,80 +591,101 @@ __global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m,
   }
 }
 
-// y = K x from the FP32 leading parts hi = fl(A_T) of the packed float pairs alone, with FP32 products
-// and sums (x rounded to FP32): half the bytes of the double-float apply and one FMA per entry.
-// Used inside the refinement cycles of the mixed form, whose residuals are formed exactly.
-template <class S>
-__global__ void __launch_bounds__(256) k_apply_K_f32(S s, DevTables t, DevMesh m, Layout L,
-                                                     const float* __restrict__ Ahi, const double* __restrict__ x,
-                                                     double* y, int EB, const int* stop) {
+// The double-float apply for elements whose packed pairs do not fit in shared memory (3D k >= 5): one
+// block per element, the packed lower triangle streamed through shared memory in chunks of whole
+// rows [r0, r1) (one contiguous range of the packed storage each); a thread owns rows i = tid + 256 m
+// and adds, per chunk, the row part A_ij x_j (j <= i, i in the chunk) and the column part A_ji x_j
+// (j in the chunk, j > i).  The same products as k_apply_K_df, summed in another order.
+template <int MAXR>
+__global__ void __launch_bounds__(256) k_apply_K_df_chunk(ElemSizes s, DevTables t, DevMesh m, Layout L,
+                                                          const float* __restrict__ Ahi,
+                                                          const float* __restrict__ Alo,
+                                                          const double* __restrict__ x, double* y, int chunk,
+                                                          const int* stop) {
   if (stop && *stop) return;
-  extern __shared__ float skf[];
+  extern __shared__ float skc[];
   const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d, nfd = (s.d + 1) * s.nF;
   const int per = nA + np_, pp = packed_pad(s);
-  float* Ah = skf;                    // [EB][pp]
-  float* xs = Ah + EB * pp;           // [EB][per]
-  int* er = (int*)(xs + EB * per);    // [EB][4]
-  float* sg = (float*)(er + EB * 4);  // [EB][4]
+  float* ch = skc;                   // [chunk] hi
+  float* cl = ch + chunk;            // [chunk] lo
+  float* xh = cl + chunk;            // [per]
+  float* xl = xh + per;              // [per]
+  int* er = (int*)(xl + per);        // [4]
+  float* sg = (float*)(er + 4);      // [4]
   const int tid = threadIdx.x;
-  const int64_t T0 = (int64_t)blockIdx.x * EB;
-  const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
-  if (tid < EB * 4) {
-    int e = tid >> 2, f = tid & 3;
-    int64_t T = T0 + e;
-    bool ok = e < nvalid && f <= d;
-    er[tid] = ok ? m.elem_rank[T * (d + 1) + f] : -1;
-    sg[tid] = ok ? (float)m.signs[T * (d + 1) + f] : 0.f;
-  }
-  vcopy16<float>(Ah, Ahi + T0 * pp, nvalid * pp, tid, blockDim.x);
-  __syncthreads();
-  for (int q = tid; q < nvalid * per; q += blockDim.x) {
-    const int e = q / per, i = q - e * per;
-    const int64_t T = T0 + e;
-    double v;
-    if (i < nA) {
-      int64_t g = local_to_global(s, L, er + e * 4, T, i);
-      v = g < 0 ? 0.0 : x[g];
-    } else {
-      v = x[L.off_p + T * np_ + (i - nA)];
+  for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) {
+    if (tid < 4) {
+      er[tid] = tid <= d ? m.elem_rank[T * (d + 1) + tid] : -1;
+      sg[tid] = tid <= d ? (float)m.signs[T * (d + 1) + tid] : 0.f;
     }
-    xs[q] = (float)v;
-  }
-  __syncthreads();
-  for (int q = tid; q < nvalid * per; q += blockDim.x) {
-    const int e = q / per, i = q - e * per;
-    const int64_t T = T0 + e;
-    const float* xe = xs + e * per;
-    float v0 = 0.f, v1 = 0.f;
-    if (i < nA) {
-      const float* ah = Ah + e * pp;
-      const int row = i * (i + 1) / 2;
-      int j = 0;
-      for (; j + 1 <= i; j += 2) {
-        v0 = __fmaf_rn(ah[row + j], xe[j], v0);
-        v1 = __fmaf_rn(ah[row + j + 1], xe[j + 1], v1);
+    __syncthreads();
+    for (int q = tid; q < per; q += blockDim.x) {
+      double v;
+      if (q < nA) {
+        const int64_t g = local_to_global(s, L, er, T, q);
+        v = g < 0 ? 0.0 : x[g];
+      } else {
+        v = x[L.off_p + T * np_ + (q - nA)];
       }
-      if (j <= i) v0 = __fmaf_rn(ah[row + j], xe[j], v0);
-      for (int jj = i + 1; jj < nA; ++jj) v1 = __fmaf_rn(ah[jj * (jj + 1) / 2 + i], xe[jj], v1);
+      const float h = (float)v;
+      xh[q] = h;
+      xl[q] = (float)(v - (double)h);
+    }
+    DF acc[MAXR];
+#pragma unroll
+    for (int u = 0; u < MAXR; ++u) acc[u] = DF{0.f, 0.f, 0.f};
+    const float* Ah = Ahi + T * (int64_t)pp;
+    const float* Al = Alo + T * (int64_t)pp;
+    int r0 = 0;
+    while (r0 < nA) {
+      int r1 = r0 + 1;   // rows [r0, r1) with at most `chunk` packed entries (one row always fits)
+      while (r1 < nA && (r1 + 1) * (r1 + 2) / 2 - r0 * (r0 + 1) / 2 <= chunk) ++r1;
+      const int base = r0 * (r0 + 1) / 2, cnt = r1 * (r1 + 1) / 2 - base;
+      __syncthreads();   // the previous chunk is consumed (and x is staged)
+      for (int q = tid; q < cnt; q += blockDim.x) {
+        ch[q] = Ah[base + q];
+        cl[q] = Al[base + q];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < MAXR; ++u) {
+        const int i = tid + u * blockDim.x;
+        if (i >= nA) continue;
+        if (i >= r0 && i < r1) {            // row part of row i
+          const int o = i * (i + 1) / 2 - base;
+          for (int j = 0; j <= i; ++j) df_mac(acc[u], ch[o + j], cl[o + j], xh[j], xl[j]);
+        }
+        for (int j = (i + 1 > r0 ? i + 1 : r0); j < r1; ++j) {   // column part: A_ji, j > i
+          const int o = j * (j + 1) / 2 - base + i;
+          df_mac(acc[u], ch[o], cl[o], xh[j], xl[j]);
+        }
+      }
+      r0 = r1;
+    }
+#pragma unroll
+    for (int u = 0; u < MAXR; ++u) {
+      const int i = tid + u * blockDim.x;
+      if (i >= nA) continue;
       if (i < nu_) {  // (B^T x_p)_i = -s_i sum_j Bhat[j][i] x_p[j]
-        const float sgn = i < nfd ? sg[e * 4 + i / s.nF] : 1.f;
-        float bt = 0.f;
-        for (int p = 0; p < np_; ++p) bt = __fmaf_rn(t.Bp_hi[p * nu_ + i], xe[nA + p], bt);
-        v0 -= sgn * bt;
+        const float sgn = i < nfd ? sg[i / s.nF] : 1.f;
+        for (int p = 0; p < np_; ++p)
+          df_mac(acc[u], -sgn * t.Bp_hi[p * nu_ + i], -sgn * t.Bp_lo[p * nu_ + i], xh[nA + p], xl[nA + p]);
       }
-      const double v = (double)v0 + (double)v1;
-      int64_t g = local_to_global(s, L, er + e * 4, T, i);
+      const double v = df_value(acc[u]);
+      const int64_t g = local_to_global(s, L, er, T, i);
       if (g < 0) continue;
       if (i >= nfd && i < nu_) y[g] = v;     // bubble: owned by T
       else atomicAdd(&y[g], v);             // facet dof: exactly two contributions into 0
-    } else {
-      const int jp = i - nA;
-      for (int c = 0; c < nu_; ++c) {
-        const float sgn = c < nfd ? sg[e * 4 + c / s.nF] : 1.f;
-        v0 = __fmaf_rn(-sgn * t.Bp_hi[jp * nu_ + c], xe[c], v0);
-      }
-      y[L.off_p + T * np_ + jp] = (double)v0;
     }
+    for (int jp = tid; jp < np_; jp += blockDim.x) {
+      DF a{0.f, 0.f, 0.f};
+      for (int c = 0; c < nu_; ++c) {
+        const float sgn = c < nfd ? sg[c / s.nF] : 1.f;
+        df_mac(a, -sgn * t.Bp_hi[jp * nu_ + c], -sgn * t.Bp_lo[jp * nu_ + c], xh[c], xl[c]);
+      }
+      y[L.off_p + T * np_ + jp] = df_value(a);
+    }
+    __syncthreads();
   }
 }
 
@@ -633,11 +715,30 @@ cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh
   // algorithmic: packed symmetric A_T, x read once, y written once; flops: full row products
   const double alg_bytes = (double)m.ne * s.n_A * (s.n_A + 1) / 2 * 8.0 + 16.0 * L.ndof;
   const double alg_flops = 2.0 * (double)m.ne * ((double)s.n_A * s.n_A + 2.0 * s.n_u * s.n_p);
+  if (K.Ahi && (2 * (size_t)packed_pad(s) + 2 * per) * sizeof(float) > 160 * 1024) {
+    // packed pairs of one element beyond shared memory: streamed in row chunks of 12,288 entries
+    const int chunk = 12288;
+    const size_t sm = (2 * (size_t)chunk + 2 * per) * sizeof(float) + 64;
+    int64_t blocks = (int64_t)sm_count() * 2;
+    if (blocks > m.ne) blocks = m.ne;
+    if (s.n_A > 512) return cudaErrorInvalidValue;
+    static std::atomic<bool> set{false};
+    if (!set.load(std::memory_order_acquire)) {
+      cudaFuncSetAttribute(k_apply_K_df_chunk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set.store(true, std::memory_order_release);
+    }
+    prof_begin(PROF_APPLY, st);
+    k_apply_K_df_chunk<2><<<(unsigned)blocks, 256, sm, st>>>(s, t, m, L, K.Ahi, K.Alo, x, y, chunk, stop);
+    note_launch();
+    prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
+    return cudaGetLastError();
+  }
   if (K.Ahi) {
     const size_t per_bytes = (2 * (size_t)packed_pad(s) + 2 * per) * sizeof(float) + 4 * (sizeof(int) + sizeof(float));
-    int EB = (int)((40 * 1024) / per_bytes);
+    // one (element, row) per thread in one pass: as many elements as fill 256 threads, within 64 KB
+    int EB = 256 / per;
+    while (EB > 1 && (size_t)EB * per_bytes > 64 * 1024) --EB;
     if (EB < 1) EB = 1;
-    if (EB > 16) EB = 16;
     const int threads = EB * per <= 128 ? 128 : 256;
     const size_t sm = (size_t)EB * per_bytes + 64;
     const int64_t blocks = (m.ne + EB - 1) / EB;
@@ -674,36 +775,6 @@ cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh
       k_apply_K<decltype(sz), true><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.AT, x, y, EB, stop);
     else
       k_apply_K<decltype(sz), false><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.AT, x, y, EB, stop);
-    note_launch();
-    prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
-  });
-  return cudaGetLastError();
-}
-
-cudaError_t launch_apply_K_f32(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, KOp K,
-                               const double* x, double* y, const int* stop, cudaStream_t st) {
-  if (!K.Ahi) return cudaErrorInvalidValue;
-  k_zero_facet<<<sm_count() * 4, 256, 0, st>>>(L, y, stop);
-  note_launch();
-  const int per = s.n_A + s.n_p;
-  // algorithmic: packed symmetric A_T in FP32, x read once, y written once
-  const double alg_bytes = (double)m.ne * s.n_A * (s.n_A + 1) / 2 * 4.0 + 16.0 * L.ndof;
-  const double alg_flops = 2.0 * (double)m.ne * ((double)s.n_A * s.n_A + 2.0 * s.n_u * s.n_p);
-  const size_t per_bytes = ((size_t)packed_pad(s) + per) * sizeof(float) + 4 * (sizeof(int) + sizeof(float));
-  int EB = (int)((24 * 1024) / per_bytes);
-  if (EB < 1) EB = 1;
-  if (EB > 16) EB = 16;
-  const int threads = EB * per <= 128 ? 128 : 256;
-  const size_t sm = (size_t)EB * per_bytes + 64;
-  const int64_t blocks = (m.ne + EB - 1) / EB;
-  dispatch_sizes(s, [&](auto sz) {
-    static std::atomic<bool> set{false};
-    if (!set.load(std::memory_order_acquire)) {
-      cudaFuncSetAttribute(k_apply_K_f32<decltype(sz)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      set.store(true, std::memory_order_release);
-    }
-    prof_begin(PROF_APPLY, st);
-    k_apply_K_f32<decltype(sz)><<<(unsigned)blocks, threads, sm, st>>>(sz, t, m, L, K.Ahi, x, y, EB, stop);
     note_launch();
     prof_end(PROF_APPLY, alg_bytes, alg_flops, st);
   });
@@ -814,6 +885,104 @@ __global__ void __launch_bounds__(256) k_residual_rows(S s, DevTables t, DevMesh
   }
 }
 
+// The rows of K_T x_T in double-double for elements whose A_T does not fit in shared memory (3D
+// k >= 5): one block per element, a thread per row i = tid + 256 u.  FP64 storage (full symmetric):
+// A_ij read as A[j][i] straight from global memory (lanes of consecutive i read consecutive
+// addresses); float pairs (packed lower): streamed through shared memory in chunks of whole rows as
+// exact doubles hi + lo, row part and column part as in k_apply_K_df_chunk.  Output slots as in
+// k_residual_rows.
+template <bool PACKED, int MAXR>
+__global__ void __launch_bounds__(256) k_residual_rows_big(ElemSizes s, DevTables t, DevMesh m, Layout L,
+                                                           const double* __restrict__ AT,
+                                                           const float* __restrict__ Ahi,
+                                                           const float* __restrict__ Alo,
+                                                           const double* __restrict__ x, double* __restrict__ Y,
+                                                           int chunk) {
+  extern __shared__ double srb[];
+  const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d, nfd = (s.d + 1) * s.nF;
+  const int per = nA + np_, pp = packed_pad(s);
+  const int64_t nd = L.ndof;
+  double* xs = srb;                  // [per]
+  double* cb = xs + per;             // [chunk] (PACKED)
+  const int tid = threadIdx.x;
+  for (int64_t T = blockIdx.x; T < m.ne; T += gridDim.x) {
+    const int8_t* sg = m.signs + T * (d + 1);
+    for (int q = tid; q < per; q += blockDim.x) {
+      double v;
+      if (q < nA) {
+        const int64_t g = local_to_global(s, L, m.elem_rank + T * (d + 1), T, q);
+        v = g < 0 ? 0.0 : x[g];
+      } else {
+        v = x[L.off_p + T * np_ + (q - nA)];
+      }
+      xs[q] = v;
+    }
+    __syncthreads();
+    DDv acc[MAXR];
+#pragma unroll
+    for (int u = 0; u < MAXR; ++u) acc[u] = DDv{0.0, 0.0};
+    if (!PACKED) {
+      const double* A = AT + T * (int64_t)nA * nA;
+#pragma unroll
+      for (int u = 0; u < MAXR; ++u) {
+        const int i = tid + u * blockDim.x;
+        if (i >= nA) continue;
+        for (int j = 0; j < nA; ++j) dd_mac(acc[u], A[(int64_t)j * nA + i], xs[j]);
+      }
+    } else {
+      const float* Ah = Ahi + T * (int64_t)pp;
+      const float* Al = Alo + T * (int64_t)pp;
+      int r0 = 0;
+      while (r0 < nA) {
+        int r1 = r0 + 1;
+        while (r1 < nA && (r1 + 1) * (r1 + 2) / 2 - r0 * (r0 + 1) / 2 <= chunk) ++r1;
+        const int base = r0 * (r0 + 1) / 2, cnt = r1 * (r1 + 1) / 2 - base;
+        __syncthreads();
+        for (int q = tid; q < cnt; q += blockDim.x) cb[q] = (double)Ah[base + q] + (double)Al[base + q];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < MAXR; ++u) {
+          const int i = tid + u * blockDim.x;
+          if (i >= nA) continue;
+          if (i >= r0 && i < r1) {
+            const int o = i * (i + 1) / 2 - base;
+            for (int j = 0; j <= i; ++j) dd_mac(acc[u], cb[o + j], xs[j]);
+          }
+          for (int j = (i + 1 > r0 ? i + 1 : r0); j < r1; ++j) dd_mac(acc[u], cb[j * (j + 1) / 2 - base + i], xs[j]);
+        }
+        r0 = r1;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < MAXR; ++u) {
+      const int i = tid + u * blockDim.x;
+      if (i >= nA) continue;
+      if (i < nu_) {  // (B^T x_p)_i = -s_i sum_p Bhat[p][i] x_p[p]
+        const double sgn = i < nfd ? (double)sg[i / s.nF] : 1.0;
+        for (int p = 0; p < np_; ++p) dd_mac(acc[u], -sgn * t.Bp[p * nu_ + i], xs[nA + p]);
+      }
+      const int64_t g = local_to_global(s, L, m.elem_rank + T * (d + 1), T, i);
+      if (g < 0) continue;
+      int slot = 0;
+      if (i < nfd) slot = sg[i / s.nF] > 0 ? 0 : 1;
+      else if (i >= nu_) slot = sg[(i - nu_) / s.nhF] > 0 ? 0 : 1;
+      Y[(2 * slot) * nd + g] = acc[u].hi;
+      Y[(2 * slot + 1) * nd + g] = acc[u].lo;
+    }
+    for (int jp = tid; jp < np_; jp += blockDim.x) {
+      DDv a{0.0, 0.0};
+      for (int c = 0; c < nu_; ++c) {
+        const double sgn = c < nfd ? (double)sg[c / s.nF] : 1.0;
+        dd_mac(a, -sgn * t.Bp[jp * nu_ + c], xs[c]);
+      }
+      const int64_t g = L.off_p + T * np_ + jp;
+      Y[g] = a.hi;
+      Y[nd + g] = a.lo;
+    }
+    __syncthreads();
+  }
+}
+
 // r_g = F_g - (slot 0 + slot 1 for facet dofs, slot 0 otherwise), in double-double, rounded once.
 __global__ void k_residual_combine(Layout L, const double* F, const double* __restrict__ Y, double* r) {
   const int64_t nd = L.ndof;
@@ -831,6 +1000,28 @@ cudaError_t launch_residual_dd(const ElemSizes& s, const DevTables& t, const Dev
   const int bs = 256;
   const int per = s.n_A + s.n_p;
   const size_t per_bytes = ((size_t)s.n_A * (s.n_A + 1) / 2 + per) * sizeof(double);
+  if (per_bytes > 160 * 1024) {
+    // one element's A_T beyond shared memory
+    if (s.n_A > 512) return cudaErrorInvalidValue;
+    const int chunk = 12288;
+    const size_t sm = ((size_t)per + (K.Ahi ? chunk : 0)) * sizeof(double) + 16;
+    int64_t g = (int64_t)sm_count() * 2;
+    if (g > m.ne) g = m.ne;
+    static std::atomic<bool> set{false};
+    if (!set.load(std::memory_order_acquire)) {
+      cudaFuncSetAttribute(k_residual_rows_big<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(k_residual_rows_big<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set.store(true, std::memory_order_release);
+    }
+    if (K.Ahi)
+      k_residual_rows_big<true, 2><<<(unsigned)g, bs, sm, st>>>(s, t, m, L, nullptr, K.Ahi, K.Alo, x, Y, chunk);
+    else
+      k_residual_rows_big<false, 2><<<(unsigned)g, bs, sm, st>>>(s, t, m, L, K.AT, nullptr, nullptr, x, Y, chunk);
+    note_launch();
+    k_residual_combine<<<sm_count() * 8, bs, 0, st>>>(L, F, Y, r);
+    note_launch();
+    return cudaGetLastError();
+  }
   int EB = bs / per;
   while (EB > 1 && (size_t)EB * per_bytes > 48 * 1024) --EB;
   if (EB < 1) EB = 1;
@@ -1093,7 +1284,7 @@ __global__ void k_from_prec(ElemSizes s, Layout L, Layout PL, const R* __restric
 //   rin_o = r_o - (B^T z_p)_o                          (WITH_BT; else rin_o = r_o)
 //   tb   += (B^T z_p)_c + (G^T rin_o)_c                 (two contributions per facet dof, into zero)
 // B = -Bhat diag(sign) (reading R18), z_p read from zp (pressure layout of the full vector).
-template <class R, class S, bool WITH_BT>
+template <class R, class S, bool WITH_BT, bool STAGE = true>
 __global__ void __launch_bounds__(256) k_elem_prologue(S s, DevTables t, DevMesh m, Layout L,
                                                        const R* __restrict__ G, const R* __restrict__ r,
                                                        const R* __restrict__ zp, R* rin, R* tb, int EB,
@@ -1102,14 +1293,17 @@ __global__ void __launch_bounds__(256) k_elem_prologue(S s, DevTables t, DevMesh
   extern __shared__ unsigned char sraw[];
   const int d = s.d, nc = s.n_c, no = s.n_bub, nu_ = s.n_u, np_ = s.n_p, nfd = (s.d + 1) * s.nF;
   const int gs = g_stride(s);
-  R* Gs = (R*)sraw;              // [EB][gs]
-  R* ro = Gs + EB * gs;          // [EB][no]
+  // STAGE: G of the EB elements in shared memory; else (one element's G beyond shared memory) read from
+  // global memory, column c of row o at o*nc + c (lanes of consecutive c: consecutive addresses)
+  R* Gst = (R*)sraw;             // [EB][gs] (STAGE)
+  R* ro = Gst + (STAGE ? EB * gs : 0);   // [EB][no]
   R* bt = ro + EB * no;          // [EB][nu]
   R* zz = bt + EB * nu_;         // [EB][np]
   const int64_t T0 = (int64_t)blockIdx.x * EB;
   const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
   const int tid = threadIdx.x;
-  vcopy16<R>(Gs, G + T0 * gs, nvalid * gs, tid, blockDim.x);
+  const R* Gs = STAGE ? Gst : G + T0 * gs;
+  if (STAGE) vcopy16<R>(Gst, G + T0 * gs, nvalid * gs, tid, blockDim.x);
   for (int q = tid; q < nvalid * no; q += blockDim.x) ro[q] = r[L.off_o + T0 * no + q];
   if (WITH_BT)
     for (int q = tid; q < nvalid * np_; q += blockDim.x) zz[q] = zp[L.off_p + T0 * np_ + q];
@@ -1153,7 +1347,7 @@ __global__ void __launch_bounds__(256) k_elem_prologue(S s, DevTables t, DevMesh
 //   x_o = A_oo^{-1} rin_o - G x_c
 // WITH_P (first application of eq. mhatinvfactor): also z_p = Shat_p^{-1}(r_p - B a), a = (x_c, x_o),
 // Shat_p = M_p = nu^{-1}(p, q)  ->  z_p = nu/|det J| (r_p - B a).
-template <class R, class S, bool WITH_P>
+template <class R, class S, bool WITH_P, bool STAGE = true>
 __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh m, Layout L, double nu,
                                                        const R* __restrict__ G, const R* __restrict__ Aoi,
                                                        const R* __restrict__ rin, const R* __restrict__ r, R* x,
@@ -1162,16 +1356,22 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
   extern __shared__ unsigned char sraw[];
   const int d = s.d, nc = s.n_c, no = s.n_bub, nu_ = s.n_u, np_ = s.n_p, nfd = (s.d + 1) * s.nF, mF = s.mF;
   const int gs = g_stride(s), as_ = a_stride(s);
-  R* Gs = (R*)sraw;              // [EB][gs]
-  R* As = Gs + EB * gs;          // [EB][as]
-  R* xc = As + EB * as_;         // [EB][nc]
+  // STAGE: G and A_oo^{-1} of the EB elements in shared memory; else read from global memory (one
+  // element), A_oo^{-1} by columns (it is symmetric), G by rows
+  R* Gst = (R*)sraw;             // [EB][gs] (STAGE)
+  R* Ast = Gst + (STAGE ? EB * gs : 0);  // [EB][as] (STAGE)
+  R* xc = Ast + (STAGE ? EB * as_ : 0);  // [EB][nc]
   R* ro = xc + EB * nc;          // [EB][no]
   R* xo = ro + EB * no;          // [EB][no]
   const int64_t T0 = (int64_t)blockIdx.x * EB;
   const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
   const int tid = threadIdx.x;
-  vcopy16<R>(Gs, G + T0 * gs, nvalid * gs, tid, blockDim.x);
-  vcopy16<R>(As, Aoi + T0 * as_, nvalid * as_, tid, blockDim.x);
+  const R* Gs = STAGE ? Gst : G + T0 * gs;
+  const R* As = STAGE ? Ast : Aoi + T0 * as_;
+  if (STAGE) {
+    vcopy16<R>(Gst, G + T0 * gs, nvalid * gs, tid, blockDim.x);
+    vcopy16<R>(Ast, Aoi + T0 * as_, nvalid * as_, tid, blockDim.x);
+  }
   for (int q = tid; q < nvalid * no; q += blockDim.x) ro[q] = rin[L.off_o + T0 * no + q];
   for (int q = tid; q < nvalid * nc; q += blockDim.x) {
     const int e = q / nc, c = q - e * nc;
@@ -1183,10 +1383,11 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
   for (int q = tid; q < nvalid * no; q += blockDim.x) {
     const int e = q / no, o = q - e * no;
     R v = 0;
-    const R* a = As + e * as_ + o * no;
+    const R* a = As + e * as_ + (STAGE ? o * no : o);   // row o, or column o of the symmetric inverse
+    const int ast = STAGE ? 1 : no;
     const R* rv = ro + e * no;
 #pragma unroll 4
-    for (int p = 0; p < no; ++p) v += a[p] * rv[p];
+    for (int p = 0; p < no; ++p) v += a[p * ast] * rv[p];
     const R* g = Gs + e * gs + o * nc;
     const R* xv = xc + e * nc;
 #pragma unroll 4
@@ -1601,7 +1802,7 @@ template <class R, class S, bool UPDATE>
 __global__ void __launch_bounds__(256) k_facet_step_warp(S s, Layout L, const R* __restrict__ Fs,
                                                          const R* __restrict__ b, const R* __restrict__ tb, R* x,
                                                          R* rr, const int* __restrict__ rec, int64_t n,
-                                                         const int* stop) {
+                                                         const int* stop, int* err) {
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char swr[];
   const int mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), fss = fs_stride(s), nc = s.n_c;
@@ -1609,8 +1810,18 @@ __global__ void __launch_bounds__(256) k_facet_step_warp(S s, Layout L, const R*
   const int se = warp_stage_elems<S, R>(s);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   R* wbase = reinterpret_cast<R*>(swr) + (size_t)wib * 2 * se;
+  // the two mbarriers of this warp's stages follow all warps' stages
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<R*>(swr) + (size_t)(blockDim.x >> 5) * 2 * se) + 2 * wib;
+  const unsigned sbytes = (unsigned)((UPDATE ? fss : 2 * slab) * (int)sizeof(R));   // stream bytes per facet
+  if (lane == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 1, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  unsigned phases = 0u;   // bit st: parity of the next phase of stage st's mbarrier
   constexpr int V = 16 / (int)sizeof(R);
-  const int cf = fss / V, cslab = 2 * slab / V, cx = fs / V;
+  const int cx = fs / V;
   const int rows = 2 * mF;
   const int LP = rows <= 16 ? 2 : 1;            // lanes per row
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -1628,9 +1839,10 @@ __global__ void __launch_bounds__(256) k_facet_step_warp(S s, Layout L, const R*
 #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2) gseg[k2] = __shfl_sync(0xffffffffu, myrec, 5 + k2);
     const int r = __shfl_sync(0xffffffffu, myrec, 0);
-    for (int q = lane; q < cf; q += 32) {
-      if (!UPDATE && q >= cslab) break;
-      cp_async16_hint(Sb + q * V, src + q * V, pol);
+    // the facet's stream block (contiguous, 16-byte aligned): one bulk copy on the stage's mbarrier
+    if (lane == 0) {
+      mbar_expect_tx(bars + st, sbytes);
+      bulk_copy_g2s(Sb, src, sbytes, bars + st, pol);
     }
     for (int q = lane; q < 2 * dp1 * cx; q += 32) {
       const int seg = q / cx, ch = q - seg * cx;   // seg = side*dp1 + local facet
@@ -1661,7 +1873,22 @@ __global__ void __launch_bounds__(256) k_facet_step_warp(S s, Layout L, const R*
     }
     cp_async_commit();
     cp_async_wait_group<1>();
+    // bounded wait for the stream block (about a second): on expiry the error flag is set, the
+    // other stage's copy is waited for (bounded too) and the warp stops
+    bool got = true;
+    if (lane == 0) got = mbar_wait_bounded(bars + st, (phases >> st) & 1u, 1000000000ull);
+    got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+    if (!got) {
+      if (lane == 0) {
+        atomicExch(err, 1);
+        if (fn < n) mbar_wait_bounded(bars + (st ^ 1), (phases >> (st ^ 1)) & 1u, 1000000000ull);
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      return;
+    }
     __syncwarp();
+    phases ^= 1u << st;
     const R* Sb = wbase + st * se;
     const R* Xs = Sb + fss;
     const R* Bs = Xs + 2 * dp1 * fs;
@@ -1699,6 +1926,76 @@ __global__ void __launch_bounds__(256) k_facet_step_warp(S s, Layout L, const R*
   cp_async_wait_all();
 }
 
+// Facet step for facet blocks too large to stage in shared memory (3D k >= 5): one block per facet
+// (grid stride over the records), the gathered segments, b and tb in shared memory, the two slabs and
+// D_F^{-1} read from global memory directly (slab column c, row t at c*mF + t: lanes of consecutive
+// t read consecutive addresses; D_F^{-1} is symmetric, so its column t is read for row t).  Same
+// arithmetic as k_facet_step.  Shared memory: [2][d+1][fs] segments, b, tb, [P][2 m_F] partial sums.
+template <class R, class S, bool UPDATE>
+__global__ void __launch_bounds__(256) k_facet_step_direct(S s, Layout L, const R* __restrict__ Fs,
+                                                           const R* __restrict__ b, const R* __restrict__ tb, R* x,
+                                                           R* rr, const int* __restrict__ rec, int64_t n,
+                                                           const int* stop) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(16) unsigned char sdr[];
+  const int mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), fss = fs_stride(s), nc = s.n_c;
+  const int fs = facet_stride(s, (int)sizeof(R));
+  const int rows = 2 * mF;
+  const int P = blockDim.x / rows > 0 ? blockDim.x / rows : 1;   // parts per row
+  R* Xs = reinterpret_cast<R*>(sdr);          // [2][d+1][fs]
+  R* Bs = Xs + 2 * dp1 * fs;                  // [fs]
+  R* Ts = Bs + fs;                            // [fs]
+  R* Yp = Ts + fs;                            // [P][rows]
+  R* Rv = Yp + P * rows;                      // [mF] r_F
+  const int tid = threadIdx.x;
+  for (int64_t f = blockIdx.x; f < n; f += gridDim.x) {
+    const int* rc = rec + f * 16;
+    const int r = rc[0];
+    for (int q = tid; q < 2 * dp1 * fs; q += blockDim.x) {
+      const int seg = q / fs, t = q - seg * fs;          // seg = side*dp1 + local facet
+      const int g = rc[5 + seg];
+      Xs[q] = (g >= 0 && t < mF) ? x[(int64_t)g * fs + t] : (R)0;
+    }
+    for (int q = tid; q < fs; q += blockDim.x) {
+      Bs[q] = (r >= 0 && q < mF) ? b[(int64_t)r * fs + q] : (R)0;
+      Ts[q] = (r >= 0 && q < mF && tb) ? tb[(int64_t)r * fs + q] : (R)0;
+    }
+    __syncthreads();
+    const R* blk = Fs + f * (int64_t)fss;
+    for (int q = tid; q < P * rows; q += blockDim.x) {
+      const int part = q / rows, row = q - part * rows;
+      const int side = row >= mF ? 1 : 0, t = row - side * mF;
+      const R* A = blk + side * slab + t;
+      const R* xv = Xs + side * dp1 * fs;
+      R y = 0;
+      for (int c = part; c < nc; c += P) {
+        const int fl = c / mF, tt = c - fl * mF;
+        y += A[(int64_t)c * mF] * xv[fl * fs + tt];
+      }
+      Yp[q] = y;
+    }
+    __syncthreads();
+    for (int t = tid; t < mF; t += blockDim.x) {
+      R y = 0;
+      for (int part = 0; part < P; ++part) y += Yp[part * rows + t] + Yp[part * rows + mF + t];
+      const R v = Bs[t] - Ts[t] - y;
+      if (UPDATE) Rv[t] = v;
+      else if (r >= 0) rr[(int64_t)r * fs + t] = v;
+    }
+    if (UPDATE) {
+      __syncthreads();
+      const R* Di = blk + 2 * slab;
+      const int f0 = rc[3];                      // local index of the facet in side 0
+      for (int t = tid; t < mF; t += blockDim.x) {
+        R v = 0;
+        for (int j = 0; j < mF; ++j) v += Di[j * mF + t] * Rv[j];
+        if (r >= 0) x[(int64_t)r * fs + t] = Xs[f0 * fs + t] + v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <class R>
 static size_t facet_step_smem(const ElemSizes& s, int FB, bool update) {
   (void)update;
@@ -1720,7 +2017,7 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
     // warp-per-facet kernel for large facet blocks (at least 4 KB of stream per facet: 3D; measured
     // faster there, slower than the batched block kernel for the 1.4 KB blocks of 2D k = 3), when the
     // 2 m_F rows fit a warp and 8 warps' stages fit in 100 KB
-    const size_t wsm = (size_t)8 * 2 * warp_stage_elems<ElemSizes, R>(s) * sizeof(R);
+    const size_t wsm = (size_t)8 * 2 * warp_stage_elems<ElemSizes, R>(s) * sizeof(R) + 8 * 2 * sizeof(uint64_t);
     if ((size_t)fs_stride(s) * sizeof(R) >= 4096 && 2 * s.mF <= 32 && wsm <= 100 * 1024) {
       bool done = false;
       dispatch_sizes(s, [&](auto sz) {
@@ -1745,9 +2042,11 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
         note_launch();
         const int* ri = reinterpret_cast<const int*>(rec0);
         if (update)
-          k_facet_step_warp<R, SZ, true><<<(unsigned)blocks, 256, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n, stop);
+          k_facet_step_warp<R, SZ, true><<<(unsigned)blocks, 256, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n, stop,
+                                                                               P.err);
         else
-          k_facet_step_warp<R, SZ, false><<<(unsigned)blocks, 256, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n, stop);
+          k_facet_step_warp<R, SZ, false><<<(unsigned)blocks, 256, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n, stop,
+                                                                                P.err);
         const double per = update ? (2.0 * s.mF * s.n_c + (double)s.mF * s.mF + 4.0 * s.mF)
                                   : (2.0 * s.mF * s.n_c + 3.0 * s.mF);
         prof_end(cls, (double)n * per * sizeof(R),
@@ -1760,6 +2059,26 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
         return cudaGetLastError();
       }
     }
+  }
+  if (facet_step_smem<R>(s, 1, update) > 200 * 1024) {
+    // one facet's stages do not fit: the unstaged kernel
+    const int fs = facet_stride(s, (int)sizeof(R));
+    const int rows = 2 * s.mF, parts = 256 / rows > 0 ? 256 / rows : 1;
+    const size_t sm = ((size_t)(2 * (s.d + 1) + 2) * fs + (size_t)parts * rows + s.mF) * sizeof(R) + 16;
+    int64_t blocks = (int64_t)sm_count() * 8;
+    if (blocks > n) blocks = n;
+    const int* ri = reinterpret_cast<const int*>(rec0);
+    const int cls = update ? PROF_FACET_GS : PROF_FACET_RES;
+    prof_begin(cls, st);
+    note_launch();
+    if (update)
+      k_facet_step_direct<R, ElemSizes, true><<<(unsigned)blocks, 256, sm, st>>>(s, L, fs0, b, tb, x, rr, ri, n, stop);
+    else
+      k_facet_step_direct<R, ElemSizes, false><<<(unsigned)blocks, 256, sm, st>>>(s, L, fs0, b, tb, x, rr, ri, n, stop);
+    const double per = update ? (2.0 * s.mF * s.n_c + (double)s.mF * s.mF + 4.0 * s.mF) : (2.0 * s.mF * s.n_c + 3.0 * s.mF);
+    prof_end(cls, (double)n * per * sizeof(R), 2.0 * (double)n * (2.0 * s.mF * s.n_c + (update ? s.mF * s.mF : 0)), st);
+    dbg_sync(P, st, update ? "k_facet_step_direct (update)" : "k_facet_step_direct (residual)");
+    return cudaGetLastError();
   }
   // small batches (at most 40 KB of stages, at least 4 facets) in narrow blocks, so that several
   // blocks share an SM and their barriers overlap; else up to 96 KB
@@ -1822,8 +2141,9 @@ template <class R, bool WITH_BT>
 static void elem_prologue(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, PrecData<R>& P,
                           const R* r, const R* zp, R* rin, R* tb, const int* stop, cudaStream_t st) {
   const size_t per = (size_t)(g_stride(s) + s.n_bub + s.n_u + s.n_p) * sizeof(R);
-  const int EB = elem_batch(per);
-  const size_t sm = per * EB + 16;
+  const bool stage = per + 16 <= 190 * 1024;   // else G is read from global memory, one element per block
+  const int EB = stage ? elem_batch(per) : 1;
+  const size_t sm = (stage ? per * EB : (size_t)(s.n_bub + s.n_u + s.n_p) * sizeof(R)) + 16;
   const int64_t blocks = (m.ne + EB - 1) / EB;
   dispatch_sizes(s, [&](auto sz) {
     using SZ = decltype(sz);
@@ -1833,7 +2153,11 @@ static void elem_prologue(const ElemSizes& s, const DevTables& t, const DevMesh&
       set.store(true, std::memory_order_release);
     }
     prof_begin(PROF_PROLOGUE, st);
-    k_elem_prologue<R, SZ, WITH_BT><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, P.G, r, zp, rin, tb, EB, stop);
+    if (stage)
+      k_elem_prologue<R, SZ, WITH_BT><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, P.G, r, zp, rin, tb, EB, stop);
+    else
+      k_elem_prologue<R, SZ, WITH_BT, false><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, P.G, r, zp, rin, tb, EB,
+                                                                                  stop);
     note_launch();
     prof_end(PROF_PROLOGUE, (double)m.ne * (s.n_bub * s.n_c + 2 * s.n_bub + s.n_c + (WITH_BT ? s.n_p : 0)) * sizeof(R),
              2.0 * (double)m.ne * s.n_bub * s.n_c, st);
@@ -1844,8 +2168,9 @@ template <class R, bool WITH_P>
 static void elem_epilogue(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
                           PrecData<R>& P, const R* rin, const R* r, R* x, R* zp, const int* stop, cudaStream_t st) {
   const size_t per = (size_t)(g_stride(s) + a_stride(s) + s.n_c + 2 * s.n_bub) * sizeof(R);
-  const int EB = elem_batch(per);
-  const size_t sm = per * EB + 16;
+  const bool stage = per + 16 <= 190 * 1024;   // else G and A_oo^{-1} are read from global memory
+  const int EB = stage ? elem_batch(per) : 1;
+  const size_t sm = (stage ? per * EB : (size_t)(s.n_c + 2 * s.n_bub) * sizeof(R)) + 16;
   const int64_t blocks = (m.ne + EB - 1) / EB;
   dispatch_sizes(s, [&](auto sz) {
     using SZ = decltype(sz);
@@ -1855,8 +2180,12 @@ static void elem_epilogue(const ElemSizes& s, const DevTables& t, const DevMesh&
       set.store(true, std::memory_order_release);
     }
     prof_begin(PROF_EPILOGUE, st);
-    k_elem_epilogue<R, SZ, WITH_P><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, nu, P.G, P.Aoi, rin, r, x, zp, EB,
-                                                                       stop);
+    if (stage)
+      k_elem_epilogue<R, SZ, WITH_P><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, nu, P.G, P.Aoi, rin, r, x, zp, EB,
+                                                                         stop);
+    else
+      k_elem_epilogue<R, SZ, WITH_P, false><<<(unsigned)blocks, 256, sm, st>>>(sz, t, m, L, nu, P.G, P.Aoi, rin, r, x,
+                                                                                zp, EB, stop);
     note_launch();
     prof_end(PROF_EPILOGUE, (double)m.ne * (s.n_bub * s.n_c + s.n_bub * s.n_bub + 2 * s.n_bub + s.n_c +
                                              (WITH_P ? 2 * s.n_p : 0)) * sizeof(R),

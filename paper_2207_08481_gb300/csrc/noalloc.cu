@@ -1,13 +1,11 @@
 // Element condensation without any device allocation (mcs_condense_noalloc).
 //
-// Some callers cannot let the library allocate device memory at call time: code that
-// enqueues work while a stream is being captured into a CUDA graph (cudaMalloc is not
-// permitted there), applications that have handed the whole device to their own memory
-// pool or run under a hard memory budget, and callbacks that must not block on the
-// allocator.  For them this entry point forms the condensed element matrices A_T of a
-// range of elements into a buffer the caller owns, using as workspace only a fixed
-// file-scope device array that every GPU loading the library holds until the process
-// exits.
+// Some callers cannot let the library allocate device memory at call time: applications that
+// have handed the whole device to their own memory pool or run under a hard memory budget, and
+// code paths that must not block on the allocator (cudaMalloc and cudaFree can synchronise the
+// device).  For them this entry point forms the condensed element matrices A_T of a range of
+// elements into a buffer the caller owns, using as workspace only a fixed file-scope device array
+// that every GPU loading the library holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>

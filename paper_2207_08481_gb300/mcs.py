@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("gmg_smooth", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("residual_dd", ctypes.c_int), ("asp", ctypes.c_int), ("lo_stab", ctypes.c_int),
-                ("outflow", ctypes.c_int)]
+                ("outflow", ctypes.c_int), ("etol", ctypes.c_double)]
 
 
 class Sizes(ctypes.Structure):
@@ -51,7 +51,8 @@ class Sizes(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("status", ctypes.c_int),
-                ("rel_res_precond", ctypes.c_double), ("rel_res_true", ctypes.c_double)]
+                ("rel_res_precond", ctypes.c_double), ("rel_res_true", ctypes.c_double),
+                ("err_est", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -274,7 +275,17 @@ class Handle:
                                              flops=buf[i].flops) for i in range(n)}
 
     def condense_noalloc(self, T0, count, AT_out):
-        """A_T of elements T0 .. T0+count-1 into the device tensor AT_out [count, n_A, n_A] (no allocation)."""
+        """A_T of elements T0 .. T0+count-1 into the device tensor AT_out [count, n_A, n_A] (no allocation).
+        The kernel writes count * n_A^2 doubles: a shorter, non-float64 or other-device tensor is refused
+        here, before the library sees the pointer."""
+        import torch
+        nA = int(self.sizes.n_A)
+        if AT_out.dtype != torch.float64:
+            raise ValueError("AT_out must be float64")
+        if AT_out.numel() < int(count) * nA * nA:
+            raise ValueError(f"AT_out holds {AT_out.numel()} doubles, {int(count) * nA * nA} are written")
+        if AT_out.device != torch.device("cuda", torch.cuda.current_device()):
+            raise ValueError("AT_out must be on the current CUDA device (the handle's device)")
         _check(lib().mcs_condense_noalloc(self._h, T0, count, _dptr(AT_out)))
 
     def solve_host(self, F: np.ndarray, x: np.ndarray, check=True):

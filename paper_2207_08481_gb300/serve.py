@@ -97,7 +97,7 @@ def estimate_bytes(dim: int, N: int, k: int) -> int:
     ndof = nf * mF + ne * (nbub + npres)
     per_elem = 8 * (nA * (nA + 1) // 2) + 4 * ((dim + 1) * (nc * mF + 3) + nbub * nc + nbub * nbub + 8)
     per_facet = 4 * (mF * mF + 4 + mF * dim * dim) + 64 + 64
-    vectors = 8 * ndof * 11 + 4 * ndof * 5
+    vectors = 8 * ndof * 12 + 4 * ndof * 5
     gmg = 2 * (N + 1) ** dim * dim * 4 * 60
     return int(1.3 * (ne * per_elem + nf * per_facet + vectors + gmg)) + (64 << 20)
 
@@ -105,7 +105,7 @@ def estimate_bytes(dim: int, N: int, k: int) -> int:
 class GpuBackend:
     """Runs requests with libmcs on the current CUDA device."""
 
-    def __init__(self, precision=None, rtol=1e-8):
+    def __init__(self, precision=None, rtol=1e-8, etol=1e-8):
         import torch
 
         import paper_2207_08481_gb300.mcs as mcs
@@ -113,6 +113,7 @@ class GpuBackend:
         self.mcs = mcs
         self.precision = mcs.MCS_MIXED if precision is None else precision
         self.rtol = rtol
+        self.etol = etol
 
     def new_stream(self):
         return self.torch.cuda.Stream()
@@ -123,7 +124,8 @@ class GpuBackend:
         hs = self.torch.cuda.Stream()
         hs.wait_stream(stream)
         with self.torch.cuda.stream(hs):
-            h = self.mcs.Handle.structured(dim, N, k, 1.0, stream=hs, precision=self.precision, rtol=self.rtol)
+            h = self.mcs.Handle.structured(dim, N, k, 1.0, stream=hs, precision=self.precision, rtol=self.rtol,
+                                           etol=self.etol)
             h.condense()
         return h
 

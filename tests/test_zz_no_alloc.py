@@ -1,9 +1,9 @@
 """mcs_condense_noalloc: element matrices for callers that cannot allocate device memory.
 
-Callers enqueuing work during CUDA-graph stream capture (where cudaMalloc is not allowed),
-or applications that own the whole device through their own memory pool, need an entry
-point that allocates nothing.  This file is collected last so that a run stopping at the
-first failure has already run every other test; it also passes on its own in a fresh process.
+Applications that own the whole device through their own memory pool or run under a hard memory
+budget, and code paths that must not block on the allocator, need an entry point that allocates
+nothing.  This file is collected last so that a run stopping at the first failure has already run
+every other test; it also passes on its own in a fresh process.
 """
 import numpy as np
 import pytest
@@ -23,7 +23,7 @@ def mcs():
     return m
 
 
-@pytest.mark.parametrize("d,N,k,nu", [(2, 8, 3, 0.7), (3, 2, 2, 1.3)])
+@pytest.mark.parametrize("d,N,k,nu", [(2, 8, 3, 0.7), (3, 2, 2, 1.3), (3, 1, 4, 0.5), (3, 2, 1, 1.0)])
 def test_noalloc_condense_matches_condense(mcs, d, N, k, nu):
     """Two calls in a row of the no-allocation entry point against mcs_condense's A_T."""
     h = mcs.Handle.structured(d, N, k, nu, precision=mcs.MCS_FP64, gmg_levels=1)
@@ -49,4 +49,9 @@ def test_noalloc_rejects_bad_arguments(mcs):
     with pytest.raises(mcs.McsError) as e:
         h.condense_noalloc(h.sizes.ne, 1, out)
     assert e.value.code == mcs.MCS_ERR_INVALID_ARG
+    # buffers the kernel would overrun are refused by the binding before any launch
+    with pytest.raises(ValueError):
+        h.condense_noalloc(0, 2, out)                              # one element's room for two
+    with pytest.raises(ValueError):
+        h.condense_noalloc(0, 1, out.to(torch.float32))
     h.close()
