@@ -335,6 +335,12 @@ def run_gpu(args):
             roof["frac_s8d"] = round(s8 / (per_launch_ms * 1e-3) / 1e9 / peak, 4)
             roof["layout_over_s8d"] = round(st["bytes"] / nl / s8, 3)
     share = {k: round(v["ms"] / sum(u["ms"] for u in stats.values()), 4) for k, v in stats.items() if v["launches"]}
+    # per class of the profiled step: launches, device ms, algorithmic GB/s (or TFLOP/s for the condensation)
+    kstats = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                  "us_per_launch": round(1e3 * v["ms"] / v["launches"], 2),
+                  "alg_gb_per_s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["bytes"] else None,
+                  "tflop_per_s": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 3) if v["flops"] else None}
+              for k, v in stats.items() if v["launches"]}
 
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -355,7 +361,7 @@ def run_gpu(args):
         "err_vs_oracle": err_vs_oracle,
         "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": 2 * ndof * 8,
                 "d2h_bytes_per_step": ndof * 8},
-        "roofline": roof, "kernel_time_share": share,
+        "roofline": roof, "kernel_time_share": share, "kernel_stats": kstats,
         "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

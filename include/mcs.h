@@ -103,17 +103,24 @@ typedef struct {
                          0 (default): all faces Dirichlet.  See "Outflow" below. */
   double etol;        /* > 0: stop on the solution's error as well as on the residual (0 = off, the
                          default).  Then both forms run refinement cycles, each restarted from the exact
-                         residual: the correction d_c of cycle c (relative size rho_c = max(|d_u|/|x_u|,
-                         |d_p|/|x_p|), 2-norms of the u and p blocks) estimates the error entering it, and
-                         the error leaving it is bounded by est_c = 10 lag_c R_c rho_c with R_c the cycle's
-                         achieved residual reduction and lag_c = max(1, (rho_c / rho_{c-1}) / R_{c-1}) (from
-                         the third cycle on; else 1) how much less the previous cycle reduced the error
-                         than its residual; the next cycle is asked for the reduction that brings that
-                         bound to etol (at least inner_rtol in the mixed form).  The solve ends at
-                         the first cycle start after est_c <= etol whose recomputed residual meets rtol.
-                         With a pressure-dominated right-hand side (nu << 1) the velocity error exceeds
-                         the relative residual by orders of magnitude, which the residual test alone does
-                         not see. */
+                         (double-double) residual: the correction d_c of cycle c (relative size rho_c =
+                         max(|d_u|/|x_u|, |d_p|/|x_p|), 2-norms of the u and p blocks) estimates the error
+                         entering it, and the error leaving it is bounded by est_c = 3 lag R_c rho_c with
+                         R_c the cycle's achieved residual reduction and lag = max(1, (rho_c/rho_{c-1}) /
+                         R_{c-1}) (from the third cycle on; else 1) how much less the previous cycle reduced
+                         the error than its residual.  The first cycle runs to rtol (mixed form: to
+                         inner_rtol); each later one ends as soon as that bound, evaluated on its
+                         correction so far every 8 iterations, is <= etol.  The solve ends at the first
+                         cycle start after est_c <= etol whose recomputed residual meets rtol; the bound is
+                         returned in mcs_solve_info.err_est.  With a pressure-dominated right-hand side
+                         (nu << 1) the velocity error exceeds the relative residual by orders of magnitude,
+                         which the residual test alone does not see. */
+  int tune;           /* 1: at the first mcs_condense of the handle, time the candidate launch shapes of the
+                         batched facet step (2D) and of the staged K apply on the handle's own data and keep
+                         the fastest (results are bitwise the same for every shape); 0 (default): the
+                         shared-memory formulas */
+  const char* tune_cache;  /* tune = 1: optional path of a text file of tuned shapes, one line per
+                         (dim, k, precision, element count); read before tuning, appended after (NULL: none) */
 } mcs_options;
 
 typedef struct {
@@ -125,6 +132,7 @@ typedef struct {
   int32_t ncolours, gmg_levels;
   int32_t nq_load;                          /* load quadrature points per element */
   int64_t bytes_resident;                   /* device bytes held by the handle */
+  int32_t facet_batch, facet_threads, apply_batch;   /* launch shapes in use (-1: formulas; see tune) */
 } mcs_sizes_t;
 
 typedef struct {

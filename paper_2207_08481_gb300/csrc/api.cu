@@ -71,6 +71,7 @@ void validate_options(const mcs_options& o) {
   if (o.outflow < 0 || o.outflow > 1) throw McsError(MCS_ERR_INVALID_ARG, "outflow");
   if (!(o.etol >= 0)) throw McsError(MCS_ERR_INVALID_ARG, "etol");
   if (o.etol > 0 && !(o.inner_rtol > 0 && o.inner_rtol < 1)) throw McsError(MCS_ERR_INVALID_ARG, "inner_rtol");
+  if (o.tune < 0 || o.tune > 1) throw McsError(MCS_ERR_INVALID_ARG, "tune");
 }
 
 template <class R>
@@ -414,6 +415,10 @@ mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* 
   if (opt) h->opt = *opt;
   else mcs_default_options(&h->opt);
   validate_options(h->opt);
+  if (h->opt.tune_cache) {   // the caller's string need not outlive the call
+    h->tune_cache = h->opt.tune_cache;
+    h->opt.tune_cache = h->tune_cache.c_str();
+  }
   if (h->opt.outflow && k == 1) throw McsError(MCS_ERR_UNSUPPORTED, "outflow with k = 1");
   h->stream = (cudaStream_t)stream;
   cuda_check(cudaGetDevice(&h->device), "cudaGetDevice");
@@ -423,6 +428,46 @@ mcs_handle* new_handle(int dim, int k, double nu, const mcs_options* opt, void* 
 }  // namespace
 
 void mcs::set_last_error(const char* msg) { g_err = msg ? msg : "unknown error"; }
+
+namespace {
+// The tuned launch shapes of a handle: from the cache file when it has a line for this (dim, k, precision,
+// element count), else by timing the candidates (autotune_launches), then appended to the cache.
+template <class R>
+void tune_handle(mcs_handle* h, PrecData<R>& P) {
+  char key[160];
+  std::snprintf(key, sizeof(key), "mcs-tune dim=%d k=%d precision=%d ne=%lld lo_stab=%d", h->d, h->k,
+                h->opt.precision, (long long)h->mesh.ne, h->es.lo_stab);
+  if (h->opt.tune_cache) {
+    if (FILE* f = std::fopen(h->opt.tune_cache, "r")) {
+      char line[512];
+      while (std::fgets(line, sizeof(line), f)) {
+        if (std::strncmp(line, key, std::strlen(key)) != 0 || line[std::strlen(key)] != ' ') continue;
+        int fb = -1, th = -1, eb = -1;
+        if (std::sscanf(line + std::strlen(key), " fb=%d threads=%d eb=%d", &fb, &th, &eb) == 3) {
+          P.fb = fb;
+          P.fthreads = th;
+          h->K.eb = eb;
+          std::fclose(f);
+          h->tuned = true;
+          return;
+        }
+      }
+      std::fclose(f);
+    }
+  }
+  char report[4096] = {0};
+  cuda_check(autotune_launches<R>(h->es, h->dt, h->dm, h->L, P, h->K, h->kv[0], h->kv[1], h->stream, report,
+                                  (int)sizeof(report)),
+             "autotune");
+  h->tuned = true;
+  if (h->opt.tune_cache) {
+    if (FILE* f = std::fopen(h->opt.tune_cache, "a")) {
+      std::fprintf(f, "%s fb=%d threads=%d eb=%d  # %s\n", key, P.fb, P.fthreads, h->K.eb, report);
+      std::fclose(f);
+    }
+  }
+}
+}  // namespace
 
 namespace {
 template <class R>
@@ -513,6 +558,8 @@ int mcs_default_options(mcs_options* o) {
   o->lo_stab = 0;
   o->outflow = 0;
   o->etol = 0.0;
+  o->tune = 0;
+  o->tune_cache = nullptr;
   return MCS_OK;
 }
 
@@ -594,6 +641,9 @@ int mcs_sizes(const mcs_handle* h, mcs_sizes_t* s) {
     s->ncolours = h->ncol; s->gmg_levels = h->nlev;
     s->nq_load = h->ref.nq_load;
     s->bytes_resident = h->bytes;
+    s->facet_batch = h->opt.precision == MCS_MIXED ? h->pf.fb : h->pd.fb;
+    s->facet_threads = h->opt.precision == MCS_MIXED ? h->pf.fthreads : h->pd.fthreads;
+    s->apply_batch = h->K.eb;
     return MCS_OK;
   });
 }
@@ -707,6 +757,10 @@ int mcs_condense(mcs_handle* h) {
       cuda_check(launch_facet_blocks<double>(h->es, h->dm, h->pd.Fs, h->stream), "facet blocks");
     }
     h->condensed = true;
+    if (h->opt.tune && !h->tuned) {
+      if (h->opt.precision == MCS_MIXED) tune_handle<float>(h, h->pf);
+      else tune_handle<double>(h, h->pd);
+    }
     return MCS_OK;
   });
 }
@@ -921,8 +975,16 @@ void capture_iterations(mcs_handle* h, double* x_acc) {
 
 // One MinRes cycle on K d = rhs from d = 0, accumulating d into x_acc.
 // g_first: preconditioned norm of the first cycle's residual (< 0 before the first cycle).
+// Early end of a cycle on the error bound (etol > 0): with x_start the iterate at the cycle's start, the
+// cycle stops at a check once bound * (|eta| / res0) * rho <= etol, rho = max(|d_u|/|x_u|, |d_p|/|x_p|)
+// for the correction d = x_acc - x_start so far (bound = the safety factor times the lag).
+struct CycleBound {
+  const double* x_start = nullptr;   // nullptr: no early end
+  double bound = 0, etol = 0;
+};
+
 void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double rtol, double floor_rtol, int maxit,
-                  double g_first) {
+                  double g_first, const CycleBound& cb = CycleBound()) {
   const int64_t n = h->L.ndof;
   cudaStream_t st = h->stream;
   double *v_old = h->kv[0], *v = h->kv[1], *z = h->kv[2], *zn = h->kv[3];
@@ -947,10 +1009,24 @@ void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double rtol, 
   const bool graphs = h->use_graphs && !h->prof;
   if (graphs && !h->gexec) capture_iterations(h, x_acc);
   const int check_every = 8;  // iterations between reads of the convergence state
+  const int64_t nu_blk = h->L.off_p, np_blk = n - h->L.off_p;
+  double* res = h->scratch + 3010;   // [|d_u|^2, |d_p|^2, |x_u|^2, |x_p|^2] of the early-end check
   while (true) {
     cuda_check(cudaMemcpyAsync(h->S_host, S, sizeof(MinresScalars), cudaMemcpyDeviceToHost, st), "read S");
     cuda_check(cudaStreamSynchronize(st), "sync");
     if (h->S_host->stop) break;
+    if (cb.x_start && h->S_host->it > 0 && h->S_host->res0 > 0) {
+      cuda_check(launch_diff_sq(x_acc, cb.x_start, nu_blk, h->scratch, res, st), "diff");
+      cuda_check(launch_diff_sq(x_acc + nu_blk, cb.x_start + nu_blk, np_blk, h->scratch, res + 1, st), "diff");
+      cuda_check(launch_dot(x_acc, x_acc, nu_blk, h->scratch, res + 2, nullptr, st), "dot");
+      cuda_check(launch_dot(x_acc + nu_blk, x_acc + nu_blk, np_blk, h->scratch, res + 3, nullptr, st), "dot");
+      double hv[4];
+      cuda_check(cudaMemcpyAsync(hv, res, sizeof(hv), cudaMemcpyDeviceToHost, st), "copy");
+      cuda_check(cudaStreamSynchronize(st), "sync");
+      const double rho = std::min(1.0, std::max(hv[2] > 0 ? std::sqrt(hv[0] / hv[2]) : 0.0,
+                                                hv[3] > 0 ? std::sqrt(hv[1] / hv[3]) : 0.0));
+      if (cb.bound * (std::fabs(h->S_host->eta) / h->S_host->res0) * rho <= cb.etol) break;
+    }
     if (graphs) {
       for (int q = 0; q < check_every / 2; ++q) {
         cuda_check(cudaGraphLaunch(h->gexec, st), "cudaGraphLaunch");
@@ -999,13 +1075,14 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
     // Error target (etol > 0): cycle c's correction d_c estimates the error entering it (relative size
     // rho_c, the larger of the u and p blocks).  The error leaving it is taken as lag * R_c * rho_c, R_c
     // the cycle's achieved residual reduction and lag = max(1, (rho_c / rho_{c-1}) / R_{c-1}) how much
-    // less the previous cycle reduced the error than the residual (from the second correction on), and
-    // bounded by est_c = kSafety lag R_c rho_c.  The next cycle is asked for the reduction that brings
-    // this bound to etol.
-    constexpr double kSafety = 10.0;
+    // less the previous cycle reduced the error than the residual (from the third correction on), and
+    // bounded by est_c = kSafety lag R_c rho_c.  The first cycle runs to rtol (mixed: inner_rtol); every
+    // later one runs until its own correction so far shows the bound met (checked every 8 iterations),
+    // or to the least reduction r_min.
+    constexpr double kSafety = 3.0;
     const double r_min = mixed ? h->opt.inner_rtol : 1e-12;   // least reduction asked of one cycle
     double est = std::numeric_limits<double>::infinity();
-    double rho_prev = -1.0, red_prev = -1.0;
+    double rho_prev = -1.0, red_prev = -1.0, lag_now = 1.0;
     int ncorr = 0;   // corrections measured so far
     double r_next = mixed ? std::max(h->opt.rtol, h->opt.inner_rtol) : h->opt.rtol;
     double* xprev = h->kv[11];
@@ -1017,8 +1094,17 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       // the residual test may end the solve only once the error bound meets etol
       const bool err_ok = etol > 0 && est <= etol;
       const double rtol_now = (etol > 0 && !err_ok) ? 0.0 : h->opt.rtol;
-      const double floor_now = etol > 0 ? (err_ok ? r_min : r_next) : floor_rtol;
-      minres_cycle(h, r, xi, rtol_now, floor_now, std::max(1, h->opt.maxit - total_it), g_first);
+      // after the first correction a cycle runs to the least reduction and ends early once its own
+      // correction shows the error bound met (the check every 8 iterations)
+      const bool adaptive = etol > 0 && !err_ok && ncorr >= 1;
+      const double floor_now = etol > 0 ? ((err_ok || adaptive) ? r_min : r_next) : floor_rtol;
+      CycleBound cbound;
+      if (adaptive) {
+        cbound.x_start = xprev;
+        cbound.bound = kSafety * lag_now;
+        cbound.etol = etol;
+      }
+      minres_cycle(h, r, xi, rtol_now, floor_now, std::max(1, h->opt.maxit - total_it), g_first, cbound);
       const MinresScalars& Sh = *h->S_host;
       g_first = Sh.g_first;
       g_now = Sh.res0;
@@ -1048,11 +1134,10 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
         const double ru = hv[2] > 0 ? std::sqrt(hv[0] / hv[2]) : 0.0;
         const double rp = hv[3] > 0 ? std::sqrt(hv[1] / hv[3]) : 0.0;
         const double rho = std::min(1.0, std::max(ru, rp));
-        double lag = 1.0;
-        if (ncorr >= 2 && rho_prev > 0 && red_prev > 0) lag = std::max(1.0, (rho / rho_prev) / red_prev);
-        const double e_now = lag * achieved * rho;   // nominal error leaving this cycle
+        if (ncorr >= 2 && rho_prev > 0 && red_prev > 0) lag_now = std::max(1.0, (rho / rho_prev) / red_prev);
+        const double e_now = lag_now * achieved * rho;   // nominal error leaving this cycle
         est = kSafety * e_now;
-        r_next = e_now > 0 ? std::min(0.1, std::max(r_min, etol / (kSafety * lag * e_now))) : 0.1;
+        r_next = e_now > 0 ? std::min(0.1, std::max(r_min, etol / (kSafety * lag_now * e_now))) : 0.1;
         rho_prev = rho;
         red_prev = achieved;
         ++ncorr;

@@ -65,6 +65,8 @@ struct mcs_handle {
   PrecData<float> pf{};
   PrecData<double> pd{};
   bool condensed = false;
+  bool tuned = false;                 // opt.tune: launch shapes chosen (by timing or from the cache)
+  std::string tune_cache;             // copy of opt.tune_cache (opt.tune_cache points here or is NULL)
   bool outflow = false;               // Gamma_Ntilde marked (phantom uhat slots, no pressure mean)
   // Krylov work
   double *kv[12] = {nullptr};  // Krylov vectors; kv[10] is the iterate the captured graph updates,

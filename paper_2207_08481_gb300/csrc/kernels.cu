@@ -738,6 +738,7 @@ cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh
     // one (element, row) per thread in one pass: as many elements as fill 256 threads, within 64 KB
     int EB = 256 / per;
     while (EB > 1 && (size_t)EB * per_bytes > 64 * 1024) --EB;
+    if (K.eb > 0 && (size_t)K.eb * per_bytes <= 160 * 1024) EB = K.eb;   // autotuned
     if (EB < 1) EB = 1;
     const int threads = EB * per <= 128 ? 128 : 256;
     const size_t sm = (size_t)EB * per_bytes + 64;
@@ -761,6 +762,7 @@ cudaError_t launch_apply_K(const ElemSizes& s, const DevTables& t, const DevMesh
   int EB = staged ? (int)((40 * 1024) / per_bytes) : 1;
   if (EB < 1) EB = 1;
   if (EB > 16) EB = 16;
+  if (staged && K.eb > 0 && (size_t)K.eb * per_bytes + 64 <= 160 * 1024) EB = K.eb;   // autotuned
   const int threads = EB * per <= 128 ? 128 : 256;
   size_t sm = (size_t)EB * (staged ? per_bytes : small_bytes) + 64;
   int64_t blocks = (m.ne + EB - 1) / EB;
@@ -2092,6 +2094,11 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
     while (FB > 1 && facet_step_smem<R>(s, FB, update) > 96 * 1024) --FB;
     threads = 256;
   }
+  const bool tuned = P.fb > 0 && P.fthreads > 0 && facet_step_smem<R>(s, P.fb, update) <= 160 * 1024;
+  if (tuned) {
+    FB = P.fb;
+    threads = P.fthreads;
+  }
   const size_t sm = facet_step_smem<R>(s, FB, update);
   const int64_t nb = (n + FB - 1) / FB;
   const int4* rec = m.frec + first * 4;
@@ -2109,7 +2116,14 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
       else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step<R, SZ, false>, threads, sm);
       per_sm[ui].store(occ > 0 ? occ : 1, std::memory_order_release);
     }
-    int64_t blocks = (int64_t)sm_count() * per_sm[ui].load(std::memory_order_acquire);
+    int occ_now = per_sm[ui].load(std::memory_order_acquire);
+    if (tuned) {   // the cached occupancy belongs to the formula's shape
+      occ_now = 0;
+      if (update) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_now, k_facet_step<R, SZ, true>, threads, sm);
+      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_now, k_facet_step<R, SZ, false>, threads, sm);
+      if (occ_now < 1) occ_now = 1;
+    }
+    int64_t blocks = (int64_t)sm_count() * occ_now;
     if (blocks > nb) blocks = nb;
     const int cls = update ? PROF_FACET_GS : PROF_FACET_RES;
     prof_begin(cls, st);
@@ -2258,6 +2272,74 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
         facet_step<R>(s, m, L, P, b, tb, x, nullptr, co[c], co[c + 1] - co[c], true, stop, st);
 }
 
+template <class R>
+cudaError_t autotune_launches(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, PrecData<R>& P,
+                              KOp& K, double* v1, double* v2, cudaStream_t st, char* report, int report_len) {
+  const Layout PL = precond_layout(L, s, sizeof(R));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_ms = [&](auto&& fn) {
+    fn();   // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) fn();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / 3.0f;
+  };
+  int pos = 0;
+  auto rep = [&](const char* fmt, int a, int b, float ms) {
+    if (report && pos < report_len - 64) pos += snprintf(report + pos, report_len - pos, fmt, a, b, ms);
+  };
+  // facet step candidates: only where the batched block kernel runs (2D; facet stream under 4 KB)
+  const bool block_kernel = !((size_t)fs_stride(s) * sizeof(R) >= 4096 && 2 * s.mF <= 32) &&
+                            facet_step_smem<R>(s, 1, true) <= 200 * 1024 && PL.nint > 0;
+  if (block_kernel) {
+    const int64_t n0 = P.colour_off[1] - P.colour_off[0];
+    float best = 1e30f;
+    int bfb = -1, bth = -1;
+    const int fbs[] = {2, 3, 4, 6, 9, 12, 16, 24};
+    for (int th : {128, 256})
+      for (int fb : fbs) {
+        if (2 * s.mF * fb > 2 * th || facet_step_smem<R>(s, fb, true) > 160 * 1024) continue;
+        P.fb = fb;
+        P.fthreads = th;
+        const float ms = time_ms([&] { facet_step<R>(s, m, PL, P, P.b, P.t, P.x, nullptr, 0, n0, true, nullptr, st); });
+        rep("facet FB=%d threads=%d %.4f ms; ", fb, th, ms);
+        if (ms < best) { best = ms; bfb = fb; bth = th; }
+      }
+    P.fb = bfb;
+    P.fthreads = bth;
+  }
+  // staged K apply candidates
+  {
+    const int per = s.n_A + s.n_p;
+    const size_t per_bytes = K.Ahi ? (2 * (size_t)packed_pad(s) + 2 * per) * sizeof(float) + 32
+                                   : (size_t)s.n_A * s.n_A * sizeof(double) + (size_t)per * 8 + 32;
+    if (per_bytes <= 160 * 1024) {
+      float best = 1e30f;
+      int beb = -1;
+      for (int eb : {1, 2, 3, 4, 5, 6, 8, 12}) {
+        if ((size_t)eb * per_bytes > 160 * 1024 || eb * per > 1024) continue;
+        K.eb = eb;
+        const float ms = time_ms([&] { launch_apply_K(s, t, m, L, K, v1, v2, nullptr, st); });
+        rep("apply EB=%d (%d) %.4f ms; ", eb, 0, ms);
+        if (ms < best) { best = ms; beb = eb; }
+      }
+      K.eb = beb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return cudaGetLastError();
+}
+template cudaError_t autotune_launches<float>(const ElemSizes&, const DevTables&, const DevMesh&, const Layout&,
+                                              PrecData<float>&, KOp&, double*, double*, cudaStream_t, char*, int);
+template cudaError_t autotune_launches<double>(const ElemSizes&, const DevTables&, const DevMesh&, const Layout&,
+                                               PrecData<double>&, KOp&, double*, double*, cudaStream_t, char*, int);
+
 // z = Khat^{-1} r (eq. mhatinvfactor, two applications of Ahat^{-1}, reading R3).
 template <class R>
 cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
@@ -2289,14 +2371,22 @@ cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh
 }
 
 // ============================================================================ Krylov helpers
+// DIFF = false: a.b; DIFF = true: |a - b|^2 (the same fixed reduction order)
+template <bool DIFF>
 __global__ void k_dot(const double* a, const double* b, int64_t n, double* part, double* out, const int* stop,
                       unsigned int* counter) {
   if (stop && *stop) return;
   __shared__ double red[32];
   __shared__ bool last;
   double v = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v += a[i] * b[i];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (DIFF) {
+      const double e = a[i] - b[i];
+      v += e * e;
+    } else {
+      v += a[i] * b[i];
+    }
+  }
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
@@ -2334,7 +2424,16 @@ cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* scra
                        cudaStream_t st) {
   int blocks = sm_count() * 4;
   if (blocks > 1024) blocks = 1024;
-  k_dot<<<blocks, 256, 0, st>>>(a, b, n, scratch, out, stop, (unsigned int*)(scratch + 1024));
+  k_dot<false><<<blocks, 256, 0, st>>>(a, b, n, scratch, out, stop, (unsigned int*)(scratch + 1024));
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diff_sq(const double* a, const double* b, int64_t n, double* scratch, double* out,
+                           cudaStream_t st) {
+  int blocks = sm_count() * 4;
+  if (blocks > 1024) blocks = 1024;
+  k_dot<true><<<blocks, 256, 0, st>>>(a, b, n, scratch, out, nullptr, (unsigned int*)(scratch + 1024));
   note_launch();
   return cudaGetLastError();
 }

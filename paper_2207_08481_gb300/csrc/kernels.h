@@ -144,6 +144,7 @@ struct KOp {
   double* AT;
   float* Ahi;
   float* Alo;
+  int eb = -1;   // elements per block of the staged K apply (-1: the shared-memory formula; autotuner)
 };
 template <class S> __host__ __device__ inline int packed_pad(const S& s) { return pad4(s.n_A * (s.n_A + 1) / 2); }
 
@@ -239,6 +240,7 @@ struct PrecData {
   // work vectors (R), all length ndof unless noted
   R *b, *x, *t, *rr, *zz;
   int* err;  // device flag: set when a bounded wait on an asynchronous copy gave up
+  int fb = -1, fthreads = -1;   // batched facet step: facets per batch and threads (-1: formulas; autotuner)
   // diagnostics (environment MCS_DEBUG_CHECKS=1 at set-up): the facet step checks every address
   // against its buffer and records the first bad one in dbg[0..3] instead of accessing it, and
   // the host synchronises after every preconditioner launch and names a kernel that failed
@@ -247,6 +249,15 @@ struct PrecData {
   R *pb[12], *px[12], *pr[12], *ptmp[12];  // GMG vectors per level
   double* coarse_tmp;  // [n0]
 };
+
+// Autotuner: times the candidate launch shapes of the batched facet step (the 2D blocks; 3D uses the
+// warp-per-facet kernel, which has none) over the first colour and of the staged K apply on the handle's
+// own data, and stores the fastest in P.fb / P.fthreads and K.eb.  Uses the preconditioner work vectors
+// and two Krylov vectors as scratch (contents do not matter).  times: the measured ms per candidate
+// (host, for the record).  Synchronous on st.
+template <class R>
+cudaError_t autotune_launches(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, PrecData<R>& P,
+                              KOp& K, double* v1, double* v2, cudaStream_t st, char* report, int report_len);
 
 template <class R>
 cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,
@@ -257,6 +268,9 @@ cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh
 // scratch: >= 2100 doubles (partials, counters) per stream.
 cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* scratch, double* out, const int* stop,
                        cudaStream_t st);
+// out[0] = |a - b|^2, same fixed reduction order as launch_dot (scratch as there)
+cudaError_t launch_diff_sq(const double* a, const double* b, int64_t n, double* scratch, double* out,
+                           cudaStream_t st);
 // remove the mean of p_h: p_{T,0} -= (sum adet_T p_{T,0}) / (sum adet_T)
 cudaError_t launch_mean_zero(const DevMesh& m, const Layout& L, int n_p, double* x, double* scratch,
                              double total_adet, const int* stop, cudaStream_t st);

@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("gmg_smooth", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("residual_dd", ctypes.c_int), ("asp", ctypes.c_int), ("lo_stab", ctypes.c_int),
-                ("outflow", ctypes.c_int), ("etol", ctypes.c_double)]
+                ("outflow", ctypes.c_int), ("etol", ctypes.c_double), ("tune", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class Sizes(ctypes.Structure):
@@ -46,7 +47,8 @@ class Sizes(ctypes.Structure):
                                                "ne", "nint", "nfacets", "nvertices", "np1")] + \
                [(n, ctypes.c_int32) for n in ("dim", "k", "nF", "n_bub", "nhF", "n_p", "n_A", "n_c", "mF",
                                                "ncolours", "gmg_levels", "nq_load")] + \
-               [("bytes_resident", ctypes.c_int64)]
+               [("bytes_resident", ctypes.c_int64)] + \
+               [(n, ctypes.c_int32) for n in ("facet_batch", "facet_threads", "apply_batch")]
 
 
 class SolveInfo(ctypes.Structure):
@@ -132,7 +134,7 @@ def default_options(**kw) -> Options:
     o = Options()
     lib().mcs_default_options(ctypes.byref(o))
     for k, v in kw.items():
-        setattr(o, k, v)
+        setattr(o, k, v.encode() if isinstance(v, str) else v)
     return o
 
 
@@ -217,6 +219,10 @@ class Handle:
     # ---------------------------------------------------------------- compute
     def condense(self):
         _check(lib().mcs_condense(self._h))
+        # the launch shapes in use can change at the first condensation (tune = 1)
+        s = Sizes()
+        _check(lib().mcs_sizes(self._h, ctypes.byref(s)))
+        self.sizes = s
 
     def element_matrices(self, T0, count):
         nA = self.sizes.n_A

@@ -55,8 +55,15 @@ def test_invalid_arguments_are_reported_not_raised(lib):
     assert L.mcs_setup_structured(2, 8, 2, -1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
     assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(o), None, None) == lib.MCS_ERR_INVALID_ARG
     assert b"NULL" in L.mcs_last_error()
-    assert L.mcs_setup_structured(3, 4, 5, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
-    assert L.mcs_setup_structured(2, 4, 6, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
+    assert L.mcs_setup_structured(3, 4, 7, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
+    assert L.mcs_setup_structured(2, 4, 0, 1.0, ctypes.byref(o), None, ctypes.byref(h)) == lib.MCS_ERR_UNSUPPORTED
+    bad = lib.default_options(etol=-1.0)
+    assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
+    assert b"etol" in L.mcs_last_error()
+    bad = lib.default_options(tune=2)
+    assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
+    assert b"tune" in L.mcs_last_error()
+    assert lib.default_options().etol == 0.0 and lib.default_options().tune == 0
     bad = lib.default_options(residual_dd=3)
     assert L.mcs_setup_structured(2, 8, 2, 1.0, ctypes.byref(bad), None, ctypes.byref(h)) == lib.MCS_ERR_INVALID_ARG
     assert b"residual_dd" in L.mcs_last_error()
