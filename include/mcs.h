@@ -121,6 +121,13 @@ typedef struct {
                          shared-memory formulas */
   const char* tune_cache;  /* tune = 1: optional path of a text file of tuned shapes, one line per
                          (dim, k, precision, element count); read before tuning, appended after (NULL: none) */
+  int facet_push;     /* multiplicative ASP: 1 (default) runs the facet sweeps before the coarse correction
+                         with a maintained residual where the warp-per-facet smoother applies (facet blocks of
+                         at least 4 KB with 2 m_F <= 32: 3D k = 2 and 2D k = 6 in both forms, 2D k = 4, 5 in
+                         the FP64 form; mcs_sizes_t.push_warps > 0 when it is in use), so that
+                         the residual for E^d^T needs no pass of its own; 0: row products and a residual
+                         pass.  Both compute the same block Gauss-Seidel sweep (Corollary aux_pc_mult) and
+                         differ only in rounding. */
 } mcs_options;
 
 typedef struct {
@@ -133,6 +140,8 @@ typedef struct {
   int32_t nq_load;                          /* load quadrature points per element */
   int64_t bytes_resident;                   /* device bytes held by the handle */
   int32_t facet_batch, facet_threads, apply_batch;   /* launch shapes in use (-1: formulas; see tune) */
+  int32_t push_warps;                       /* warps per block of the maintained-residual forward sweep
+                                               (0: not in use; see facet_push) */
 } mcs_sizes_t;
 
 typedef struct {

@@ -72,6 +72,7 @@ void validate_options(const mcs_options& o) {
   if (!(o.etol >= 0)) throw McsError(MCS_ERR_INVALID_ARG, "etol");
   if (o.etol > 0 && !(o.inner_rtol > 0 && o.inner_rtol < 1)) throw McsError(MCS_ERR_INVALID_ARG, "inner_rtol");
   if (o.tune < 0 || o.tune > 1) throw McsError(MCS_ERR_INVALID_ARG, "tune");
+  if (o.facet_push < 0 || o.facet_push > 1) throw McsError(MCS_ERR_INVALID_ARG, "facet_push");
 }
 
 template <class R>
@@ -198,6 +199,12 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   P.t = h->dalloc<R>(n);
   P.rr = h->dalloc<R>(n);
   P.zz = h->dalloc<R>(n);
+  P.push_warps = (h->opt.facet_push == 1 && P.multiplicative) ? facet_push_warps<R>(h->es) : 0;
+  if (P.push_warps > 0) {
+    const int64_t ndd = nint * (int64_t)facet_stride(h->es, (int)sizeof(R));
+    P.q0 = h->dalloc<R>(ndd);
+    P.q1 = h->dalloc<R>(ndd);
+  }
   P.coarse_tmp = nullptr;
   P.err = h->dalloc<int>(1);
   cuda_check(cudaMemset(P.err, 0, sizeof(int)), "memset");
@@ -329,6 +336,17 @@ void finish_setup(mcs_handle* h, std::vector<HostMesh>& levels) {
       o[4] = floc[r * 2 + 1];
       for (int side = 0; side < 2; ++side)
         for (int f = 0; f <= d; ++f) o[5 + side * (d + 1) + f] = fsr[(r * 2 + side) * (d + 1) + f];
+      // [13]: bit side*(d+1) + f set when element o[1 + side] is side 1 of the facet o[5 + side*(d+1) + f]
+      int32_t bits = 0;
+      for (int side = 0; side < 2; ++side)
+        for (int f = 0; f <= d; ++f) {
+          const int32_t H = o[5 + side * (d + 1) + f], T = o[1 + side];
+          if (H < 0 || T < 0) continue;
+          if (fel[H * 2] == T) continue;
+          if (fel[H * 2 + 1] != T) throw McsError(MCS_ERR_INVALID_ARG, "inconsistent facet-element incidence");
+          bits |= 1 << (side * (d + 1) + f);
+        }
+      o[13] = bits;
     }
     dm.frec = reinterpret_cast<const int4*>(h->upload(rec));
   }
@@ -560,6 +578,7 @@ int mcs_default_options(mcs_options* o) {
   o->etol = 0.0;
   o->tune = 0;
   o->tune_cache = nullptr;
+  o->facet_push = 1;
   return MCS_OK;
 }
 
@@ -644,6 +663,7 @@ int mcs_sizes(const mcs_handle* h, mcs_sizes_t* s) {
     s->facet_batch = h->opt.precision == MCS_MIXED ? h->pf.fb : h->pd.fb;
     s->facet_threads = h->opt.precision == MCS_MIXED ? h->pf.fthreads : h->pd.fthreads;
     s->apply_batch = h->K.eb;
+    s->push_warps = h->opt.precision == MCS_MIXED ? h->pf.push_warps : h->pd.push_warps;
     return MCS_OK;
   });
 }

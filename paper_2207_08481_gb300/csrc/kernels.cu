@@ -1863,17 +1863,18 @@ __global__ void __launch_bounds__(256) k_facet_step_warp(S s, Layout L, const R*
   };
   // the shuffles in issue() need every lane, so all lanes run the loop the same number of times
   int st = 0;
-  int rec_next = (f0 < n && lane < 16) ? rec[f0 * 16 + lane] : -1;
-  if (f0 < n) issue(0, f0, rec_next);
+  // records two facets ahead: the load of the next-but-one record overlaps this facet's work
+  int rec_a = (f0 < n && lane < 16) ? rec[f0 * 16 + lane] : -1;            // facet f
+  int rec_b = (f0 + W < n && lane < 16) ? rec[(f0 + W) * 16 + lane] : -1;  // facet f + W
+  if (f0 < n) issue(0, f0, rec_a);
   cp_async_commit();
   for (int64_t f = f0; f < n; f += W) {
-    const int rec_cur = rec_next;
+    const int rec_cur = rec_a;
     const int64_t fn = f + W;
-    if (fn < n) {
-      rec_next = lane < 16 ? rec[fn * 16 + lane] : -1;
-      issue(st ^ 1, fn, rec_next);
-    }
+    if (fn < n) issue(st ^ 1, fn, rec_b);
     cp_async_commit();
+    rec_a = rec_b;
+    rec_b = (fn + W < n && lane < 16) ? rec[(fn + W) * 16 + lane] : -1;
     cp_async_wait_group<1>();
     // bounded wait for the stream block (about a second): on expiry the error flag is set, the
     // other stage's copy is waited for (bounded too) and the warp stops
@@ -1998,6 +1999,286 @@ __global__ void __launch_bounds__(256) k_facet_step_direct(S s, Layout L, const 
   }
 }
 
+// Forward colour sweep with a maintained residual (the sweeps of the multiplicative ASP before the
+// coarse correction, which start from x = 0).  Besides x the sweep keeps, per interior facet H and side
+// s, a partial residual q_s[H]: q_0 starts as b - tb and q_1 as 0, and every block update subtracts
+// A^d_T[H, F] delta_F from the slot of H's element T, so that r_F = q_0[F] + q_1[F] equals
+// b_F - tb_F - sum_{T ni F} A^d_T[F, :] x_T at every step.  After the block solve delta = D_F^{-1} r_F
+// the facet pushes -A^d_T[H, F] delta = -(A^d_T[F, H])^T delta into the slot of every facet H of both
+// its elements; A^d_T[F, H] are the columns of its own slabs, already in shared memory, so the sweep
+// reads the same stream as the row-product form and forms no row products.  Facets of one colour share
+// no element, so each (H, side) slot has one writer per launch and is read by no other facet of the
+// launch.  After the last forward colour q_0 + q_1 is the residual, which the coarse correction needs.
+// Record field [13]: bit side*(d+1) + f set when element rec[1 + side] is side 1 of the facet
+// H = rec[5 + side*(d+1) + f].  One warp per facet as in k_facet_step_warp, with a two-stage pipeline:
+// the stream block by one bulk copy on an mbarrier (bounded wait), the q segments of the 2(d+1) facets of
+// both elements and x_F by cp.async; the records are loaded two facets ahead.  xin = nullptr: x = 0
+// before the launch (the first sweep).
+template <class S, class R>
+__host__ __device__ inline int push_stage_elems(const S& s) {
+  const int fs = facet_stride(s, (int)sizeof(R));
+  return fs_stride(s) + 2 * (s.d + 1) * fs + fs;
+}
+template <class R, class S>
+__global__ void __launch_bounds__(256) k_facet_push_warp(S s, const R* __restrict__ Fs, const R* xin, R* x, R* q0,
+                                                         R* q1, const int* __restrict__ rec, int64_t n,
+                                                         const int* stop, int* err) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(16) unsigned char swq[];
+  const int mF = s.mF, dp1 = s.d + 1, slab = slab_pad(s), fss = fs_stride(s), nc = s.n_c;
+  const int fs = facet_stride(s, (int)sizeof(R));
+  const int se = push_stage_elems<S, R>(s);
+  const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // per warp: two stages and a scratch of 32 entries (r_F, then delta), then all warps' mbarriers
+  R* wbase = reinterpret_cast<R*>(swq) + (size_t)wib * (2 * se + 32);
+  R* Rs = wbase + 2 * se;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<R*>(swq) + (size_t)nw * (2 * se + 32)) + 2 * wib;
+  const unsigned sbytes = (unsigned)(fss * (int)sizeof(R));
+  if (lane == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 1, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  unsigned phases = 0u;   // bit st: parity of the next phase of stage st's mbarrier
+  constexpr int V = 16 / (int)sizeof(R);
+  const int cx = fs / V;
+  const int nseg = 2 * dp1;
+  const int64_t W = (int64_t)gridDim.x * nw;
+  const int64_t f0 = (int64_t)blockIdx.x * nw + wib;
+  const uint64_t pol = l2_evict_first_policy();
+  const bool vec = ((mF * (int)sizeof(R)) & 15) == 0;   // slab columns and D_F^{-1} rows on 16-byte boundaries
+  // the lane's slab columns c = 32u + lane (2 n_c <= 128): offset in the stage, segment, mode
+  int c_off[4], c_seg[4], c_tp[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = 32 * u + lane;
+    const bool act = c < 2 * nc;
+    const int side = (act && c >= nc) ? 1 : 0;
+    const int cc = act ? c - side * nc : 0;
+    const int fl = cc / mF;
+    c_off[u] = side * slab + cc * mF;
+    c_seg[u] = act ? side * dp1 + fl : -1;
+    c_tp[u] = cc - fl * mF;
+  }
+  // sum_{t < mF} a[t] b[t] in the order t = 0, 1, ... (b a register array when REG)
+  auto dot_m = [&](const R* a, const R* bv) -> R {
+    R acc = 0;
+    if (vec) {
+#pragma unroll
+      for (int t0 = 0; t0 < 16; t0 += V) {
+        if (t0 < mF) {
+          if constexpr (sizeof(R) == 4) {
+            const float4 A = *reinterpret_cast<const float4*>(a + t0);
+            const float4 B = *reinterpret_cast<const float4*>(bv + t0);
+            acc += A.x * B.x;
+            acc += A.y * B.y;
+            acc += A.z * B.z;
+            acc += A.w * B.w;
+          } else {
+            const double2 A = *reinterpret_cast<const double2*>(a + t0);
+            const double2 B = *reinterpret_cast<const double2*>(bv + t0);
+            acc += A.x * B.x;
+            acc += A.y * B.y;
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 16; ++t)
+        if (t < mF) acc += a[t] * bv[t];
+    }
+    return acc;
+  };
+
+  // stage: [stream block | q segments of the 2(d+1) facets of both elements | x_F]
+  auto issue = [&](int st, int64_t f, int myrec) {
+    R* Sb = wbase + st * se;
+    R* Qs = Sb + fss;
+    R* Xs = Qs + nseg * fs;
+    int gseg[8];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) gseg[k2] = __shfl_sync(0xffffffffu, myrec, 5 + k2);
+    const int bits = __shfl_sync(0xffffffffu, myrec, 13);
+    const int r = __shfl_sync(0xffffffffu, myrec, 0);
+    if (lane == 0) {
+      mbar_expect_tx(bars + st, sbytes);
+      bulk_copy_g2s(Sb, Fs + f * fss, sbytes, bars + st, pol);
+    }
+    for (int q = lane; q < nseg * cx; q += 32) {
+      const int seg = q / cx, ch = q - seg * cx;   // seg = side*dp1 + local facet
+      const int g = gseg[seg];
+      R* dst = Qs + seg * fs + ch * V;
+      if (g >= 0) cp_async16(dst, (((bits >> seg) & 1) ? q1 : q0) + (int64_t)g * fs + ch * V);
+      else *reinterpret_cast<int4*>(dst) = make_int4(0, 0, 0, 0);
+    }
+    for (int q = lane; q < cx; q += 32) {
+      R* dst = Xs + q * V;
+      if (xin && r >= 0) cp_async16(dst, xin + (int64_t)r * fs + q * V);
+      else *reinterpret_cast<int4*>(dst) = make_int4(0, 0, 0, 0);
+    }
+  };
+  int st = 0;
+  int rec_a = (f0 < n && lane < 16) ? rec[f0 * 16 + lane] : -1;            // facet f
+  int rec_b = (f0 + W < n && lane < 16) ? rec[(f0 + W) * 16 + lane] : -1;  // facet f + W
+  if (f0 < n) issue(0, f0, rec_a);
+  cp_async_commit();
+  for (int64_t f = f0; f < n; f += W) {
+    const int rec_cur = rec_a;
+    const int64_t fn = f + W;
+    if (fn < n) issue(st ^ 1, fn, rec_b);
+    cp_async_commit();
+    rec_a = rec_b;
+    rec_b = (fn + W < n && lane < 16) ? rec[(fn + W) * 16 + lane] : -1;
+    cp_async_wait_group<1>();
+    bool got = true;
+    if (lane == 0) got = mbar_wait_bounded(bars + st, (phases >> st) & 1u, 1000000000ull);
+    got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+    if (!got) {
+      if (lane == 0) {
+        atomicExch(err, 1);
+        if (fn < n) mbar_wait_bounded(bars + (st ^ 1), (phases >> (st ^ 1)) & 1u, 1000000000ull);
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      return;
+    }
+    __syncwarp();
+    phases ^= 1u << st;
+    const R* Sb = wbase + st * se;
+    const R* Qs = Sb + fss;
+    const R* Xs = Qs + nseg * fs;
+    const int r = __shfl_sync(0xffffffffu, rec_cur, 0);
+    const int fl0 = __shfl_sync(0xffffffffu, rec_cur, 3);
+    const int fl1 = __shfl_sync(0xffffffffu, rec_cur, 4);
+    const int bits = __shfl_sync(0xffffffffu, rec_cur, 13);
+    // r_F on lanes t < mF (the facet's own q slots are the segments of its local facets in both
+    // elements) into the scratch, then delta = D_F^{-1} r_F (row t on lane t) into the scratch
+    if (lane < mF) {
+      R rv = Qs[fl0 * fs + lane];
+      if (fl1 >= 0) rv += Qs[(dp1 + fl1) * fs + lane];
+      Rs[lane] = rv;
+    }
+    __syncwarp();
+    if (lane < mF) {
+      const R v = dot_m(Sb + 2 * slab + lane * mF, Rs);
+      Rs[16 + lane] = v;
+      if (r >= 0) x[(int64_t)r * fs + lane] = Xs[lane] + v;
+    }
+    __syncwarp();
+    R dl[16];   // delta on every lane (m_F <= 16)
+#pragma unroll
+    for (int t = 0; t < 16; ++t) dl[t] = t < mF ? Rs[16 + t] : (R)0;
+    // push: the lane's columns of the slabs against delta
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int seg = c_seg[u] < 0 ? 0 : c_seg[u];
+      const int H = __shfl_sync(0xffffffffu, rec_cur, 5 + seg);
+      if (c_seg[u] < 0 || H < 0) continue;
+      const R* col = Sb + c_off[u];
+      R val = 0;
+      if (vec) {
+#pragma unroll
+        for (int t0 = 0; t0 < 16; t0 += V) {
+          if (t0 < mF) {
+            if constexpr (sizeof(R) == 4) {
+              const float4 a = *reinterpret_cast<const float4*>(col + t0);
+              val += a.x * dl[t0];
+              val += a.y * dl[t0 + 1];
+              val += a.z * dl[t0 + 2];
+              val += a.w * dl[t0 + 3];
+            } else {
+              const double2 a = *reinterpret_cast<const double2*>(col + t0);
+              val += a.x * dl[t0];
+              val += a.y * dl[t0 + 1];
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (t < mF) val += col[t] * dl[t];
+      }
+      R* qd = ((bits >> seg) & 1) ? q1 : q0;
+      qd[(int64_t)H * fs + c_tp[u]] = Qs[seg * fs + c_tp[u]] - val;
+    }
+    __syncwarp();
+    st ^= 1;
+  }
+  cp_async_wait_all();
+}
+
+// q_0 = b - tb, q_1 = 0 (entries of all facet slots): the partial residuals before a forward sweep from
+// x = 0.  With COMBINE: rr = q_0 + q_1 on the modes t < m_F, the residual after the sweep.
+template <class R, bool COMBINE>
+__global__ void k_push_vectors(int64_t nint, int fs, int mF, const R* __restrict__ b, const R* __restrict__ tb,
+                               R* q0, R* q1, R* rr, const int* stop) {
+  if (stop && *stop) return;
+  const int64_t total = nint * fs;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (COMBINE) {
+      if ((int)(i % fs) < mF) rr[i] = q0[i] + q1[i];
+    } else {
+      q0[i] = b[i] - (tb ? tb[i] : (R)0);
+      q1[i] = (R)0;
+    }
+  }
+}
+
+template <class R>
+int facet_push_warps(const ElemSizes& s) {
+  if (2 * s.mF > 32) return 0;
+  if ((size_t)fs_stride(s) * sizeof(R) < 4096) return 0;   // small blocks: the batched row-product kernel
+  for (int nw = 8; nw >= 2; nw /= 2)
+    if ((size_t)nw * (2 * push_stage_elems<ElemSizes, R>(s) + 32) * sizeof(R) + (size_t)nw * 2 * sizeof(uint64_t) <=
+        100 * 1024)
+      return nw;
+  return 0;
+}
+template int facet_push_warps<float>(const ElemSizes&);
+template int facet_push_warps<double>(const ElemSizes&);
+
+template <class R>
+static cudaError_t facet_push(const ElemSizes& s, const DevMesh& m, const Layout& L, PrecData<R>& P, const R* xin,
+                              R* x, int64_t first, int64_t n, const int* stop, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  if (L.fstride != facet_stride(s, (int)sizeof(R)) || P.push_warps <= 0 || !P.q0 || !P.q1)
+    return cudaErrorInvalidValue;
+  const int nw = P.push_warps;
+  const size_t wsm =
+      (size_t)nw * (2 * push_stage_elems<ElemSizes, R>(s) + 32) * sizeof(R) + (size_t)nw * 2 * sizeof(uint64_t);
+  const int* ri = reinterpret_cast<const int*>(m.frec + first * 4);
+  const R* fs0 = P.Fs + first * (int64_t)fs_stride(s);
+  dispatch_sizes(s, [&](auto sz) {
+    using SZ = decltype(sz);
+    // occupancy cached per shared-memory size (the run-time-size instantiation serves several (d, k))
+    static std::atomic<int64_t> cached{0};   // (wsm << 8) | blocks per SM
+    int64_t c = cached.load(std::memory_order_acquire);
+    if ((c >> 8) != (int64_t)wsm) {
+      cudaFuncSetAttribute(k_facet_push_warp<R, SZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_push_warp<R, SZ>, nw * 32, wsm);
+      c = ((int64_t)wsm << 8) | (int64_t)(occ > 0 ? (occ < 255 ? occ : 255) : 1);
+      cached.store(c, std::memory_order_release);
+    }
+    int64_t blocks = (int64_t)sm_count() * (c & 255);
+    const int64_t need = (n + nw - 1) / nw;
+    if (blocks > need) blocks = need;
+    prof_begin(PROF_FACET_GS, st);
+    note_launch();
+    k_facet_push_warp<R, SZ><<<(unsigned)blocks, nw * 32, wsm, st>>>(sz, fs0, xin, x, P.q0, P.q1, ri, n, stop,
+                                                                      P.err);
+    // algorithmic bytes per facet as for the row-product update (the stream block, b, tb, x_F read and
+    // written; here q_0, q_1 of the facet stand for b, tb); the q segments of the neighbours, like the
+    // gathered x there, are L2-resident vectors
+    const double per = 2.0 * s.mF * s.n_c + (double)s.mF * s.mF + 4.0 * s.mF;
+    prof_end(PROF_FACET_GS, (double)n * per * sizeof(R), 2.0 * (double)n * (2.0 * s.mF * s.n_c + s.mF * s.mF), st);
+  });
+  dbg_sync(P, st, "k_facet_push_warp");
+  return cudaGetLastError();
+}
+
 template <class R>
 static size_t facet_step_smem(const ElemSizes& s, int FB, bool update) {
   (void)update;
@@ -2018,37 +2299,53 @@ static cudaError_t facet_step(const ElemSizes& s, const DevMesh& m, const Layout
   {
     // warp-per-facet kernel for large facet blocks (at least 4 KB of stream per facet: 3D; measured
     // faster there, slower than the batched block kernel for the 1.4 KB blocks of 2D k = 3), when the
-    // 2 m_F rows fit a warp and 8 warps' stages fit in 100 KB
-    const size_t wsm = (size_t)8 * 2 * warp_stage_elems<ElemSizes, R>(s) * sizeof(R) + 8 * 2 * sizeof(uint64_t);
-    if ((size_t)fs_stride(s) * sizeof(R) >= 4096 && 2 * s.mF <= 32 && wsm <= 100 * 1024) {
+    // 2 m_F rows fit a warp and the stages of 8 (else 4) warps fit in 100 KB
+    int nwarp = 0;
+    size_t wsm = 0;
+    if ((size_t)fs_stride(s) * sizeof(R) >= 4096 && 2 * s.mF <= 32) {
+      for (int w = 8; w >= 4; w /= 2) {
+        const size_t b_ = (size_t)w * 2 * warp_stage_elems<ElemSizes, R>(s) * sizeof(R) + (size_t)w * 2 * sizeof(uint64_t);
+        if (b_ <= 100 * 1024) {
+          nwarp = w;
+          wsm = b_;
+          break;
+        }
+      }
+    }
+    if (nwarp > 0) {
       bool done = false;
       dispatch_sizes(s, [&](auto sz) {
         using SZ = decltype(sz);
-        static std::atomic<int> per_sm_w[2];
+        // occupancy cached per (update, shared-memory size)
+        static std::atomic<int64_t> cached[2];   // (wsm << 8) | blocks per SM
         const int ui = update ? 1 : 0;
-        if (!per_sm_w[ui].load(std::memory_order_acquire)) {
+        int64_t c = cached[ui].load(std::memory_order_acquire);
+        if ((c >> 8) != (int64_t)wsm) {
           cudaFuncSetAttribute(k_facet_step_warp<R, SZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                200 * 1024);
           cudaFuncSetAttribute(k_facet_step_warp<R, SZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                200 * 1024);
           int occ = 0;
-          if (update) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step_warp<R, SZ, true>, 256, wsm);
-          else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step_warp<R, SZ, false>, 256, wsm);
-          per_sm_w[ui].store(occ > 0 ? occ : 1, std::memory_order_release);
+          if (update)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step_warp<R, SZ, true>, nwarp * 32, wsm);
+          else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_facet_step_warp<R, SZ, false>, nwarp * 32, wsm);
+          c = ((int64_t)wsm << 8) | (int64_t)(occ > 0 ? (occ < 255 ? occ : 255) : 1);
+          cached[ui].store(c, std::memory_order_release);
         }
-        int64_t blocks = (int64_t)sm_count() * per_sm_w[ui].load(std::memory_order_acquire);
-        const int64_t need = (n + 7) / 8;
+        int64_t blocks = (int64_t)sm_count() * (c & 255);
+        const int64_t need = (n + nwarp - 1) / nwarp;
         if (blocks > need) blocks = need;
         const int cls = update ? PROF_FACET_GS : PROF_FACET_RES;
         prof_begin(cls, st);
         note_launch();
         const int* ri = reinterpret_cast<const int*>(rec0);
         if (update)
-          k_facet_step_warp<R, SZ, true><<<(unsigned)blocks, 256, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n, stop,
-                                                                               P.err);
+          k_facet_step_warp<R, SZ, true><<<(unsigned)blocks, nwarp * 32, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n,
+                                                                                      stop, P.err);
         else
-          k_facet_step_warp<R, SZ, false><<<(unsigned)blocks, 256, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n, stop,
-                                                                                P.err);
+          k_facet_step_warp<R, SZ, false><<<(unsigned)blocks, nwarp * 32, wsm, st>>>(sz, L, fs0, b, tb, x, rr, ri, n,
+                                                                                       stop, P.err);
         const double per = update ? (2.0 * s.mF * s.n_c + (double)s.mF * s.mF + 4.0 * s.mF)
                                   : (2.0 * s.mF * s.n_c + 3.0 * s.mF);
         prof_end(cls, (double)n * per * sizeof(R),
@@ -2238,7 +2535,24 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   cudaMemsetAsync(x, 0, sizeof(R) * L.n_dd, st);
   if (L.n_hat) cudaMemsetAsync(x + L.off_h, 0, sizeof(R) * L.n_hat, st);
   const int64_t* co = P.colour_off;
-  if (P.multiplicative) {
+  if (P.multiplicative && P.push_warps > 0 && P.q0 && P.q1) {
+    // forward sweeps with the maintained residual (from x = 0: q_0 = b - tb, q_1 = 0), then rr = q_0 + q_1
+    if (L.nint > 0) {
+      k_push_vectors<R, false><<<g, bs, 0, st>>>(L.nint, L.fstride, s.mF, b, tb, P.q0, P.q1, nullptr, stop);
+      note_launch();
+      dbg_sync(P, st, "k_push_vectors");
+    }
+    for (int sw = 0; sw < P.smooth; ++sw)
+      for (int c = 0; c < P.ncol; ++c)
+        facet_push<R>(s, m, L, P, sw == 0 ? nullptr : x, x, co[c], co[c + 1] - co[c], stop, st);   // sweep 0: x_F = 0
+    if (L.nint > 0) {
+      prof_begin(PROF_FACET_RES, st);
+      k_push_vectors<R, true><<<g, bs, 0, st>>>(L.nint, L.fstride, s.mF, nullptr, nullptr, P.q0, P.q1, P.rr, stop);
+      note_launch();
+      prof_end(PROF_FACET_RES, (double)L.nint * s.mF * 3.0 * sizeof(R), (double)L.nint * s.mF, st);
+      dbg_sync(P, st, "k_push_vectors");
+    }
+  } else if (P.multiplicative) {
     for (int sw = 0; sw < P.smooth; ++sw)
       for (int c = 0; c < P.ncol; ++c)
         facet_step<R>(s, m, L, P, b, tb, x, nullptr, co[c], co[c + 1] - co[c], true, stop, st);

@@ -239,6 +239,10 @@ struct PrecData {
   const double* coarse_inv;    // [n0][n0] FP64
   // work vectors (R), all length ndof unless noted
   R *b, *x, *t, *rr, *zz;
+  // forward sweeps with a maintained residual (push_warps > 0: warps per block of k_facet_push_warp;
+  // 0: row products and a residual pass): the partial residuals of each facet's two elements, [n_dd] each
+  int push_warps = 0;
+  R *q0 = nullptr, *q1 = nullptr;
   int* err;  // device flag: set when a bounded wait on an asynchronous copy gave up
   int fb = -1, fthreads = -1;   // batched facet step: facets per batch and threads (-1: formulas; autotuner)
   // diagnostics (environment MCS_DEBUG_CHECKS=1 at set-up): the facet step checks every address
@@ -258,6 +262,11 @@ struct PrecData {
 template <class R>
 cudaError_t autotune_launches(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, PrecData<R>& P,
                               KOp& K, double* v1, double* v2, cudaStream_t st, char* report, int report_len);
+
+// Warps per block of the maintained-residual forward sweep for these sizes in precision R (0: the
+// sweep keeps the row-product form with a residual pass; facet blocks under 4 KB or 2 m_F > 32).
+template <class R>
+int facet_push_warps(const ElemSizes& s);
 
 template <class R>
 cudaError_t launch_precond(const ElemSizes& s, const DevTables& t, const DevMesh& m, const Layout& L, double nu,

@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("residual_dd", ctypes.c_int), ("asp", ctypes.c_int), ("lo_stab", ctypes.c_int),
                 ("outflow", ctypes.c_int), ("etol", ctypes.c_double), ("tune", ctypes.c_int),
-                ("tune_cache", ctypes.c_char_p)]
+                ("tune_cache", ctypes.c_char_p), ("facet_push", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -48,7 +48,7 @@ class Sizes(ctypes.Structure):
                [(n, ctypes.c_int32) for n in ("dim", "k", "nF", "n_bub", "nhF", "n_p", "n_A", "n_c", "mF",
                                                "ncolours", "gmg_levels", "nq_load")] + \
                [("bytes_resident", ctypes.c_int64)] + \
-               [(n, ctypes.c_int32) for n in ("facet_batch", "facet_threads", "apply_batch")]
+               [(n, ctypes.c_int32) for n in ("facet_batch", "facet_threads", "apply_batch", "push_warps")]
 
 
 class SolveInfo(ctypes.Structure):
