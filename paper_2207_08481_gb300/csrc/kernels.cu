@@ -453,8 +453,17 @@ __global__ void __launch_bounds__(256) k_apply_K(S s, DevTables t, DevMesh m, La
     xs[q] = v;
   }
   __syncthreads();
+  // the n_A rows of every element first, then the n_p pressure rows (warps do not mix the two kinds)
   for (int q = tid; q < nvalid * per; q += blockDim.x) {
-    const int e = q / per, i = q - e * per;
+    int e, i;
+    if (q < nvalid * nA) {
+      e = q / nA;
+      i = q - e * nA;
+    } else {
+      const int qq = q - nvalid * nA;
+      e = qq / np_;
+      i = nA + (qq - e * np_);
+    }
     const int64_t T = T0 + e;
     const double* xe = xs + e * per;
     if (i < nA) {
@@ -506,23 +515,65 @@ __device__ __forceinline__ void df_mac(DF& a, float xh, float xl, float yh, floa
   a.c = __fmaf_rn(xh, yl, a.c);
   a.c = __fmaf_rn(xl, yh, a.c);
 }
-__device__ __forceinline__ double df_value(const DF& a) { return (double)a.hi + ((double)a.lo + (double)a.c); }
+// The conversions between double and float pairs with integer operations on the IEEE bit patterns, so
+// that the apply spends no FP64-pipe instruction on them (FP64 runs at a small fraction of the FP32 rate
+// on this GPU).  Values outside the range the bit manipulation covers take the conversion instructions.
+// float -> double, exact.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+  if (ex == 0u || ex == 255u) return (double)f;   // subnormal, inf, nan
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ex + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// v = h + l with h the significand of v rounded to 24 bits (to nearest, ties away from zero) and l the
+// remainder rounded to float: |v - h - l| <= 2^-48 |v|.
+__device__ __forceinline__ void split_ff(double v, float& h, float& l) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ffull);
+  if ((b << 1) == 0ull) {   // +-0
+    h = l = __uint_as_float((unsigned)(b >> 32));
+    return;
+  }
+  if (ex < 949 || ex > 1149) {   // h or the scale of l would leave the normal float range
+    h = (float)v;
+    l = (float)(v - (double)h);
+    return;
+  }
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long m = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;   // 53-bit significand
+  unsigned long long mh = (m + 0x10000000ull) >> 29;                                 // 24 bits, rounded
+  const int r = (int)((long long)m - (long long)(mh << 29));                         // |r| <= 2^28, exact
+  int eh = ex;
+  if (mh == 0x1000000ull) {   // rounded up into the next binade
+    mh = 0x800000ull;
+    ++eh;
+  }
+  h = __uint_as_float(sgn | ((unsigned)(eh - 896) << 23) | (unsigned)(mh & 0x7fffffull));
+  const float scale = __uint_as_float((unsigned)(ex - 948) << 23);   // 2^(ex - 1075)
+  const float lr = (float)r * scale;
+  l = sgn ? -lr : lr;
+}
+// hi + (lo + c) as a double: lo + c rounded in FP32 (both are O(2^-24) of hi), then one FP64 add.
+__device__ __forceinline__ double df_value(const DF& a) { return f2d_bits(a.hi) + f2d_bits(__fadd_rn(a.lo, a.c)); }
 
-// y = K x with A_T as packed-lower float pairs and double-float arithmetic (mixed form).
+// y = K x with A_T as packed-lower float pairs and double-float arithmetic (mixed form).  The block
+// stages the pairs of EB elements with hi and lo of each entry side by side (one 8-byte shared load per
+// entry), and x split into float pairs the same way.
 template <class S>
 __global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m, Layout L,
                                                     const float* __restrict__ Ahi, const float* __restrict__ Alo,
                                                     const double* __restrict__ x, double* y, int EB, const int* stop) {
   if (stop && *stop) return;
-  extern __shared__ float skf[];
+  extern __shared__ __align__(16) float skf[];
   const int nA = s.n_A, np_ = s.n_p, nu_ = s.n_u, d = s.d, nfd = (s.d + 1) * s.nF;
   const int per = nA + np_, pp = packed_pad(s);
-  float* Ah = skf;                    // [EB][pp]
-  float* Al = Ah + EB * pp;           // [EB][pp]
-  float* xh = Al + EB * pp;           // [EB][per]
-  float* xl = xh + EB * per;          // [EB][per]
-  int* er = (int*)(xl + EB * per);    // [EB][4]
-  float* sg = (float*)(er + EB * 4);  // [EB][4]
+  float2* Ap = reinterpret_cast<float2*>(skf);    // [EB][pp] (hi, lo)
+  float2* Xp = Ap + (size_t)EB * pp;              // [EB][per] (hi, lo)
+  int* er = reinterpret_cast<int*>(Xp + (size_t)EB * per);   // [EB][4]
+  float* sg = reinterpret_cast<float*>(er + EB * 4);         // [EB][4]
   const int tid = threadIdx.x;
   const int64_t T0 = (int64_t)blockIdx.x * EB;
   const int nvalid = (int)((m.ne - T0) < EB ? (m.ne - T0) : EB);
@@ -533,8 +584,18 @@ __global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m,
     er[tid] = ok ? m.elem_rank[T * (d + 1) + f] : -1;
     sg[tid] = ok ? (float)m.signs[T * (d + 1) + f] : 0.f;
   }
-  vcopy16<float>(Ah, Ahi + T0 * pp, nvalid * pp, tid, blockDim.x);
-  vcopy16<float>(Al, Alo + T0 * pp, nvalid * pp, tid, blockDim.x);
+  {
+    // the block's elements are contiguous in Ahi / Alo; pp is a multiple of 4 (16-byte chunks)
+    const float4* hs = reinterpret_cast<const float4*>(Ahi + T0 * pp);
+    const float4* ls = reinterpret_cast<const float4*>(Alo + T0 * pp);
+    float4* dst = reinterpret_cast<float4*>(Ap);
+    const int nq = nvalid * pp / 4;
+    for (int q = tid; q < nq; q += blockDim.x) {
+      const float4 h = __ldg(hs + q), l = __ldg(ls + q);
+      dst[2 * q] = make_float4(h.x, l.x, h.y, l.y);
+      dst[2 * q + 1] = make_float4(h.z, l.z, h.w, l.w);
+    }
+  }
   __syncthreads();
   for (int q = tid; q < nvalid * per; q += blockDim.x) {
     const int e = q / per, i = q - e * per;
@@ -546,20 +607,28 @@ __global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m,
     } else {
       v = x[L.off_p + T * np_ + (i - nA)];
     }
-    const float h = (float)v;
-    xh[q] = h;
-    xl[q] = (float)(v - (double)h);
+    float h, l;
+    split_ff(v, h, l);
+    Xp[q] = make_float2(h, l);
   }
   __syncthreads();
+  // threads take the n_A rows of every element first, then the n_p pressure rows of every element, so
+  // that the warps do not mix the two kinds of rows
   for (int q = tid; q < nvalid * per; q += blockDim.x) {
-    const int e = q / per, i = q - e * per;
+    int e, i;
+    if (q < nvalid * nA) {
+      e = q / nA;
+      i = q - e * nA;
+    } else {
+      const int qq = q - nvalid * nA;
+      e = qq / np_;
+      i = nA + (qq - e * np_);
+    }
     const int64_t T = T0 + e;
-    const float* xe = xh + e * per;
-    const float* xle = xl + e * per;
+    const float2* xe = Xp + (size_t)e * per;
     DF acc{0.f, 0.f, 0.f};
     if (i < nA) {
-      const float* ah = Ah + e * pp;
-      const float* al = Al + e * pp;
+      const float2* ap = Ap + (size_t)e * pp;
       // one loop over the row, the packed index chosen per entry (row part j <= i, column part
       // j > i), so the lanes of a warp, which hold rows of different lengths, do not diverge
       const int row = i * (i + 1) / 2;
@@ -567,13 +636,16 @@ __global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m,
 #pragma unroll 4
       for (int j = 0; j < nA; ++j) {
         const int idx = j <= i ? row + j : colidx;
-        df_mac(acc, ah[idx], al[idx], xe[j], xle[j]);
+        const float2 a = ap[idx], xv = xe[j];
+        df_mac(acc, a.x, a.y, xv.x, xv.y);
         if (j >= i) colidx += j + 1;      // next: (j+1)(j+2)/2 + i
       }
       if (i < nu_) {  // (B^T x_p)_i = -s_i sum_j Bhat[j][i] x_p[j]
         const float sgn = i < nfd ? sg[e * 4 + i / s.nF] : 1.f;
-        for (int p = 0; p < np_; ++p)
-          df_mac(acc, -sgn * t.Bp_hi[p * nu_ + i], -sgn * t.Bp_lo[p * nu_ + i], xe[nA + p], xle[nA + p]);
+        for (int p = 0; p < np_; ++p) {
+          const float2 xv = xe[nA + p];
+          df_mac(acc, -sgn * t.Bp_hi[p * nu_ + i], -sgn * t.Bp_lo[p * nu_ + i], xv.x, xv.y);
+        }
       }
       const double v = df_value(acc);
       int64_t g = local_to_global(s, L, er + e * 4, T, i);
@@ -584,7 +656,8 @@ __global__ void __launch_bounds__(256) k_apply_K_df(S s, DevTables t, DevMesh m,
       const int jp = i - nA;
       for (int c = 0; c < nu_; ++c) {
         const float sgn = c < nfd ? sg[e * 4 + c / s.nF] : 1.f;
-        df_mac(acc, -sgn * t.Bp_hi[jp * nu_ + c], -sgn * t.Bp_lo[jp * nu_ + c], xe[c], xle[c]);
+        const float2 xv = xe[c];
+        df_mac(acc, -sgn * t.Bp_hi[jp * nu_ + c], -sgn * t.Bp_lo[jp * nu_ + c], xv.x, xv.y);
       }
       y[L.off_p + T * np_ + jp] = df_value(acc);
     }
@@ -627,9 +700,10 @@ __global__ void __launch_bounds__(256) k_apply_K_df_chunk(ElemSizes s, DevTables
       } else {
         v = x[L.off_p + T * np_ + (q - nA)];
       }
-      const float h = (float)v;
+      float h, l;
+      split_ff(v, h, l);
       xh[q] = h;
-      xl[q] = (float)(v - (double)h);
+      xl[q] = l;
     }
     DF acc[MAXR];
 #pragma unroll
