@@ -110,7 +110,7 @@ typedef struct {
                          R_{c-1}) (from the third cycle on; else 1) how much less the previous cycle reduced
                          the error than its residual.  The first cycle runs to rtol (mixed form: to
                          inner_rtol); each later one ends as soon as that bound, evaluated on its
-                         correction so far every 8 iterations, is <= etol.  The solve ends at the first
+                         correction so far every 4 iterations, is <= etol.  The solve ends at the first
                          cycle start after est_c <= etol whose recomputed residual meets rtol; the bound is
                          returned in mcs_solve_info.err_est.  With a pressure-dominated right-hand side
                          (nu << 1) the velocity error exceeds the relative residual by orders of magnitude,

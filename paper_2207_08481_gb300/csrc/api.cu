@@ -160,7 +160,17 @@ void build_precision(mcs_handle* h, PrecData<R>& P, const std::vector<Csr>& A, c
   cuda_check(cudaMemset((void*)P.Fs, 0, sizeof(R) * nint * (int64_t)fs_stride(s)), "memset");  // padding
   P.G = h->dalloc<R>(ne * (int64_t)g_stride(s));
   P.Aoi = h->dalloc<R>(ne * (int64_t)a_stride(s));
-  P.Eb = h->upload(cast_vec<R>(Eb));
+  {
+    // device layout [nint][d][mF][d] (facet vertex w, mode t, component a): each of the d vertices of a
+    // facet reads one contiguous slice in E^d^T
+    const int d = h->d, mF = s.mF, dd = d * d;
+    std::vector<R> Et(Eb.size());
+    for (int64_t rk = 0; rk < nint; ++rk)
+      for (int t = 0; t < mF; ++t)
+        for (int w = 0; w < d; ++w)
+          for (int a = 0; a < d; ++a) Et[((rk * d + w) * mF + t) * d + a] = (R)Eb[(rk * mF + t) * dd + w * d + a];
+    P.Eb = h->upload(Et);
+  }
   P.fvr = h->upload(fvr);
   P.vf_ptr = h->upload(vf_ptr);
   P.vf_idx = h->upload(vf_idx);
@@ -1028,7 +1038,9 @@ void minres_cycle(mcs_handle* h, const double* rhs, double* x_acc, double rtol, 
   const int* stop = &S->stop;
   const bool graphs = h->use_graphs && !h->prof;
   if (graphs && !h->gexec) capture_iterations(h, x_acc);
-  const int check_every = 8;  // iterations between reads of the convergence state
+  // iterations between reads of the convergence state; 4 in a cycle that may end on the error bound,
+  // whose check is cheap against the iterations a coarser check would run past it
+  const int check_every = cb.x_start ? 4 : 8;
   const int64_t nu_blk = h->L.off_p, np_blk = n - h->L.off_p;
   double* res = h->scratch + 3010;   // [|d_u|^2, |d_p|^2, |x_u|^2, |x_p|^2] of the early-end check
   while (true) {
@@ -1097,7 +1109,7 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
     // the cycle's achieved residual reduction and lag = max(1, (rho_c / rho_{c-1}) / R_{c-1}) how much
     // less the previous cycle reduced the error than the residual (from the third correction on), and
     // bounded by est_c = kSafety lag R_c rho_c.  The first cycle runs to rtol (mixed: inner_rtol); every
-    // later one runs until its own correction so far shows the bound met (checked every 8 iterations),
+    // later one runs until its own correction so far shows the bound met (checked every 4 iterations),
     // or to the least reduction r_min.
     constexpr double kSafety = 3.0;
     const double r_min = mixed ? h->opt.inner_rtol : 1e-12;   // least reduction asked of one cycle
@@ -1115,7 +1127,7 @@ int mcs_solve(mcs_handle* h, const double* F, double* x, mcs_solve_info* info) {
       const bool err_ok = etol > 0 && est <= etol;
       const double rtol_now = (etol > 0 && !err_ok) ? 0.0 : h->opt.rtol;
       // after the first correction a cycle runs to the least reduction and ends early once its own
-      // correction shows the error bound met (the check every 8 iterations)
+      // correction shows the error bound met (the check every 4 iterations)
       const bool adaptive = etol > 0 && !err_ok && ncorr >= 1;
       const double floor_now = etol > 0 ? ((err_ok || adaptive) ? r_min : r_next) : floor_rtol;
       CycleBound cbound;

@@ -1680,11 +1680,11 @@ __global__ void __launch_bounds__(256) k_facet_step(S s, DevMesh m, Layout L, co
   cp_async_wait_all();
 }
 
-// xbar = E^d^T rr: one warp per P1 vertex; the lanes take the (incident facet, mode) pairs and the
+// xbar = E^d^T rr (rr + rr2 when rr2 is given): one warp per P1 vertex; the lanes take the (incident facet, mode) pairs and the
 // d sums are combined by a fixed butterfly, so the result does not depend on scheduling.
 template <class R>
 __global__ void k_embed_T(ElemSizes s, Layout L, const R* Eb, const int32_t* vf_ptr, const int32_t* vf_idx,
-                          int64_t nP1, const R* rr, R* xb, const int* stop) {
+                          int64_t nP1, const R* rr, const R* rr2, R* xb, const int* stop) {
   if (stop && *stop) return;
   const int d = s.d, mF = s.mF, dd = d * d, lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1694,8 +1694,9 @@ __global__ void k_embed_T(ElemSizes s, Layout L, const R* Eb, const int32_t* vf_
     for (int q = lane; q < ne * mF; q += 32) {
       const int ei = q / mF, t = q - ei * mF;
       const int32_t rk = vf_idx[2 * (e0 + ei)], w = vf_idx[2 * (e0 + ei) + 1];
-      const R r = rr[coup_idx<R>(s, L, rk, t)];
-      const R* B = Eb + (int64_t)rk * mF * dd + t * dd + w * d;
+      const int64_t ci = coup_idx<R>(s, L, rk, t);
+      const R r = rr2 ? rr[ci] + rr2[ci] : rr[ci];   // rr2: the residual kept as two partial sums
+      const R* B = Eb + (((int64_t)rk * d + w) * mF + t) * d;   // layout [nint][d (w)][mF][d (a)]
       for (int a = 0; a < d; ++a) acc[a] += B[a] * r;
     }
     for (int a = 0; a < d; ++a) {
@@ -1716,12 +1717,12 @@ __global__ void k_embed(ElemSizes s, Layout L, const R* Eb, const int32_t* fvr, 
        q += (int64_t)gridDim.x * blockDim.x) {
     int64_t rk = q / mF;
     int t = (int)(q % mF);
-    const R* B = Eb + rk * mF * dd + t * dd;
     R v = 0;
     for (int w = 0; w < d; ++w) {
       int32_t vr = fvr[rk * d + w];
       if (vr < 0) continue;
-      for (int a = 0; a < d; ++a) v += B[w * d + a] * xb[(int64_t)vr * d + a];
+      const R* B = Eb + ((rk * d + w) * mF + t) * d;   // layout [nint][d (w)][mF][d (a)]
+      for (int a = 0; a < d; ++a) v += B[a] * xb[(int64_t)vr * d + a];
     }
     x[coup_idx<R>(s, L, (int32_t)rk, t)] += v;
   }
@@ -2284,19 +2285,15 @@ __global__ void __launch_bounds__(256) k_facet_push_warp(S s, const R* __restric
 }
 
 // q_0 = b - tb, q_1 = 0 (entries of all facet slots): the partial residuals before a forward sweep from
-// x = 0.  With COMBINE: rr = q_0 + q_1 on the modes t < m_F, the residual after the sweep.
-template <class R, bool COMBINE>
-__global__ void k_push_vectors(int64_t nint, int fs, int mF, const R* __restrict__ b, const R* __restrict__ tb,
-                               R* q0, R* q1, R* rr, const int* stop) {
+// x = 0.
+template <class R>
+__global__ void k_push_init(int64_t nint, int fs, const R* __restrict__ b, const R* __restrict__ tb, R* q0, R* q1,
+                            const int* stop) {
   if (stop && *stop) return;
   const int64_t total = nint * fs;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    if (COMBINE) {
-      if ((int)(i % fs) < mF) rr[i] = q0[i] + q1[i];
-    } else {
-      q0[i] = b[i] - (tb ? tb[i] : (R)0);
-      q1[i] = (R)0;
-    }
+    q0[i] = b[i] - (tb ? tb[i] : (R)0);
+    q1[i] = (R)0;
   }
 }
 
@@ -2612,20 +2609,14 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
   if (P.multiplicative && P.push_warps > 0 && P.q0 && P.q1) {
     // forward sweeps with the maintained residual (from x = 0: q_0 = b - tb, q_1 = 0), then rr = q_0 + q_1
     if (L.nint > 0) {
-      k_push_vectors<R, false><<<g, bs, 0, st>>>(L.nint, L.fstride, s.mF, b, tb, P.q0, P.q1, nullptr, stop);
+      k_push_init<R><<<g, bs, 0, st>>>(L.nint, L.fstride, b, tb, P.q0, P.q1, stop);
       note_launch();
-      dbg_sync(P, st, "k_push_vectors");
+      dbg_sync(P, st, "k_push_init");
     }
     for (int sw = 0; sw < P.smooth; ++sw)
       for (int c = 0; c < P.ncol; ++c)
         facet_push<R>(s, m, L, P, sw == 0 ? nullptr : x, x, co[c], co[c + 1] - co[c], stop, st);   // sweep 0: x_F = 0
-    if (L.nint > 0) {
-      prof_begin(PROF_FACET_RES, st);
-      k_push_vectors<R, true><<<g, bs, 0, st>>>(L.nint, L.fstride, s.mF, nullptr, nullptr, P.q0, P.q1, P.rr, stop);
-      note_launch();
-      prof_end(PROF_FACET_RES, (double)L.nint * s.mF * 3.0 * sizeof(R), (double)L.nint * s.mF, st);
-      dbg_sync(P, st, "k_push_vectors");
-    }
+    // the residual rr = q_0 + q_1 is summed where E^d^T reads it
   } else if (P.multiplicative) {
     for (int sw = 0; sw < P.smooth; ++sw)
       for (int c = 0; c < P.ncol; ++c)
@@ -2644,7 +2635,9 @@ static void asp_core(const ElemSizes& s, const DevMesh& m, const Layout& L, Prec
     int64_t ge = (P.nP1 * 32 + bs - 1) / bs;  // a warp per P1 vertex
     if (ge > (int64_t)sm_count() * 32) ge = (int64_t)sm_count() * 32;
     if (ge < 1) ge = 1;
-    k_embed_T<R><<<(unsigned)ge, bs, 0, st>>>(s, L, P.Eb, P.vf_ptr, P.vf_idx, P.nP1, P.rr, P.pb[top], stop);
+    const bool push = P.multiplicative && P.push_warps > 0 && P.q0 && P.q1;
+    k_embed_T<R><<<(unsigned)ge, bs, 0, st>>>(s, L, P.Eb, P.vf_ptr, P.vf_idx, P.nP1, push ? P.q0 : P.rr,
+                                             push ? P.q1 : nullptr, P.pb[top], stop);
   }
   note_launch();
   dbg_sync(P, st, "k_embed_T");

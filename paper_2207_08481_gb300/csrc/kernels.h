@@ -52,7 +52,8 @@ struct DevMesh {
   const int32_t* fsr;        // [nint][2][d+1] interior ranks of the facets of each side element
   // facet records in colour order (64 bytes each): [0] interior rank r, [1..2] the two elements,
   // [3..4] local facet indices, [5..] interior ranks of the facets of element 0 (d+1), then of
-  // element 1 (d+1); unused entries -1
+  // element 1 (d+1); [13] bit side*(d+1) + f set when element [1 + side] is side 1 of the facet
+  // [5 + side*(d+1) + f]; unused entries -1
   const int4* frec;
   const int32_t* fpos;       // [nint] position of interior facet r in colour order (its record index)
   const int8_t* fout;        // [nint] 1 for an outflow facet (phantom uhat slots); NULL without outflow
@@ -223,7 +224,7 @@ struct PrecData {
   R* Fs;                    // facet stream [nint][fs_stride] in colour order (slabs of A^d, D_F^{-1})
   const R* G;
   const R* Aoi;
-  const R* Eb;              // [nint][mF][d*d]
+  const R* Eb;              // [nint][d][mF][d]: E^d_F entry (mode t, facet vertex w, component a) at (w*mF + t)*d + a
   const int32_t* fvr;       // [nint][d] P1 rank of each facet vertex (-1 on the boundary)
   const int32_t* vf_ptr;    // P1 vertex -> (facet rank, facet-vertex index) list, CSR over P1 vertices
   const int32_t* vf_idx;    // pairs (facet rank, col)
