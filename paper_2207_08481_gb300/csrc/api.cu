@@ -1278,7 +1278,8 @@ int mcs_profile_read(mcs_handle* h, mcs_kernel_stat* out, int max_n) {
     if (!h->prof) return 0;
     h->prof->collect();
     static const char* names[PROF_NCLASS] = {"condense", "facet_blocks", "apply_K", "facet_gs_step",
-                                             "facet_residual", "elem_prologue", "elem_epilogue", "gmg_vcycle"};
+                                             "facet_residual", "elem_prologue", "elem_epilogue", "gmg_vcycle",
+                                             "facet_push"};
     int n = 0;
     for (int c = 0; c < PROF_NCLASS && n < max_n; ++c) {
       mcs_kernel_stat& o = out[n++];

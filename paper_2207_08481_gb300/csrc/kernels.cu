@@ -2336,7 +2336,7 @@ static cudaError_t facet_push(const ElemSizes& s, const DevMesh& m, const Layout
     int64_t blocks = (int64_t)sm_count() * (c & 255);
     const int64_t need = (n + nw - 1) / nw;
     if (blocks > need) blocks = need;
-    prof_begin(PROF_FACET_GS, st);
+    prof_begin(PROF_FACET_PUSH, st);
     note_launch();
     k_facet_push_warp<R, SZ><<<(unsigned)blocks, nw * 32, wsm, st>>>(sz, fs0, xin, x, P.q0, P.q1, ri, n, stop,
                                                                       P.err);
@@ -2344,7 +2344,7 @@ static cudaError_t facet_push(const ElemSizes& s, const DevMesh& m, const Layout
     // written; here q_0, q_1 of the facet stand for b, tb); the q segments of the neighbours, like the
     // gathered x there, are L2-resident vectors
     const double per = 2.0 * s.mF * s.n_c + (double)s.mF * s.mF + 4.0 * s.mF;
-    prof_end(PROF_FACET_GS, (double)n * per * sizeof(R), 2.0 * (double)n * (2.0 * s.mF * s.n_c + s.mF * s.mF), st);
+    prof_end(PROF_FACET_PUSH, (double)n * per * sizeof(R), 2.0 * (double)n * (2.0 * s.mF * s.n_c + s.mF * s.mF), st);
   });
   dbg_sync(P, st, "k_facet_push_warp");
   return cudaGetLastError();

@@ -12,7 +12,7 @@ namespace mcs {
 // points install the handle's profiler for the duration of a call; launchers bracket their
 // main kernel with prof_begin / prof_end (no-ops when no profiler is installed).
 enum ProfClass { PROF_CONDENSE = 0, PROF_FACET_BLOCKS, PROF_APPLY, PROF_FACET_GS, PROF_FACET_RES, PROF_PROLOGUE,
-                 PROF_EPILOGUE, PROF_GMG, PROF_NCLASS };
+                 PROF_EPILOGUE, PROF_GMG, PROF_FACET_PUSH, PROF_NCLASS };
 struct Profiler;
 extern thread_local Profiler* g_prof;
 void prof_begin(int cls, cudaStream_t st);
