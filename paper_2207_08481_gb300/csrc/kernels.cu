@@ -1498,7 +1498,7 @@ __global__ void __launch_bounds__(256) k_elem_epilogue(S s, DevTables t, DevMesh
 //   r_F = b_F - tb_F - sum_{T in F} (A^d_T x_T)|_F,
 // UPDATE: x_F += D_F^{-1} r_F (block Gauss-Seidel within one colour); else rr_F = r_F.
 // Vectors are in the preconditioner layout (L.fstride > 0): the m_F coupling values of a facet
-// are one 32-byte-aligned segment, fetched with 16-byte copies.  Persistent blocks walk batches
+// are one 16-byte-aligned segment, fetched with 16-byte copies.  Persistent blocks walk batches
 // of FB facets.  Everything a batch needs (A^d slabs of both elements, D_F^{-1}, the segments of
 // all facets of both elements, b, tb) is fetched with asynchronous copies into one of two
 // shared-memory stages while the previous batch is computed; the 64-byte facet records are read

@@ -33,8 +33,8 @@ struct Layout {
   int64_t off_o, off_h, off_p;
   // 0: the external layout [u_d | u_o | uhat | p].  > 0: the preconditioner's internal layout, in
   // which the m_F coupling dofs of interior facet r (its u_d modes, then its uhat modes) sit
-  // together at r*fstride .. r*fstride + m_F - 1 (fstride = m_F rounded up to 32 bytes), followed
-  // by the bubbles and the pressure; one facet's values are one 32-byte-aligned segment.
+  // together at r*fstride .. r*fstride + m_F - 1 (fstride = m_F rounded up to 16 bytes), followed
+  // by the bubbles and the pressure; one facet's values are one 16-byte-aligned segment.
   int64_t fstride = 0;
 };
 
@@ -91,9 +91,10 @@ template <class S> __host__ __device__ inline int slab_pad(const S& s) { return 
 template <class S> __host__ __device__ inline int g_stride(const S& s) { return pad4(s.n_bub * s.n_c); }
 template <class S> __host__ __device__ inline int a_stride(const S& s) { return pad4(s.n_bub * s.n_bub); }
 template <class S> __host__ __device__ inline int dinv_stride(const S& s) { return pad4(s.mF * s.mF); }
-// facet stride of the preconditioner layout: m_F rounded up to a multiple of 32 bytes
+// facet stride of the preconditioner layout: m_F rounded up to a multiple of 16 bytes (one 16-byte copy
+// granule; 3D k = 2 in FP32: 12 values, 48 bytes)
 template <class S> __host__ __device__ inline int facet_stride(const S& s, int elem_bytes) {
-  const int v = 32 / elem_bytes;
+  const int v = 16 / elem_bytes;
   return (s.mF + v - 1) / v * v;
 }
 template <class S>
