@@ -414,9 +414,9 @@ def _c2(args, torch, mcs, workloads, timed, info_dict):
     return out
 
 
-def _random_solve(h, torch, seed, warm=True):
+def _random_solve(h, torch, seed, warm=True, keep_x=False):
     """One warm-up (optional) and one timed mcs_solve for F = M_u c, c ~ N(0, 1) on the velocity dofs
-    (seeded)."""
+    (seeded); keep_x: also the solution (host copy)."""
     s = h.sizes
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
@@ -434,6 +434,8 @@ def _random_solve(h, torch, seed, warm=True):
     info = h.solve(F, x)
     e1.record()
     torch.cuda.synchronize()
+    if keep_x:
+        return round(e0.elapsed_time(e1), 2), info, x.cpu()
     return round(e0.elapsed_time(e1), 2), info
 
 
@@ -509,13 +511,16 @@ def _multi_degree(args, torch, mcs):
         t_sep[f"k={k}"] = round(timed(h.condense, warm=k <= 4), 2)
     t_batch = timed(lambda: mcs.condense_batch(hs), warm=False)
     solves = {}
+    x_seq = []
     for k, h in zip(ks, hs):
-        ms, info = _random_solve(h, torch, 100 + k, warm=k <= 4)
+        ms, info, x = _random_solve(h, torch, 100 + k, warm=k <= 4, keep_x=True)
+        x_seq.append(x)
         solves[f"k={k}"] = {"ndof": int(h.sizes.ndof), "ms": ms, "iterations": info.iterations,
                             "cycles": info.refinements, "rel_res": info.rel_res_precond, "err_est": info.err_est,
                             "resident_gb": round(h.sizes.bytes_resident / 1e9, 2)}
     for h in hs:
         h.close()
+    concurrent = _concurrent_solves(ks, torch, mcs, x_seq, sum(v["ms"] for v in solves.values()))
     # k = 1 with the stabilisation weight nu h_T^2 (lo_stab = 1) instead of nu: same right-hand side
     h1 = mcs.Handle.structured(3, 16, 1, 1.0, maxit=8000, lo_stab=1, **FORMS["mixed"])
     h1.condense()
@@ -526,7 +531,50 @@ def _multi_degree(args, torch, mcs):
     return {"config": "3D unit cube, 16^3 cells x 6 = 24,576 tetrahedra each, k = 1 (lowest-order variant), 2, 3, 4, 5, 6, "
                       "nu = 1, mixed form (rel. residual 1e-8, error estimate <= 1e-8), random F = M_u c (c ~ N(0,1))",
             "condense_batched_ms": round(t_batch, 2), "condense_separate_ms": round(sum(t_sep.values()), 2),
-            "condense_separate_by_k_ms": t_sep, "solves": solves}
+            "condense_separate_by_k_ms": t_sep, "solves": solves, "solves_concurrent": concurrent}
+
+
+def _concurrent_solves(ks, torch, mcs, x_seq, sequential_ms):
+    """The six problems again, each handle on a stream of its own: condensed in one batched launch, then
+    the six solves issued at once from one host thread each, so their kernels overlap on the device.  Same
+    right-hand sides as the solves one by one; the solutions must agree with those bit for bit."""
+    hs = [mcs.Handle.structured(3, 16, k, 1.0, stream=torch.cuda.Stream(), maxit=8000 if k == 1 else 2000,
+                                **FORMS["mixed"]) for k in ks]
+    mcs.condense_batch(hs)
+    Fs, xs = [], []
+    for k, h in zip(ks, hs):
+        with torch.cuda.stream(h.stream):
+            s = h.sizes
+            g = torch.Generator(device="cuda")
+            g.manual_seed(100 + k)
+            c = torch.zeros(s.ndof, dtype=torch.float64, device="cuda")
+            c[:s.off_h] = torch.randn(s.off_h, dtype=torch.float64, device="cuda", generator=g)
+            F = torch.zeros_like(c)
+            h.mass_velocity(c, F)
+            Fs.append(F)
+            xs.append(torch.zeros_like(F))
+    torch.cuda.synchronize()
+    infos = [None] * len(hs)
+
+    def run(i):
+        infos[i] = hs[i].solve(Fs[i], xs[i])
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(len(hs))]
+    t0 = time.perf_counter()
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3
+    same = all(torch.equal(xs[i].cpu(), x_seq[i]) for i in range(len(hs)))
+    out = {"wall_ms": round(wall, 2), "sum_of_solves_one_by_one_ms": round(sequential_ms, 2),
+           "iterations": {f"k={k}": infos[i].iterations for i, k in enumerate(ks)},
+           "identical_to_solves_one_by_one": bool(same),
+           "how": "one stream per handle, one host thread per solve, after one batched condensation"}
+    for h in hs:
+        h.close()
+    return out
 
 
 def _serving(args, rank, world, torch, dist, n, rate):
@@ -728,11 +776,20 @@ def main():
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving traces (--serve-requests at --serve-rate, then --serve-requests2 at "
                          "--serve-rate2) and print their summaries")
+    ap.add_argument("--c4-only", action="store_true",
+                    help="the batched six-degree sweep alone (condensation batched and one by one, solves one by "
+                         "one and concurrently)")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None)
     ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+    elif args.c4_only:
+        import torch
+        from paper_2207_08481_gb300 import build
+        build.build()
+        import paper_2207_08481_gb300.mcs as mcs
+        print(json.dumps({"multi_degree": _multi_degree(args, torch, mcs)}), flush=True)
     elif args.serve_only:
         import torch
         from paper_2207_08481_gb300 import build
