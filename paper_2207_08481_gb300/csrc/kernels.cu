@@ -322,7 +322,7 @@ template <class R>
 __global__ void k_facet_blocks(ElemSizes s, DevMesh m, R* Fs) {
   extern __shared__ double sm2[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int mF = s.mF, nc = s.n_c;
+  const int mF = s.mF;
   double* A = sm2 + (int64_t)wib * 2 * mF * mF;
   double* I = A + mF * mF;
   for (int64_t r = (int64_t)blockIdx.x * wpb + wib; r < m.nint; r += (int64_t)gridDim.x * wpb) {
@@ -1686,7 +1686,7 @@ template <class R>
 __global__ void k_embed_T(ElemSizes s, Layout L, const R* Eb, const int32_t* vf_ptr, const int32_t* vf_idx,
                           int64_t nP1, const R* rr, const R* rr2, R* xb, const int* stop) {
   if (stop && *stop) return;
-  const int d = s.d, mF = s.mF, dd = d * d, lane = threadIdx.x & 31;
+  const int d = s.d, mF = s.mF, lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = w0; v < nP1; v += ws) {
     const int32_t e0 = vf_ptr[v], ne = vf_ptr[v + 1] - e0;
@@ -1712,7 +1712,7 @@ template <class R>
 __global__ void k_embed(ElemSizes s, Layout L, const R* Eb, const int32_t* fvr, int64_t nint, const R* xb, R* x,
                         const int* stop) {
   if (stop && *stop) return;
-  const int d = s.d, mF = s.mF, dd = d * d;
+  const int d = s.d, mF = s.mF;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nint * mF;
        q += (int64_t)gridDim.x * blockDim.x) {
     int64_t rk = q / mF;
