@@ -169,6 +169,54 @@ def _s8d_bytes_per_colour_launch(s, ncol):
     return 4.0 * (s.ne * s.n_c * (s.n_c + 1) / 2 + s.nint * s.mF * s.mF) / ncol
 
 
+def _roofline(stats, sizes, peak, peak_kind):
+    """The roofline object of the bench line for the dominant kernel class of a profiled step.  stats:
+    per class {launches, ms, bytes, flops} from the library's CUDA-event timers; sizes: the handle's
+    mcs_sizes (ne, nint, n_c, mF, ncolours); peak: HBM GB/s."""
+    # the facet-block Gauss-Seidel sweep runs as two kernels (maintained-residual forward colours and
+    # row-product backward colours, the same bytes per facet): one class for the choice of the dominant one
+    rstats = dict(stats)
+    sweep_parts = {}
+    if stats.get("facet_push", {}).get("launches"):
+        a_, b_ = stats["facet_gs_step"], stats["facet_push"]
+        rstats["facet_gs_step"] = {k: a_[k] + b_[k] for k in ("launches", "ms", "bytes", "flops")}
+        del rstats["facet_push"]
+        for label, key in (("row_products", "facet_gs_step"), ("push", "facet_push")):
+            v = stats[key]
+            if v["launches"]:
+                us = 1e3 * v["ms"] / v["launches"]
+                sweep_parts[label] = {"launches": v["launches"], "avg_launch_us": round(us, 2),
+                                      "frac": round(v["bytes"] / v["launches"] / (us * 1e-6) / 1e9 / peak, 4),
+                                      "traffic": _traffic(key, HEADLINE)}
+    name, st = max(rstats.items(), key=lambda kv: kv[1]["ms"])
+    nl = max(st["launches"], 1)
+    per_launch_ms = st["ms"] / nl
+    if name in ("condense",):
+        achieved = st["flops"] / nl / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": 1.20, "unit": "TFLOP/s",
+                "frac": achieved / 1.20, "traffic": None, "peak_kind": "measured FP64 FMA probe"}
+    else:
+        achieved = st["bytes"] / nl / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": _traffic(name, HEADLINE),
+                "algorithmic_bytes_per_launch": st["bytes"] / nl,
+                "avg_launch_us": round(per_launch_ms * 1e3, 2), "peak_kind": peak_kind,
+                "measured": "CUDA events around each launch on the handle's stream, one profiled step after "
+                            "the timed loop"}
+        if name == "facet_gs_step" and sweep_parts:
+            roof["kernel"] = "facet_gs_step (push forward colours + row-product backward colours)"
+            roof["parts"] = sweep_parts
+            tr = [(p_["traffic"], p_["launches"]) for p_ in sweep_parts.values()]
+            roof["traffic"] = (sum(t * n for t, n in tr) / sum(n for _, n in tr)
+                               if all(t is not None for t, _ in tr) else None)
+        if name in ("facet_gs_step", "facet_push"):
+            s8 = _s8d_bytes_per_colour_launch(sizes, sizes.ncolours)
+            roof["s8d_bytes_per_launch"] = s8
+            roof["frac_s8d"] = round(s8 / (per_launch_ms * 1e-3) / 1e9 / peak, 4)
+            roof["layout_over_s8d"] = round(st["bytes"] / nl / s8, 3)
+    return roof
+
+
 def run_gpu(args):
     import torch
 
@@ -314,47 +362,7 @@ def run_gpu(args):
 
     # ---------------- roofline of the dominant kernel class
     peak, peak_kind = _peaks()
-    # the facet-block Gauss-Seidel sweep runs as two kernels (maintained-residual forward colours and
-    # row-product backward colours, the same bytes per facet): one class for the choice of the dominant one
-    rstats = dict(stats)
-    sweep_parts = {}
-    if stats.get("facet_push", {}).get("launches"):
-        a_, b_ = stats["facet_gs_step"], stats["facet_push"]
-        rstats["facet_gs_step"] = {k: a_[k] + b_[k] for k in ("launches", "ms", "bytes", "flops")}
-        del rstats["facet_push"]
-        for label, key in (("row_products", "facet_gs_step"), ("push", "facet_push")):
-            v = stats[key]
-            if v["launches"]:
-                us = 1e3 * v["ms"] / v["launches"]
-                sweep_parts[label] = {"launches": v["launches"], "avg_launch_us": round(us, 2),
-                                      "frac": round(v["bytes"] / v["launches"] / (us * 1e-6) / 1e9 / peak, 4),
-                                      "traffic": _traffic(key, HEADLINE)}
-    name, st = max(rstats.items(), key=lambda kv: kv[1]["ms"])
-    nl = max(st["launches"], 1)
-    per_launch_ms = st["ms"] / nl
-    if name in ("condense",):
-        achieved = st["flops"] / nl / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": 1.20, "unit": "TFLOP/s",
-                "frac": achieved / 1.20, "traffic": None, "peak_kind": "measured FP64 FMA probe"}
-    else:
-        achieved = st["bytes"] / nl / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": _traffic(name, HEADLINE),
-                "algorithmic_bytes_per_launch": st["bytes"] / nl,
-                "avg_launch_us": round(per_launch_ms * 1e3, 2), "peak_kind": peak_kind,
-                "measured": "CUDA events around each launch on the handle's stream, one profiled step after "
-                            "the timed loop"}
-        if name == "facet_gs_step" and sweep_parts:
-            roof["kernel"] = "facet_gs_step (push forward colours + row-product backward colours)"
-            roof["parts"] = sweep_parts
-            tr = [(p_["traffic"], p_["launches"]) for p_ in sweep_parts.values()]
-            roof["traffic"] = (sum(t * n for t, n in tr) / sum(n for _, n in tr)
-                               if all(t is not None for t, _ in tr) else None)
-        if name in ("facet_gs_step", "facet_push"):
-            s8 = _s8d_bytes_per_colour_launch(sizes, sizes.ncolours)
-            roof["s8d_bytes_per_launch"] = s8
-            roof["frac_s8d"] = round(s8 / (per_launch_ms * 1e-3) / 1e9 / peak, 4)
-            roof["layout_over_s8d"] = round(st["bytes"] / nl / s8, 3)
+    roof = _roofline(stats, sizes, peak, peak_kind)
     share = {k: round(v["ms"] / sum(u["ms"] for u in stats.values()), 4) for k, v in stats.items() if v["launches"]}
     # per class of the profiled step: launches, device ms, algorithmic GB/s (or TFLOP/s for the condensation)
     kstats = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
